@@ -1,0 +1,303 @@
+"""Plain FP64 CPU oracle of the THC second-order self-energy.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import this
+module: only the tests, the smoke check and the CPU-baseline leg of the
+benchmark use it.  It shares no code with the CUDA path; both take their
+inputs from the seeded generators in ``workloads``.
+
+Conventions (Sec. II.A of arXiv:2404.17744, read for real orbitals and a
+closed-shell restricted reference):
+
+* G_pq(tau) = -<T p(tau) q^dagger>, so for 0 < tau < beta
+  G(tau) is negative-definite-like and G(-tau) = -G(beta - tau).
+* Chemist-notation integrals from the THC factors (Eq. THC_ERI):
+  (pq|rs) = sum_PQ X_pP X_qP V_PQ X_rQ X_sQ, with the paper's core matrix
+  U_PQ written V here.
+* G and Sigma are per spin; the direct (bubble) term carries the factor -2
+  of the closed spin loop, the exchange (SOX) term carries +1.  The paper
+  prints the SOX expression (Sec. II.C) with an overall minus sign; with the
+  G convention above that sign yields a negative exchange contribution to
+  the Galitskii-Migdal energy, opposite to second-order perturbation theory.
+  The oracle therefore uses +1, the reading that makes E_dyn[G0] equal twice
+  the textbook closed-shell MP2 energy at low temperature; the printed sign
+  matches if the paper's "G(-tau)" stands for G(beta - tau).
+
+Two routes are implemented for each term:
+
+* the four-index definitions (feasible for n up to ~10), and
+* the paper's THC contraction order for SOX (Sec. II.C, the nine-step
+  scheme from U_Pqs to Sigma_tr) and the THC form of the direct term that
+  the paper takes over from THC-GW (derived in the docstring of
+  ``sigma_direct_thc``).
+
+Pins (tests/test_oracle_pins.py): four-index agreement, one-orbital closed
+form, finite-temperature MP2 closed form, zero-temperature textbook MP2,
+symmetry, V-scaling, fragment separability.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Overall factors of the two second-order terms (per-spin G, restricted).
+C_DIRECT = -2.0
+C_SOX = +1.0
+
+
+# ---------------------------------------------------------------- integrals
+def eri_from_thc(X: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """(pq|rs) = sum_PQ X_pP X_qP V_PQ X_rQ X_sQ (Eq. THC_ERI, real factors)."""
+    pair = np.einsum("pP,qP->pqP", X, X)
+    return np.einsum("pqP,PQ,rsQ->pqrs", pair, V, pair, optimize=True)
+
+
+def g_minus_tau(G_beta_minus_tau: np.ndarray) -> np.ndarray:
+    """G(-tau) = -G(beta - tau) (fermionic antiperiodicity, 0 < tau < beta)."""
+    return -G_beta_minus_tau
+
+
+# ------------------------------------------------ four-index (definition) routes
+def sigma_sox_four_index(v: np.ndarray, G: np.ndarray, Gm: np.ndarray) -> np.ndarray:
+    """SOX self-energy at one tau from its four-index definition (Sec. II.C).
+
+    Sigma_tr = C_SOX * sum_{pqsuvw} (pr|qs)(tu|vw) G_wp(tau) G_uq(tau) G_sv(-tau)
+    G, Gm: n x n arrays G(tau), G(-tau).  Unoptimised einsum: the sum as
+    written, one nested loop over all eight indices.
+    """
+    return C_SOX * np.einsum("prqs,tuvw,wp,uq,sv->tr", v, v, G, G, Gm, optimize=False)
+
+
+def sigma_direct_four_index(v: np.ndarray, G: np.ndarray, Gm: np.ndarray) -> np.ndarray:
+    """Second-order direct (bubble) self-energy at one tau, four-index form.
+
+    Sigma_tr = C_DIRECT * sum (tu|vw)(xr|yz) G_ux(tau) G_vz(tau) G_yw(-tau):
+    the interaction line (tu|vw) attaches the external index t, the line
+    (xr|yz) the external index r; the bubble closes over (v,w) and (y,z).
+    """
+    return C_DIRECT * np.einsum("tuvw,xryz,ux,vz,yw->tr", v, v, G, G, Gm, optimize=False)
+
+
+# ---------------------------------------------------------- THC routes
+def thc_U(X: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """U_Pqs = sum_Q V_PQ X_qQ X_sQ (Eq. U_contraction), shape N x n x n."""
+    N = V.shape[0]
+    n = X.shape[0]
+    kr = (X[:, None, :] * X[None, :, :]).reshape(n * n, N)  # [(q,s), Q] = X_qQ X_sQ
+    return (V @ kr.T).reshape(N, n, n)
+
+
+def sigma_sox_thc(X: np.ndarray, U: np.ndarray, G: np.ndarray, Gm: np.ndarray,
+                  return_intermediates: bool = False):
+    """SOX at one tau in the paper's THC order (Sec. II.C scheme).
+
+    Steps, with lower-case AO and upper-case THC indices:
+      G_Rq   = sum_u X_uR G_uq(tau)
+      G_wP   = sum_p G_wp(tau) X_pP
+      A_Pqv  = sum_s U_Pqs G_sv(-tau)
+      B_PRv  = sum_q A_Pqv G_Rq
+      C_RvP  = sum_w U_Rvw G_wP
+      D_PR   = sum_v C_RvP B_PRv
+      S_RP   = C_SOX * D_PR
+      Sigma_tr = sum_PR X_tR S_RP X_rP
+    (The printed summation labels of the two projections are read as sum_u
+    and sum_p.)
+    """
+    G_Rq = X.T @ G
+    G_wP = G @ X
+    A = np.matmul(U, Gm)                               # [P, q, v]
+    B = np.einsum("Pqv,Rq->PRv", A, G_Rq, optimize=True)
+    C = np.einsum("Rvw,wP->RvP", U, G_wP, optimize=True)
+    D = np.einsum("RvP,PRv->PR", C, B, optimize=True)
+    S_RP = C_SOX * D.T
+    sigma = X @ S_RP @ X.T
+    if return_intermediates:
+        return sigma, dict(G_Rq=G_Rq, G_wP=G_wP, A=A, B=B, C=C, D=D)
+    return sigma
+
+
+def sigma_direct_thc(X: np.ndarray, V: np.ndarray, G: np.ndarray, Gm: np.ndarray) -> np.ndarray:
+    """Direct term at one tau in THC form.
+
+    Inserting Eq. THC_ERI into both interaction lines of the direct term,
+      Sigma_tr = C_DIRECT * sum_{PQRS} X_tP X_rR V_PQ V_RS G^X_PR(tau) G^X_QS(tau) G^X_SQ(-tau)
+    with G^X(tau) = X^T G(tau) X.  Hence, with the polarisation
+      Pi_QS = G^X_QS(tau) G^X_SQ(-tau)   and   W = V Pi V,
+      Sigma = C_DIRECT * X (G^X(tau) o W) X^T        (o = elementwise).
+    """
+    GX = X.T @ G @ X
+    GXm = X.T @ Gm @ X
+    Pi = GX * GXm.T
+    W = V @ Pi @ V
+    return C_DIRECT * (X @ (GX * W) @ X.T)
+
+
+def sigma_thc(X: np.ndarray, V: np.ndarray, G_tau: np.ndarray, G_bmt: np.ndarray,
+              U: np.ndarray | None = None, terms: str = "both") -> np.ndarray:
+    """Sigma(tau_k) = Sigma^dir + Sigma^SOX at every tau point (THC routes).
+
+    G_tau[k] = G(tau_k), G_bmt[k] = G(beta - tau_k); returns n_tau x n x n.
+    """
+    if U is None and terms in ("both", "sox"):
+        U = thc_U(X, V)
+    out = np.zeros_like(G_tau)
+    for k in range(G_tau.shape[0]):
+        G = G_tau[k]
+        Gm = g_minus_tau(G_bmt[k])
+        if terms in ("both", "sox"):
+            out[k] += sigma_sox_thc(X, U, G, Gm)
+        if terms in ("both", "direct"):
+            out[k] += sigma_direct_thc(X, V, G, Gm)
+    return out
+
+
+def sigma_four_index(v: np.ndarray, G_tau: np.ndarray, G_bmt: np.ndarray, terms: str = "both") -> np.ndarray:
+    """Sigma at every tau from the four-index definitions."""
+    out = np.zeros_like(G_tau)
+    for k in range(G_tau.shape[0]):
+        G = G_tau[k]
+        Gm = g_minus_tau(G_bmt[k])
+        if terms in ("both", "sox"):
+            out[k] += sigma_sox_four_index(v, G, Gm)
+        if terms in ("both", "direct"):
+            out[k] += sigma_direct_four_index(v, G, Gm)
+    return out
+
+
+# ---------------------------------------------------------------- energy
+def energy_dyn_tau(G_bmt: np.ndarray, Sigma_tau: np.ndarray, weights: np.ndarray) -> float:
+    """Galitskii-Migdal dynamical energy on the tau axis (Eq. E2b).
+
+    (1/beta) sum_n Tr[G(iw_n) Sigma(iw_n)] = -int_0^beta Tr[G(beta - tau) Sigma(tau)] dtau,
+    evaluated with the quadrature weights of the tau grid.  Per spin, as
+    written in Eq. E2b for the restricted G: the spin sum and the 1/2 of the
+    Galitskii-Migdal formula cancel.
+    """
+    tr = np.array([np.trace(G_bmt[k] @ Sigma_tau[k]) for k in range(G_bmt.shape[0])])
+    return float(-np.dot(weights, tr))
+
+
+# ----------------------------------------------------- noninteracting G
+def fermi_pair(e: np.ndarray, beta: float) -> tuple[np.ndarray, np.ndarray]:
+    """(n, 1 - n) for occupation n = 1/(1 + e^{beta e}), both computed without cancellation."""
+    t = np.tanh(0.5 * beta * e)
+    return 0.5 * (1.0 - t), 0.5 * (1.0 + t)
+
+
+def g0_tau(F: np.ndarray, S: np.ndarray, mu: float, beta: float, tau: np.ndarray) -> np.ndarray:
+    """Noninteracting G(tau) from Dyson with Sigma = 0 (Sec. II.A).
+
+    G(iw) = [(iw + mu) S - F]^{-1}; with F C = S C diag(eps), C^T S C = I,
+    G(tau) = -C diag((1 - n_k) e^{-e'_k tau}) C^T, e' = eps - mu.  The factor
+    is written as exp(-e' tau) (1-n) for e' >= 0 and exp(e'(beta - tau)) n
+    for e' < 0, the two equal forms that never overflow.
+    """
+    import scipy.linalg
+
+    eps, C = scipy.linalg.eigh(F, S)
+    e = eps - mu
+    n_occ, n_vir = fermi_pair(e, beta)
+    out = np.empty((len(tau), F.shape[0], F.shape[0]))
+    pos = e >= 0.0
+    for k, t in enumerate(tau):
+        f = np.empty_like(e)
+        f[pos] = np.exp(-e[pos] * t) * n_vir[pos]
+        f[~pos] = np.exp(e[~pos] * (beta - t)) * n_occ[~pos]
+        out[k] = -(C * f[None, :]) @ C.T
+    return out
+
+
+# -------------------------------------------------------- closed forms
+def one_orbital_sigma(v: float, e: float, beta: float, tau: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """(Sigma^dir, Sigma^SOX) for a single orbital with (00|00) = v, e = eps - mu.
+
+    With G(tau) = -(1-n) e^{-e tau}, G(-tau) = n e^{e tau}, both terms are
+    v^2 G(tau)^2 G(-tau) times their factor: (1-n)^2 n e^{-e tau} v^2 times
+    C_DIRECT and C_SOX.
+    """
+    n_occ, n_vir = fermi_pair(np.array([e]), beta)
+    base = v * v * n_vir[0] ** 2 * n_occ[0] * np.exp(-e * tau)
+    return C_DIRECT * base, C_SOX * base
+
+
+def _pair_weight(e_in1, e_in2, e_out1, e_out2, beta):
+    """w = [n_in1 n_in2 nbar_out1 nbar_out2 - nbar_in1 nbar_in2 n_out1 n_out2] / Delta,
+    Delta = e_out1 + e_out2 - e_in1 - e_in2, with the Delta -> 0 limit
+    beta n_in1 n_in2 nbar_out1 nbar_out2.  Arguments broadcast."""
+    n1, nb1 = fermi_pair(e_in1, beta)
+    n2, nb2 = fermi_pair(e_in2, beta)
+    n3, nb3 = fermi_pair(e_out1, beta)
+    n4, nb4 = fermi_pair(e_out2, beta)
+    a = n1 * n2 * nb3 * nb4
+    b = nb1 * nb2 * n3 * n4
+    delta = e_out1 + e_out2 - e_in1 - e_in2
+    small = np.abs(delta) < 1e-12
+    safe = np.where(small, 1.0, delta)
+    return np.where(small, beta * a, (a - b) / safe)
+
+
+def mp2_finite_T(v_mo: np.ndarray, e: np.ndarray, beta: float) -> tuple[float, float]:
+    """(E^dir_dyn, E^SOX_dyn) of the GM energy at G0, closed form in the eigenbasis.
+
+    Derivation: with diagonal G0, -int_0^beta Tr[G(beta - tau) Sigma(tau)] reduces
+    to single exponentials in tau, integrated analytically:
+      E^dir = C_DIRECT * sum_{tuvw} (tu|vw)^2 w(t, w -> u, v)
+      E^SOX = C_SOX    * sum_{ptqv} (pt|qv)(tq|vp) w(t, v -> p, q)
+    where w(a, b -> c, d) is ``_pair_weight`` with Delta = e_c + e_d - e_a - e_b.
+    v_mo are the integrals in the orthonormal eigenbasis, e = eps - mu.
+    """
+    et = e[:, None, None, None]
+    eu = e[None, :, None, None]
+    ev = e[None, None, :, None]
+    ew = e[None, None, None, :]
+    # direct: indices (t,u,v,w), in = (t, w), out = (u, v)
+    w_dir = _pair_weight(et, ew, eu, ev, beta)
+    E_dir = C_DIRECT * float(np.sum(v_mo ** 2 * w_dir))
+    # exchange: indices (p,t,q,v) of (pt|qv); in = (t, v), out = (p, q)
+    ep = e[:, None, None, None]
+    et2 = e[None, :, None, None]
+    eq = e[None, None, :, None]
+    ev2 = e[None, None, None, :]
+    w_x = _pair_weight(et2, ev2, ep, eq, beta)
+    prod = v_mo * np.einsum("tqvp->ptqv", v_mo)  # (pt|qv) * (tq|vp)
+    E_x = C_SOX * float(np.sum(prod * w_x))
+    return E_dir, E_x
+
+
+def mp2_zero_T_closed_shell(v_mo: np.ndarray, eps: np.ndarray, n_occ: int) -> float:
+    """Textbook closed-shell MP2 energy
+    sum_{ijab} (ia|jb)[2(ia|jb) - (ib|ja)] / (e_i + e_j - e_a - e_b)."""
+    o = slice(0, n_occ)
+    vv = slice(n_occ, len(eps))
+    iajb = v_mo[o, vv, o, vv]
+    eo = eps[o]
+    ev = eps[vv]
+    denom = eo[:, None, None, None] + eo[None, None, :, None] - ev[None, :, None, None] - ev[None, None, None, :]
+    ibja = np.einsum("ibja->iajb", v_mo[o, vv, o, vv])
+    return float(np.sum(iajb * (2.0 * iajb - ibja) / denom))
+
+
+def mo_eri(v: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """Integrals in the basis of the columns of C: (ab|cd) = sum C_pa C_qb C_rc C_sd (pq|rs)."""
+    return np.einsum("pqrs,pa,qb,rc,sd->abcd", v, C, C, C, C, optimize=True)
+
+
+# ---------------------------------------------------------- tau quadrature
+def composite_gauss_legendre(beta: float, n_panels_per_side: int = 24, order: int = 24,
+                             smallest: float = 1e-6) -> tuple[np.ndarray, np.ndarray]:
+    """Mirror-symmetric composite Gauss-Legendre rule on (0, beta).
+
+    Panels are geometrically graded towards both ends, where G(tau) and
+    Sigma(tau) vary as e^{-|e| tau} on scales down to 1/|e|.
+    """
+    half = 0.5 * beta
+    edges = np.concatenate([[0.0], half * np.geomspace(smallest / half, 1.0, n_panels_per_side)])
+    x, w = np.polynomial.legendre.leggauss(order)
+    nodes = []
+    weights = []
+    for a, b in zip(edges[:-1], edges[1:]):
+        nodes.append(0.5 * (b - a) * x + 0.5 * (a + b))
+        weights.append(0.5 * (b - a) * w)
+    left = np.concatenate(nodes)
+    wl = np.concatenate(weights)
+    tau = np.concatenate([left, beta - left[::-1]])
+    wts = np.concatenate([wl, wl[::-1]])
+    return tau, wts

@@ -1,0 +1,228 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+* four-index definitions (brute force on tiny inputs, generic non-symmetric G)
+* the one-orbital closed form
+* the finite-temperature MP2 closed form of E_dyn[G0] (analytic tau integral)
+* the zero-temperature textbook closed-shell MP2 energy (E_dyn[G0] -> 2 E_MP2)
+* Sigma_ij = Sigma_ji, Sigma ~ lambda^2 under V -> lambda V, fragment separability
+  (appendix of arXiv:2404.17744), and G(0+) + G(beta-) = -S^{-1}
+Planted-mistake tests show that a sign or index error in the oracle fails a pin.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import thc_oracle as o
+from workloads import synth
+
+
+def _tiny(n, N, seed, n_tau=2, symmetric=False):
+    rng = synth.rng_for(seed)
+    X = synth.draw_X(n, N, rng)
+    V = synth.draw_V(N, rng)
+    if symmetric:
+        Gt = synth.random_symmetric(n_tau, n, rng)
+        Gb = synth.random_symmetric(n_tau, n, rng)
+    else:
+        Gt = rng.standard_normal((n_tau, n, n))
+        Gb = rng.standard_normal((n_tau, n, n))
+    return X, V, Gt, Gb
+
+
+@pytest.mark.parametrize("n,N,seed", [(3, 5, 1), (5, 9, 2), (6, 11, 3)])
+def test_sox_thc_equals_four_index(n, N, seed):
+    X, V, Gt, Gb = _tiny(n, N, seed)
+    v = o.eri_from_thc(X, V)
+    ref = o.sigma_four_index(v, Gt, Gb, "sox")
+    got = o.sigma_thc(X, V, Gt, Gb, terms="sox")
+    assert np.abs(ref).max() > 1e-3
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n,N,seed", [(3, 5, 4), (5, 9, 5), (6, 11, 6)])
+def test_direct_thc_equals_four_index(n, N, seed):
+    X, V, Gt, Gb = _tiny(n, N, seed)
+    v = o.eri_from_thc(X, V)
+    ref = o.sigma_four_index(v, Gt, Gb, "direct")
+    got = o.sigma_thc(X, V, Gt, Gb, terms="direct")
+    assert np.abs(ref).max() > 1e-3
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_eri_and_U_against_loops():
+    n, N = 3, 4
+    rng = synth.rng_for(7)
+    X = synth.draw_X(n, N, rng)
+    V = synth.draw_V(N, rng)
+    v = o.eri_from_thc(X, V)
+    U = o.thc_U(X, V)
+    for p in range(n):
+        for q in range(n):
+            for r in range(n):
+                for s in range(n):
+                    acc = 0.0
+                    for P in range(N):
+                        for Q in range(N):
+                            acc += X[p, P] * X[q, P] * V[P, Q] * X[r, Q] * X[s, Q]
+                    assert abs(acc - v[p, q, r, s]) < 1e-14
+    for P in range(N):
+        for q in range(n):
+            for s in range(n):
+                acc = sum(V[P, Q] * X[q, Q] * X[s, Q] for Q in range(N))
+                assert abs(acc - U[P, q, s]) < 1e-14
+    # (pq|rs) = sum_P X_pP X_qP U_Prs
+    np.testing.assert_allclose(np.einsum("pP,qP,Prs->pqrs", X, X, U), v, atol=1e-14)
+
+
+@pytest.mark.parametrize("e", [0.7, -0.4, 1e-9])
+def test_one_orbital_closed_form(e):
+    beta = 20.0
+    rng = synth.rng_for(8)
+    N = 3
+    X = rng.standard_normal((1, N))
+    V = synth.draw_V(N, rng)
+    vv = float(o.eri_from_thc(X, V)[0, 0, 0, 0])
+    tau = np.array([0.3, 2.0, 9.5, 17.0])
+    G = o.g0_tau(np.array([[e]]), np.eye(1), 0.0, beta, tau)
+    Gb = o.g0_tau(np.array([[e]]), np.eye(1), 0.0, beta, beta - tau)
+    d_ref, x_ref = o.one_orbital_sigma(vv, e, beta, tau)
+    d = o.sigma_thc(X, V, G, Gb, terms="direct")[:, 0, 0]
+    x = o.sigma_thc(X, V, G, Gb, terms="sox")[:, 0, 0]
+    np.testing.assert_allclose(d, d_ref, rtol=1e-10)
+    np.testing.assert_allclose(x, x_ref, rtol=1e-10)
+    # closed form stated directly: Sigma^x = v^2 (1-n)^2 n e^{-e tau}, n = 1/(1+e^{beta e})
+    nocc = 1.0 / (1.0 + np.exp(beta * e))
+    np.testing.assert_allclose(x, vv ** 2 * (1 - nocc) ** 2 * nocc * np.exp(-e * tau), rtol=1e-10)
+    np.testing.assert_allclose(d, -2 * x, rtol=1e-12)
+
+
+def _mp2_setup(beta, n=4, N=8, n_occ=2, seed=3, identity_S=False):
+    case = synth.make_sigma_case(n, N, 4, beta, seed, n_occ=n_occ, identity_S=identity_S)
+    tau, w = o.composite_gauss_legendre(beta)
+    G = o.g0_tau(case.F, case.S, 0.0, beta, tau)
+    Gb = G[::-1]
+    v = o.eri_from_thc(case.X, case.V)
+    eps, C = scipy.linalg.eigh(case.F, case.S)
+    vmo = o.mo_eri(v, C)
+    return case, tau, w, G, Gb, v, eps, vmo
+
+
+@pytest.mark.parametrize("beta", [5.0, 20.0])
+def test_energy_matches_finite_T_closed_form(beta):
+    case, tau, w, G, Gb, v, eps, vmo = _mp2_setup(beta)
+    Sd = o.sigma_four_index(v, G, Gb, "direct")
+    Sx = o.sigma_four_index(v, G, Gb, "sox")
+    Ed = o.energy_dyn_tau(Gb, Sd, w)
+    Ex = o.energy_dyn_tau(Gb, Sx, w)
+    cd, cx = o.mp2_finite_T(vmo, eps, beta)
+    assert abs(Ed - cd) < 1e-12 * abs(cd)
+    assert abs(Ex - cx) < 1e-12 * abs(cx)
+    assert Ed < 0 < Ex
+
+
+def test_energy_zero_temperature_is_twice_textbook_mp2():
+    beta = 400.0
+    case, tau, w, G, Gb, v, eps, vmo = _mp2_setup(beta)
+    S = o.sigma_thc(case.X, case.V, G, Gb)
+    E = o.energy_dyn_tau(Gb, S, w)
+    emp2 = o.mp2_zero_T_closed_shell(vmo, eps, 2)
+    assert abs(E - 2 * emp2) < 1e-12 * abs(emp2)
+
+
+def test_symmetry_and_V_scaling():
+    case = synth.make_sigma_case(6, 14, 6, 30.0, 11)
+    S1 = o.sigma_thc(case.X, case.V, case.G_tau, case.G_bmt)
+    np.testing.assert_allclose(S1, np.swapaxes(S1, 1, 2), atol=1e-15 * np.abs(S1).max())
+    S2 = o.sigma_thc(case.X, 1.7 * case.V, case.G_tau, case.G_bmt)
+    np.testing.assert_allclose(S2, 1.7 ** 2 * S1, rtol=1e-12, atol=1e-15)
+
+
+def test_fragment_separability():
+    """Two non-interacting fragments (appendix): block-diagonal Sigma, additive E_dyn."""
+    beta = 15.0
+    a = synth.make_sigma_case(3, 5, 8, beta, 21, n_occ=1)
+    b = synth.make_sigma_case(4, 7, 8, beta, 22, n_occ=2)
+    X = scipy.linalg.block_diag(a.X, b.X)
+    V = scipy.linalg.block_diag(a.V, b.V)
+    F = scipy.linalg.block_diag(a.F, b.F)
+    tau, w = o.composite_gauss_legendre(beta, n_panels_per_side=12, order=16)
+    G = o.g0_tau(F, np.eye(7), 0.0, beta, tau)
+    Gb = G[::-1]
+    S = o.sigma_thc(X, V, G, Gb)
+    assert np.abs(S[:, :3, 3:]).max() < 1e-15
+    Ga = o.g0_tau(a.F, np.eye(3), 0.0, beta, tau)
+    Gbb = o.g0_tau(b.F, np.eye(4), 0.0, beta, tau)
+    Sa = o.sigma_thc(a.X, a.V, Ga, Ga[::-1])
+    Sb = o.sigma_thc(b.X, b.V, Gbb, Gbb[::-1])
+    np.testing.assert_allclose(S[:, :3, :3], Sa, atol=1e-14)
+    np.testing.assert_allclose(S[:, 3:, 3:], Sb, atol=1e-14)
+    E = o.energy_dyn_tau(Gb, S, w)
+    Ea = o.energy_dyn_tau(Ga[::-1], Sa, w)
+    Eb = o.energy_dyn_tau(Gbb[::-1], Sb, w)
+    assert abs(E - (Ea + Eb)) < 1e-13
+
+
+def test_g0_boundary_identity_and_generator_agreement():
+    case = synth.make_sigma_case(7, 10, 6, 50.0, 31, identity_S=False, n_occ=3)
+    G = o.g0_tau(case.F, case.S, 0.0, case.beta, np.array([0.0, case.beta]))
+    np.testing.assert_allclose(G[0] + G[1], -np.linalg.inv(case.S), atol=1e-13)
+    # particle number per spin: gamma = -G(beta^-), Tr[gamma S] = sum_k 1/(1 + e^{beta eps_k})
+    n_exact = np.sum(1.0 / (1.0 + np.exp(case.beta * case.eps)))
+    assert abs(np.trace(-G[1] @ case.S) - n_exact) < 1e-12
+    assert abs(n_exact - 3.0) < 1e-2
+    G_or = o.g0_tau(case.F, case.S, 0.0, case.beta, case.tau)
+    np.testing.assert_allclose(G_or, case.G_tau, atol=1e-13)
+
+
+# ------------------------------------------------------------ planted mistakes
+def test_planted_sign_mistake_fails_mp2_pin(monkeypatch):
+    monkeypatch.setattr(o, "C_SOX", -1.0)
+    beta = 400.0
+    case, tau, w, G, Gb, v, eps, vmo = _mp2_setup(beta)
+    E = o.energy_dyn_tau(Gb, o.sigma_thc(case.X, case.V, G, Gb), w)
+    emp2 = o.mp2_zero_T_closed_shell(vmo, eps, 2)
+    assert abs(E - 2 * emp2) > 1e-3 * abs(emp2)
+
+
+def test_planted_index_mistake_fails_four_index_pin(monkeypatch):
+    X, V, Gt, Gb = _tiny(5, 9, 2)
+    v = o.eri_from_thc(X, V)
+    ref = o.sigma_four_index(v, Gt, Gb, "sox")
+    real = o.sigma_sox_thc
+
+    def wrong(X, U, G, Gm, return_intermediates=False):
+        return real(X, U, G.T, Gm)          # G_Rq built from G^T: a transposed operand
+
+    monkeypatch.setattr(o, "sigma_sox_thc", wrong)
+    got = o.sigma_thc(X, V, Gt, Gb, terms="sox")
+    assert np.abs(got - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_planted_dropped_term_fails_closed_form(monkeypatch):
+    """Dropping the polarisation's G(-tau) factor (a lost term) breaks the MP2 pin."""
+    def wrong(X, V, G, Gm):
+        GX = X.T @ G @ X
+        W = V @ GX @ V
+        return o.C_DIRECT * (X @ (GX * W) @ X.T)
+
+    monkeypatch.setattr(o, "sigma_direct_thc", wrong)
+    beta = 20.0
+    case, tau, w, G, Gb, v, eps, vmo = _mp2_setup(beta)
+    Ed = o.energy_dyn_tau(Gb, o.sigma_thc(case.X, case.V, G, Gb, terms="direct"), w)
+    cd, _ = o.mp2_finite_T(vmo, eps, beta)
+    assert abs(Ed - cd) > 1e-3 * abs(cd)
+
+
+def test_golden_thc20_regression():
+    """The oracle reproduces the stored thc20 values (written by tests/golden/make_golden.py)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "thc20_oracle.json")
+    g = json.load(open(path))
+    case = synth.make_workload("thc20")
+    Sd = o.sigma_thc(case.X, case.V, case.G_tau, case.G_bmt, terms="direct")
+    Sx = o.sigma_thc(case.X, case.V, case.G_tau, case.G_bmt, terms="sox")
+    assert abs(o.energy_dyn_tau(case.G_bmt, Sd, case.tau_w) - g["E_dyn_direct"]) < 1e-13
+    assert abs(o.energy_dyn_tau(case.G_bmt, Sx, case.tau_w) - g["E_dyn_sox"]) < 1e-13
+    for k, i, j, d, x in g["samples"]:
+        assert abs(Sd[k, i, j] - d) < 1e-14 and abs(Sx[k, i, j] - x) < 1e-14
