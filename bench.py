@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark of the THC second-order self-energy on GB300.
+
+One step = one thc_sigma_eval over every tau point (direct + SOX: the
+projections, A, B, fused C/D, polarisation, V Pi V, merge, back-transform)
+followed by thc_energy, on the 200-AO workload (n_ao=200, n_thc=1000,
+n_tau=100, beta=100, non-orthogonal S, 40 occupied levels).  U_Pqs is built
+once in thc_sigma_init, outside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the path has no exchange step), the timed region is bracketed by
+barriers, and the MAX time over ranks is used.  --impl reference times the
+FP64 CPU oracle on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "THC Σ(τ) TFLOP/s & s/scGF2 iteration, % tensor peak; mixed+learned vs FP64"
+UNIT = "TFLOP/s"
+# FP64 peak of the GB300: nominal 1.25 TFLOP/s = 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="thc200")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def algorithmic_flops(n, N, n_tau):
+    """Flops of one Sigma evaluation (both terms), 2 per multiply-add."""
+    return n_tau * (2 * N * n ** 3 + 4 * N ** 2 * n ** 2 + 4 * N ** 3 + 8 * N ** 2 * n + 6 * N * n ** 2)
+
+
+def workload_desc(case, name):
+    return (f"{name}: n_ao={case.n}, n_thc={case.N}, n_tau={case.n_tau} (Gauss-Legendre, mirror-symmetric), "
+            f"beta={case.beta:g}, G = noninteracting G(tau) of a seeded (F, S)")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(case, seconds_target=15.0, max_points=None):
+    """Times the FP64 CPU oracle on a bounded sample of tau points of the workload.
+
+    Returns (TFLOP/s, points timed, seconds).  U_Pqs is built outside the timing,
+    as in the GPU step; each timed point is one full Sigma(tau_k) (SOX + direct).
+    """
+    from oracle import thc_oracle as o
+    U = o.thc_U(case.X, case.V)
+    per_point = algorithmic_flops(case.n, case.N, 1)
+    done, elapsed = 0, 0.0
+    limit = max_points or case.n_tau
+    k = 0
+    while done < limit and (elapsed < seconds_target or done == 0):
+        G = case.G_tau[k % case.n_tau]
+        Gm = o.g_minus_tau(case.G_bmt[k % case.n_tau])
+        t0 = time.perf_counter()
+        o.sigma_sox_thc(case.X, U, G, Gm)
+        o.sigma_direct_thc(case.X, case.V, G, Gm)
+        elapsed += time.perf_counter() - t0
+        done += 1
+        k += 1
+    return per_point * done / elapsed / 1e12, done, elapsed
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from workloads import synth
+    case = synth.make_workload(args.workload)
+    cores = len(os.sched_getaffinity(0))
+    from oracle import thc_oracle as o
+    U = o.thc_U(case.X, case.V)
+    per_point = algorithmic_flops(case.n, case.N, 1)
+
+    def step(k):
+        G = case.G_tau[k % case.n_tau]
+        Gm = o.g_minus_tau(case.G_bmt[k % case.n_tau])
+        o.sigma_sox_thc(case.X, U, G, Gm)
+        o.sigma_direct_thc(case.X, case.V, G, Gm)
+
+    for w in range(args.warmup):
+        step(w)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        step(args.warmup + s)
+    dt = time.perf_counter() - t0
+    value = per_point * args.steps / dt / 1e12
+    sample = f"one tau point of the workload (full Sigma(tau_k): SOX + direct) per step, U built outside the timing"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(case, args.workload), "precision": "fp64", "terms": "direct+sox",
+                   "parallelism": "host cores (numpy/BLAS threads)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+    from paper_2404_17744_gb300 import thc
+    from workloads import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    case = synth.make_workload(args.workload)
+    stream = torch.cuda.Stream(device=dev)
+    flops_step = algorithmic_flops(case.n, case.N, case.n_tau)
+    with torch.cuda.stream(stream):
+        X = torch.from_numpy(case.X).to(dev)
+        V = torch.from_numpy(case.V).to(dev)
+        G = torch.from_numpy(case.G_tau).to(dev)
+        S = torch.empty_like(G)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+        stream.synchronize()
+        ctx = thc.thc_sigma_init(case.n, case.N, case.n_tau, case.beta, X, V, case.tau, thc.THC_FP64,
+                                 thc.THC_DIRECT | thc.THC_SOX, stream.cuda_stream)
+        lib_flops, u_flops = thc.thc_sigma_flops(ctx)
+        assert abs(lib_flops - flops_step) < 1e-6 * flops_step
+        energies = []
+
+        def step():
+            thc.thc_sigma_eval(ctx, G, None, S)
+            energies.append(thc.thc_energy(ctx, G, None, S, case.tau_w))
+
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+        thc.thc_profile(ctx, True)
+        launches0 = thc.thc_launch_count(ctx)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for e0, e1 in evs:
+            flush.zero_()                 # L2 flush between timed steps (2x L2 written)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        launches = thc.thc_launch_count(ctx) - launches0
+        clocks = sampler.stop() if sampler else None
+        ms_steps = [e0.elapsed_time(e1) for e0, e1 in evs]
+        kernels = {}
+        k = 0
+        while True:
+            r = thc.thc_profile_get(ctx, k)
+            if r is None:
+                break
+            name, nl, ms, fl = r
+            if nl:
+                kernels[name] = {"launches": nl, "ms": ms, "tflops": (fl / ms / 1e9) if ms > 0 and fl > 0 else None}
+            k += 1
+        thc.thc_profile(ctx, False)
+        total_ms = float(sum(ms_steps))
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        value = world * flops_step * args.steps / (total_ms * 1e-3) / 1e12
+
+        # end to end through the host-buffer entry point (H2D of G, D2H of Sigma inside)
+        Gh = torch.from_numpy(case.G_tau).pin_memory()
+        Sh = torch.empty_like(Gh).pin_memory()
+        thc.thc_sigma_eval_host(ctx, Gh, None, Sh)
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 2))
+        for _ in range(e2e_steps):
+            thc.thc_sigma_eval_host(ctx, Gh, None, Sh)
+        e2e_dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_dt = float(t.item())
+        e2e_value = world * flops_step * e2e_steps / e2e_dt / 1e12
+        thc.thc_destroy(ctx)
+
+    if rank != 0:
+        return 0
+    dom = max(kernels.items(), key=lambda kv: kv[1]["ms"] if kv[1]["tflops"] else -1)
+    dom_name, dom_stat = dom
+    per_launch_flops = dom_stat["tflops"] * 1e12 * (dom_stat["ms"] / dom_stat["launches"]) * 1e-3
+    roofline = {
+        "kernel": dom_name, "bound": "alu", "achieved": dom_stat["tflops"], "peak": FP64_PEAK_TFLOPS,
+        "unit": "TFLOP/s", "frac": dom_stat["tflops"] / FP64_PEAK_TFLOPS,
+        "peak_source": "FP64 DFMA nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no measured FP64 peak in "
+                       "MEASURED_PEAKS.json)",
+        "flops_per_launch": per_launch_flops, "ms_per_launch": dom_stat["ms"] / dom_stat["launches"],
+        "traffic": None,
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(case, args.workload), "precision": "fp64", "terms": "direct+sox",
+                   "step": "thc_sigma_eval over all tau + thc_energy", "s_per_sigma_eval": total_ms / args.steps / 1e3,
+                   "fp64_frac_of_peak": value / world / FP64_PEAK_TFLOPS,
+                   "l2": "flushed between timed steps (258 MiB write); U_Pqs (320 MB) exceeds L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "E_dyn": energies[-1] if energies else None},
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Gh.numel() * 8),
+                "d2h_bytes_per_step": int(Sh.numel() * 8), "entry": "thc_sigma_eval_host (pinned host buffers)"},
+        "clocks": clocks,
+        "kernels": kernels,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, pts, secs = oracle_sample(case)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                                "sample": f"{pts} tau points of the workload (full Sigma(tau_k) each), "
+                                          f"{secs:.1f} s, U built outside the timing"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

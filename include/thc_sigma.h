@@ -1,0 +1,169 @@
+/*
+ * thc_sigma.h -- C ABI of the GB300 THC second-order self-energy library.
+ *
+ * The library evaluates the second-order self-energy of fully
+ * self-consistent imaginary-time GF2 with tensor-hypercontracted (THC)
+ * two-electron integrals (Pokhilko, Yeh, Morales, Zgid, arXiv:2404.17744):
+ *
+ *   Sigma(tau) = Sigma^dir(tau) + Sigma^SOX(tau)   at every tau point,
+ *
+ * with (pq|rs) = sum_PQ X_pP X_qP V_PQ X_rQ X_sQ (Eq. THC_ERI, the paper's
+ * core matrix U_PQ is called V here).  SOX follows the paper's contraction
+ * order (Sec. II.C): U_Pqs = sum_Q V_PQ X_qQ X_sQ built once, then per tau
+ * the projections G_Rq, G_wP, the intermediates A_Pqv, B_PRv, C_RvP, D_PR
+ * and the back-transform to Sigma_tr.  The direct term is the THC-GW form
+ * of the second-order bubble (Sec. II.C, first paragraph):
+ *   Pi = G^X(tau) o G^X(-tau),  W = V Pi V,  Sigma^dir = -2 X (G^X(tau) o W) X^T,
+ * with G^X = X^T G X and o the elementwise product.
+ *
+ * Conventions shared by every entry point
+ *   - All matrices are real, FP64, row-major.  G(tau) and Sigma(tau) are per
+ *     spin (closed-shell restricted), symmetric n x n; the result for a
+ *     non-symmetric G is unspecified.
+ *   - G_pq(tau) = -<T p(tau) q^+> (Sec. II.A, Eq. G_def).  For 0 < tau < beta
+ *     the library forms G(-tau) = -G(beta - tau).
+ *   - Sign reading: the SOX term enters with +1 on G(-tau) (the paper prints
+ *     -1, which matches if its "G(-tau)" denotes G(beta - tau)); the direct
+ *     term carries -2 (closed spin loop).
+ *   - "dev" pointers are CUDA device pointers owned by the caller; "host"
+ *     pointers are ordinary host memory owned by the caller.  Everything the
+ *     library allocates (U_Pqs, workspaces, copies of X and V) belongs to
+ *     the context and is released by thc_destroy.
+ *   - Calls are ordered on the context's stream and return before the GPU
+ *     work finishes, except thc_energy and thc_sigma_eval_host, which
+ *     synchronise the stream.
+ *   - Return value: THC_OK (0) or a negative THC_E* code.  Nothing aborts,
+ *     and no C++ exception crosses the ABI.  thc_last_error(ctx) describes
+ *     the last failure on ctx (thc_last_error(NULL): the last failure of a
+ *     thc_sigma_init on the calling thread).
+ */
+#ifndef THC_SIGMA_H
+#define THC_SIGMA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define THC_OK        0
+#define THC_EINVAL   -1   /* bad sizes, NULL pointers, non-mirrored grid without G_bmt */
+#define THC_ENOMEM   -2   /* device allocation failed */
+#define THC_ECUDA    -3   /* a CUDA runtime call or kernel launch failed */
+#define THC_ETIMEOUT -4   /* a bounded device-side wait ran out */
+#define THC_ENOTSUP  -5   /* option not available in this build */
+
+/* precision of the contractions */
+#define THC_FP64     0    /* every step in FP64 (DFMA) */
+#define THC_BF16X3   1    /* projections and V contractions as 3 BF16 products
+                             (hi*hi + hi*lo + lo*hi) on tcgen05 tensor cores with
+                             FP32 accumulation; inputs and outputs stay FP64 */
+
+/* terms (bit mask) */
+#define THC_DIRECT   1
+#define THC_SOX      2
+
+typedef struct thc_ctx thc_ctx;   /* opaque, library-owned */
+
+/*
+ * thc_sigma_init -- set up a context and build U_Pqs = sum_Q V_PQ X_qQ X_sQ
+ * (Eq. U_contraction, Sec. II.C: G-independent, built once, reused every
+ * iteration).
+ *   ctx       out: new context (NULL on failure)
+ *   n_ao      n, number of atomic orbitals (>= 1)
+ *   n_thc     N, number of THC interpolation points (>= 1)
+ *   n_tau     number of imaginary-time points (>= 1)
+ *   beta      inverse temperature (> 0)
+ *   X         dev, n x N row-major collocation matrix X_iP (copied)
+ *   V         dev, N x N row-major symmetric THC core (copied)
+ *   tau       host, n_tau ascending points in (0, beta) (copied); if the grid
+ *             is mirror-symmetric (|tau_k + tau_{n_tau-1-k} - beta| <= 1e-10 beta
+ *             for all k) G(beta - tau_k) is read from G_tau itself
+ *   precision THC_FP64 or THC_BF16X3
+ *   terms     THC_DIRECT | THC_SOX (non-zero)
+ *   stream    cudaStream_t the context launches on (NULL: legacy default stream)
+ * Device memory held: U (N n^2 doubles) plus a workspace sized at init from
+ * the free device memory (at most a quarter of it, or THC_WORKSPACE_BYTES
+ * from the environment when set).
+ */
+int thc_sigma_init(thc_ctx **ctx, int n_ao, int n_thc, int n_tau, double beta,
+                   const double *X, const double *V, const double *tau,
+                   int precision, int terms, void *stream);
+
+/*
+ * thc_sigma_eval -- Sigma(tau_k) for every k (Sec. II.C scheme + direct term).
+ *   G_tau      dev, n_tau x n x n, G(tau_k)
+ *   G_bmt      dev, n_tau x n x n, G(beta - tau_k); NULL when the grid is
+ *              mirror-symmetric (then G(beta - tau_k) = G_tau[n_tau-1-k])
+ *   Sigma_tau  dev, n_tau x n x n, overwritten with Sigma(tau_k); must not
+ *              alias G_tau or G_bmt
+ * THC_EINVAL if G_bmt is NULL and the grid is not mirror-symmetric.
+ */
+int thc_sigma_eval(thc_ctx *ctx, const double *G_tau, const double *G_bmt, double *Sigma_tau);
+
+/*
+ * thc_sigma_eval_host -- thc_sigma_eval with host buffers: copies G in,
+ * evaluates, copies Sigma out and synchronises.  The device staging buffers
+ * are allocated on first use and kept by the context.  Pinned host memory
+ * gives the fastest copies.  Arguments as for thc_sigma_eval, host pointers.
+ */
+int thc_sigma_eval_host(thc_ctx *ctx, const double *G_tau, const double *G_bmt, double *Sigma_tau);
+
+/*
+ * thc_energy -- Galitskii-Migdal dynamical energy on the tau axis (Eq. E2b):
+ *   E_dyn = (1/beta) sum_n Tr[G(iw_n) Sigma(iw_n)]
+ *         = -int_0^beta Tr[G(beta - tau) Sigma(tau)] dtau
+ *        ~= -sum_k w_k Tr[G(beta - tau_k) Sigma(tau_k)],
+ * per spin as written for the restricted G (spin sum and 1/2 cancel).
+ *   G_tau, G_bmt  dev, as for thc_sigma_eval (G_bmt may be NULL on a mirrored grid)
+ *   Sigma_tau     dev, n_tau x n x n
+ *   tau_weights   host, n_tau quadrature weights of the tau grid
+ *   E_dyn         host out
+ * Reduction in FP64, fixed order (deterministic).  Synchronises the stream.
+ */
+int thc_energy(thc_ctx *ctx, const double *G_tau, const double *G_bmt,
+               const double *Sigma_tau, const double *tau_weights, double *E_dyn);
+
+/* thc_set_stream -- launch subsequent work of ctx on stream (cudaStream_t). */
+int thc_set_stream(thc_ctx *ctx, void *stream);
+
+/*
+ * thc_sigma_flops -- algorithmic FP64-equivalent flop count of one
+ * thc_sigma_eval on ctx (contractions of the scheme only, 2 per multiply-add):
+ *   n_tau (2 N n^3 + 4 N^2 n^2 + 4 N^3 + 8 N^2 n + 6 N n^2)  for both terms;
+ * and of the one-off U build, 2 N^2 n^2 (returned through u_flops if non-NULL).
+ */
+double thc_sigma_flops(const thc_ctx *ctx, double *u_flops);
+
+/*
+ * thc_profile -- enable (1: clear counters and start) or stop (0) timing of
+ * every kernel launch of ctx with CUDA events recorded on ctx's stream.
+ * Timing adds two event records per launch; results are read with
+ * thc_profile_get.  Synchronises the stream when pending events exist.
+ */
+int thc_profile(thc_ctx *ctx, int enable);
+
+/*
+ * thc_profile_get -- totals of kernel class kclass (0 <= kclass < number of
+ * classes; THC_EINVAL past the last) since the last thc_profile(ctx, 1):
+ * its name, number of launches, summed device time in ms and summed
+ * algorithmic flops of those launches.  Any out-pointer may be NULL.
+ * Synchronises the stream.  Class names: u_build, project, sox_A, sox_B,
+ * sox_CD, polarisation, direct_VPi, direct_W, back_transform, energy, split.
+ */
+int thc_profile_get(thc_ctx *ctx, int kclass, const char **name, long long *launches,
+                    double *ms, double *flops);
+
+/* thc_launch_count -- kernels launched by ctx since init (always counted). */
+long long thc_launch_count(const thc_ctx *ctx);
+
+/* thc_destroy -- free everything ctx owns (NULL is a no-op).  Synchronises. */
+void thc_destroy(thc_ctx *ctx);
+
+/* thc_last_error -- text of the last failure on ctx, or of the last failed
+ * init on this thread when ctx is NULL.  Never NULL; "" when none. */
+const char *thc_last_error(const thc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* THC_SIGMA_H */

@@ -1,0 +1,282 @@
+// FP64 evaluation of the THC second-order self-energy (Sec. II.C of
+// arXiv:2404.17744): U build, per-tau SOX scheme, direct term, back-transform
+// and the Galitskii-Migdal energy.  Every contraction runs in the DFMA tile
+// of dfma_tile.cuh; see that file for why FP64 work is DFMA-bound on GB300.
+#include <algorithm>
+#include <cstdio>
+
+#include "dfma_tile.cuh"
+#include "thc_internal.cuh"
+
+namespace thc {
+namespace {
+
+using f64::BM;
+using f64::BN;
+using f64::NT;
+using f64::View;
+
+constexpr double C_DIRECT = -2.0;  // closed spin loop of the bubble
+constexpr double C_SOX = +1.0;     // sign reading of the SOX term on G(-tau)
+
+inline dim3 grid_for(long long M, long long Nn, long long batch) {
+  return dim3((unsigned)((M + BM - 1) / BM), (unsigned)((Nn + BN - 1) / BN), (unsigned)batch);
+}
+
+// One batched contraction; the profiler attributes 2 M Nn K batch flops to kclass.
+template <bool AK, bool BK_, class LA, class LB, class Epi>
+int launch_gemm(thc_ctx* ctx, int kclass, long long M, long long Nn, long long K, long long batch, const LA& a,
+                const LB& b, const Epi& e, const char* what) {
+  if (M <= 0 || Nn <= 0 || batch <= 0) return THC_OK;
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, kclass, 2.0 * M * Nn * K * batch, &rec));
+  f64::gemm_kernel<AK, BK_><<<grid_for(M, Nn, batch), NT, 0, ctx->stream>>>(M, Nn, K, a, b, e);
+  return prof_end(ctx, &rec, cudaGetLastError(), what);
+}
+
+// ------------------------------------------------------------------ kernels
+
+// Fused C and D steps of the SOX scheme for one tau and one block of P:
+//   C_RvP = sum_w U_Rvw G_wP          (G_wP = sum_p G_wp X_pP = Y_Pw for symmetric G)
+//   D_PR  = sum_v C_RvP B_PRv
+// CTA (x, y) owns R = y and 64 consecutive P of the block; it walks all v
+// tiles, multiplies each C tile by the matching B entries and reduces over v
+// in registers, so C is never stored.  Deterministic: no atomics.
+__global__ void __launch_bounds__(NT) sox_cd_kernel(int n, int N, int P0, int Pcnt, const double* __restrict__ U,
+                                                     const double* __restrict__ Y, const double* __restrict__ Bblk,
+                                                     double* __restrict__ D) {
+  __shared__ __align__(16) f64::Tiles T;
+  __shared__ double red[4][BN];
+  const long long R = blockIdx.y;
+  const long long p0 = (long long)blockIdx.x * BN;  // local P offset in the block
+  const f64::Lane L;
+  // A(m = v, k = w) = U[R, v, w];  B(k = w, c = p) = Y[P0 + p, w]
+  const View a{U + R * n * (long long)n, 0, n, 1};
+  const View b{Y + (long long)P0 * n, 0, 1, n};
+  double part[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long v0 = 0; v0 < n; v0 += BM) {
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    f64::mainloop<true, true>(T, a, b, 0, v0, p0, n, Pcnt, n, L, acc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long v = v0 + L.rm + i;
+      if (v >= n) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const long long p = p0 + L.rn + j;
+        if (p < Pcnt) part[j] = fma(acc[i][j], Bblk[(p * N + R) * n + v], part[j]);
+      }
+    }
+  }
+  // reduce over the 4 lanes along m (lane bits 3, 4), then over the 4 warps along m
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    part[j] += __shfl_xor_sync(0xffffffffu, part[j], 8);
+    part[j] += __shfl_xor_sync(0xffffffffu, part[j], 16);
+  }
+  if (L.lm == 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) red[L.wm][L.rn + j] = part[j];
+  }
+  __syncthreads();
+  if (threadIdx.x < BN) {
+    const long long p = p0 + threadIdx.x;
+    if (p < Pcnt) {
+      const double s = (red[0][threadIdx.x] + red[1][threadIdx.x]) + (red[2][threadIdx.x] + red[3][threadIdx.x]);
+      D[((long long)P0 + p) * N + R] = s;
+    }
+  }
+}
+
+// Pi = G^X(tau) o G^X(-tau)^T for a batch of tau points (Pi_QS = G^X_QS(tau) G^X_SQ(-tau)).
+__global__ void polarisation_kernel(long long N, long long batch, const double* __restrict__ GXp,
+                                    const double* __restrict__ GXm, double* __restrict__ Pi) {
+  const long long NN = N * N;
+  const long long total = NN * batch;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long b = idx / NN, r = idx - b * NN;
+    const long long i = r / N, j = r - i * N;
+    Pi[idx] = GXp[idx] * GXm[b * NN + j * N + i];
+  }
+}
+
+// Epilogue of W = (V Pi) V: merged THC-space self-energy
+//   M_RP = C_SOX * D_PR + C_DIRECT * G^X_RP(tau) W_RP
+struct MergeEpi {
+  double* M;
+  const double* D;    // may be null (direct term only)
+  const double* GXp;
+  long long N;
+  __device__ __forceinline__ void operator()(long long b, long long r, long long p, double w) const {
+    const long long o = b * N * N;
+    double m = C_DIRECT * GXp[o + r * N + p] * w;
+    if (D) m = fma(C_SOX, D[o + p * N + r], m);
+    M[o + r * N + p] = m;
+  }
+};
+
+// Partial traces t_k = sum_ij Gb_k[i, j] S_k[j, i], one CTA per tau point.
+__global__ void trace_kernel(int n, const double* __restrict__ Gb0, long long sGb, const double* __restrict__ S,
+                             double* __restrict__ part) {
+  const long long k = blockIdx.x;
+  const double* g = Gb0 + k * sGb;
+  const double* s = S + k * (long long)n * n;
+  double acc = 0.0;
+  const long long nn = (long long)n * n;
+  for (long long idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const long long i = idx / n, j = idx - i * n;
+    acc = fma(g[idx], s[j * n + i], acc);
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) part[k] = v;
+  }
+}
+
+// E = -sum_k w_k t_k in a fixed order (one warp).
+__global__ void energy_sum_kernel(int n_tau, const double* __restrict__ part, const double* __restrict__ w,
+                                  double* __restrict__ out) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n_tau; k += 32) acc = fma(w[k], part[k], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x == 0) out[0] = -acc;
+}
+
+}  // namespace
+
+size_t fp64_workspace_bytes(int n, int N, int tc, int Pb) {
+  const size_t d = sizeof(double);
+  const size_t NN = (size_t)N * N, Nn = (size_t)N * n;
+  return d * ((size_t)tc * (2 * Nn + 4 * NN + Nn) + (size_t)Pb * ((size_t)n * n + Nn));
+}
+
+// U_Pqs = sum_Q V_PQ X_qQ X_sQ (Eq. U_contraction), the Khatri-Rao operand generated in the loader.
+int fp64_build_U(thc_ctx* ctx) {
+  const long long n = ctx->n, N = ctx->N;
+  const View a{ctx->V, 0, N, 1};                 // A(m = P, k = Q) = V[P, Q]
+  const f64::KhatriRao b{ctx->X, ctx->n, ctx->N};  // B(k = Q, c = q n + s)
+  const f64::StoreEpi e{ctx->U, 0, n * n, 1, 1.0};
+  return launch_gemm<true, true>(ctx, K_UBUILD, N, n * n, N, 1, a, b, e, "U build");
+}
+
+int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
+  const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau;
+  const long long nn = n * n, NN = N * N, Nn = N * n;
+  const bool sox = ctx->terms & THC_SOX, dir = ctx->terms & THC_DIRECT;
+  for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
+    const long long tc = std::min<long long>(ctx->tc, nt - c0);
+    // G(tau_k) and G(beta - tau_k) views for this chunk
+    const View g{G_tau + c0 * nn, nn, n, 1};
+    View gb;
+    if (G_bmt)
+      gb = View{G_bmt + c0 * nn, nn, n, 1};
+    else
+      gb = View{G_tau + (nt - 1 - c0) * nn, -nn, n, 1};
+    // Y_Rq = sum_u X_uR G_uq(tau): computed as (m = q, c = R), A(q, u) = G[u, q], B(u, R) = X[u, R]
+    {
+      const View a{g.p, g.sb, 1, n};
+      const View b{ctx->X, 0, N, 1};
+      THC_TRY(launch_gemm<false, false>(ctx, K_PROJECT, n, N, n, tc, a, b, f64::StoreEpi{ctx->Y, Nn, 1, n, 1.0}, "Y"));
+      if (dir) {
+        // Ym = X^T G(-tau) = -X^T G(beta - tau)
+        const View am{gb.p, gb.sb, 1, n};
+        THC_TRY(launch_gemm<false, false>(ctx, K_PROJECT, n, N, n, tc, am, b, f64::StoreEpi{ctx->Ym, Nn, 1, n, -1.0}, "Ym"));
+      }
+    }
+    if (dir) {
+      // G^X(+-tau) = Y(+-) X : (m = P, c = R), A(P, q) = Y[P, q], B(q, R) = X[q, R]
+      const View b{ctx->X, 0, N, 1};
+      THC_TRY(launch_gemm<true, false>(ctx, K_PROJECT, N, N, n, tc, View{ctx->Y, Nn, n, 1}, b,
+                                       f64::StoreEpi{ctx->GXp, NN, N, 1, 1.0}, "GX+"));
+      THC_TRY(launch_gemm<true, false>(ctx, K_PROJECT, N, N, n, tc, View{ctx->Ym, Nn, n, 1}, b,
+                                       f64::StoreEpi{ctx->GXm, NN, N, 1, 1.0}, "GX-"));
+      const long long total = NN * tc;
+      const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+      ProfRec rec;
+      THC_TRY(prof_begin(ctx, K_POLARISATION, 0.0, &rec));
+      polarisation_kernel<<<blocks, 256, 0, ctx->stream>>>(N, tc, ctx->GXp, ctx->GXm, ctx->Pi);
+      THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "polarisation"));
+    }
+    if (sox) {
+      for (long long k = 0; k < tc; ++k) {
+        const double* Gb = gb.p + k * gb.sb;  // G(beta - tau_k)
+        const double* Yk = ctx->Y + k * Nn;
+        double* Dk = ctx->D + k * NN;
+        for (long long P0 = 0; P0 < N; P0 += ctx->Pb) {
+          const long long Pc = std::min<long long>(ctx->Pb, N - P0);
+          // A_Pqv = sum_s U_Pqs G_sv(-tau) = -sum_s U_Pqs G_sv(beta - tau):
+          // (m = v, c = (P, q)), A(v, s) = Gb[s, v], B(s, (P, q)) = U[P0 + P, q, s]
+          THC_TRY(launch_gemm<false, true>(ctx, K_SOX_A, n, Pc * n, n, 1, View{Gb, 0, 1, n},
+                                           View{ctx->U + P0 * nn, 0, 1, n},
+                                           f64::StoreEpi{ctx->Ablk, 0, 1, n, -1.0}, "A"));
+          // B_PRv = sum_q A_Pqv G_Rq (batched over P): (m = v, c = R), A(v, q) = A[P, q, v], B(q, R) = Y[R, q]
+          THC_TRY(launch_gemm<false, true>(ctx, K_SOX_B, n, N, n, Pc, View{ctx->Ablk, nn, 1, n}, View{Yk, 0, 1, n},
+                                           f64::StoreEpi{ctx->Bblk, Nn, 1, n, 1.0}, "B"));
+          // C and D fused
+          ProfRec rec;
+          THC_TRY(prof_begin(ctx, K_SOX_CD, 2.0 * Pc * N * nn + 2.0 * Pc * N * n, &rec));
+          sox_cd_kernel<<<dim3((unsigned)((Pc + BN - 1) / BN), (unsigned)N), NT, 0, ctx->stream>>>(
+              (int)n, (int)N, (int)P0, (int)Pc, ctx->U, Yk, ctx->Bblk, Dk);
+          THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "C/D"));
+        }
+      }
+    }
+    // M = C_SOX D^T + C_DIRECT G^X o (V Pi V)
+    const double* Mbuf;
+    View mview;
+    if (dir) {
+      // T = V Pi -> GXm buffer;  W = T V with the merge epilogue -> Pi buffer
+      THC_TRY(launch_gemm<true, false>(ctx, K_DIRECT_VPI, N, N, N, tc, View{ctx->V, 0, N, 1}, View{ctx->Pi, NN, N, 1},
+                                       f64::StoreEpi{ctx->GXm, NN, N, 1, 1.0}, "V Pi"));
+      THC_TRY(launch_gemm<true, false>(ctx, K_DIRECT_W, N, N, N, tc, View{ctx->GXm, NN, N, 1}, View{ctx->V, 0, N, 1},
+                                       MergeEpi{ctx->Pi, sox ? ctx->D : nullptr, ctx->GXp, N}, "W"));
+      Mbuf = ctx->Pi;
+      mview = View{Mbuf, NN, N, 1};
+    } else {
+      Mbuf = ctx->D;  // M_RP = D_PR (C_SOX = +1)
+      mview = View{Mbuf, NN, 1, N};
+    }
+    // T2 = M X^T : (m = R, c = r), A(R, P) = M[R, P], B(P, r) = X[r, P]
+    if (dir)
+      THC_TRY(launch_gemm<true, true>(ctx, K_BACK, N, n, N, tc, mview, View{ctx->X, 0, 1, N},
+                                      f64::StoreEpi{ctx->T2, Nn, n, 1, 1.0}, "M X^T"));
+    else
+      THC_TRY(launch_gemm<false, true>(ctx, K_BACK, N, n, N, tc, mview, View{ctx->X, 0, 1, N},
+                                       f64::StoreEpi{ctx->T2, Nn, n, 1, C_SOX}, "M X^T"));
+    // Sigma = X T2 : (m = t, c = r), A(t, R) = X[t, R], B(R, r) = T2[R, r]
+    THC_TRY(launch_gemm<true, false>(ctx, K_BACK, n, n, N, tc, View{ctx->X, 0, N, 1}, View{ctx->T2, Nn, n, 1},
+                                     f64::StoreEpi{Sigma + c0 * nn, nn, n, 1, 1.0}, "X T2"));
+  }
+  return THC_OK;
+}
+
+int energy_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const double* Sigma,
+                const double* w_host, double* E) {
+  const long long n = ctx->n, nt = ctx->n_tau, nn = n * n;
+  const double* gb0 = G_bmt ? G_bmt : G_tau + (nt - 1) * nn;
+  const long long sgb = G_bmt ? nn : -nn;
+  THC_TRY(check_cuda(ctx, cudaMemcpyAsync(ctx->e_w, w_host, sizeof(double) * nt, cudaMemcpyHostToDevice, ctx->stream),
+                     "copy weights"));
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, K_ENERGY, 0.0, &rec));
+  trace_kernel<<<(unsigned)nt, 256, 0, ctx->stream>>>((int)n, gb0, sgb, Sigma, ctx->e_part);
+  THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "trace"));
+  THC_TRY(prof_begin(ctx, K_ENERGY, 0.0, &rec));
+  energy_sum_kernel<<<1, 32, 0, ctx->stream>>>((int)nt, ctx->e_part, ctx->e_w, ctx->e_out);
+  THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "energy sum"));
+  THC_TRY(check_cuda(ctx, cudaMemcpyAsync(E, ctx->e_out, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+                     "copy energy"));
+  return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "energy sync");
+}
+
+}  // namespace thc

@@ -1,0 +1,252 @@
+// C ABI of the THC self-energy library (declared in include/thc_sigma.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "thc_internal.cuh"
+
+namespace {
+thread_local std::string g_init_error;
+}  // namespace
+
+namespace thc {
+
+int fail(thc_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  else g_init_error = msg;
+  return code;
+}
+
+int check_cuda(thc_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return THC_OK;
+  const int code = (e == cudaErrorMemoryAllocation) ? THC_ENOMEM : THC_ECUDA;
+  return fail(ctx, code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int ctx_alloc(thc_ctx* ctx, void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  if (bytes == 0) return THC_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free allocation error
+    *p = nullptr;
+    return fail(ctx, THC_ENOMEM, std::string("cudaMalloc ") + what + " (" + std::to_string(bytes) + " bytes): " +
+                                     cudaGetErrorString(e));
+  }
+  ctx->owned.push_back(*p);
+  return THC_OK;
+}
+
+}  // namespace thc
+
+namespace {
+
+void release(thc_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  thc::prof_release(ctx);
+  for (void* p : ctx->owned) cudaFree(p);
+  ctx->owned.clear();
+}
+
+int choose_blocking(thc_ctx* ctx, size_t budget) {
+  const size_t d = sizeof(double);
+  const size_t n = ctx->n, N = ctx->N;
+  const size_t per_p = d * (n * n + N * n);
+  const size_t per_t = d * (3 * N * n + 4 * N * N);
+  size_t pb = std::max<size_t>(1, (budget / 2) / per_p);
+  pb = std::min<size_t>(pb, N);
+  size_t rest = budget > pb * per_p ? budget - pb * per_p : 0;
+  size_t tc = std::max<size_t>(1, rest / per_t);
+  tc = std::min<size_t>(tc, (size_t)ctx->n_tau);
+  ctx->Pb = (int)pb;
+  ctx->tc = (int)tc;
+  return THC_OK;
+}
+
+int init_impl(thc_ctx* ctx, const double* X, const double* V, const double* tau) {
+  using namespace thc;
+  const size_t n = ctx->n, N = ctx->N, nt = ctx->n_tau;
+  ctx->tau.assign(tau, tau + nt);
+  for (size_t k = 0; k < nt; ++k) {
+    if (!(tau[k] > 0.0 && tau[k] < ctx->beta) || (k > 0 && !(tau[k] > tau[k - 1])))
+      return fail(ctx, THC_EINVAL, "tau must be strictly ascending inside (0, beta)");
+  }
+  ctx->mirrored = true;
+  for (size_t k = 0; k < nt; ++k)
+    if (std::fabs(tau[k] + tau[nt - 1 - k] - ctx->beta) > 1e-10 * ctx->beta) ctx->mirrored = false;
+
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->X, sizeof(double) * n * N, "X"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->V, sizeof(double) * N * N, "V"));
+  THC_TRY(check_cuda(ctx, cudaMemcpyAsync(ctx->X, X, sizeof(double) * n * N, cudaMemcpyDefault, ctx->stream), "copy X"));
+  THC_TRY(check_cuda(ctx, cudaMemcpyAsync(ctx->V, V, sizeof(double) * N * N, cudaMemcpyDefault, ctx->stream), "copy V"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->e_part, sizeof(double) * nt, "energy partials"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->e_w, sizeof(double) * nt, "energy weights"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->e_out, sizeof(double), "energy"));
+
+  if (ctx->precision == THC_FP64) {
+    if (ctx->terms & THC_SOX) THC_TRY(ctx_alloc(ctx, (void**)&ctx->U, sizeof(double) * N * n * n, "U"));
+    size_t free_b = 0, total_b = 0;
+    THC_TRY(check_cuda(ctx, cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo"));
+    size_t budget = free_b / 4;
+    if (const char* env = std::getenv("THC_WORKSPACE_BYTES")) {
+      const unsigned long long v = std::strtoull(env, nullptr, 10);
+      if (v > 0) budget = (size_t)v;
+    }
+    choose_blocking(ctx, budget);
+    const size_t NN = N * N, Nn = N * n, tc = ctx->tc, pb = ctx->Pb;
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->Y, sizeof(double) * tc * Nn, "Y"));
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->Ym, sizeof(double) * tc * Nn, "Ym"));
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->GXp, sizeof(double) * tc * NN, "GX+"));
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->GXm, sizeof(double) * tc * NN, "GX-"));
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->Pi, sizeof(double) * tc * NN, "Pi"));
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->D, sizeof(double) * tc * NN, "D"));
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->T2, sizeof(double) * tc * Nn, "T2"));
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->Ablk, sizeof(double) * pb * n * n, "A block"));
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->Bblk, sizeof(double) * pb * Nn, "B block"));
+    if (ctx->terms & THC_SOX) THC_TRY(fp64_build_U(ctx));
+  } else {
+    return fail(ctx, THC_ENOTSUP, "precision mode not available in this build");
+  }
+  return THC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int thc_sigma_init(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, const double* X, const double* V,
+                   const double* tau, int precision, int terms, void* stream) {
+  using namespace thc;
+  g_init_error.clear();
+  if (!out) return fail(nullptr, THC_EINVAL, "ctx out-pointer is NULL");
+  *out = nullptr;
+  if (n_ao < 1 || n_thc < 1 || n_tau < 1 || !(beta > 0.0))
+    return fail(nullptr, THC_EINVAL, "need n_ao, n_thc, n_tau >= 1 and beta > 0");
+  if (n_thc > 65535) return fail(nullptr, THC_EINVAL, "n_thc above 65535 is not supported");
+  if (!X || !V || !tau) return fail(nullptr, THC_EINVAL, "X, V and tau must be non-NULL");
+  if (precision != THC_FP64 && precision != THC_BF16X3) return fail(nullptr, THC_EINVAL, "unknown precision");
+  if (terms <= 0 || terms > (THC_DIRECT | THC_SOX)) return fail(nullptr, THC_EINVAL, "terms must be a non-empty subset of THC_DIRECT|THC_SOX");
+  thc_ctx* ctx = nullptr;
+  try {
+    ctx = new thc_ctx();
+  } catch (...) {
+    return fail(nullptr, THC_ENOMEM, "host allocation of the context failed");
+  }
+  ctx->n = n_ao;
+  ctx->N = n_thc;
+  ctx->n_tau = n_tau;
+  ctx->beta = beta;
+  ctx->precision = precision;
+  ctx->terms = terms;
+  ctx->stream = (cudaStream_t)stream;
+  int rc;
+  try {
+    rc = init_impl(ctx, X, V, tau);
+  } catch (...) {
+    rc = fail(ctx, THC_ENOMEM, "host allocation failed during init");
+  }
+  if (rc != THC_OK) {
+    g_init_error = ctx->err;
+    release(ctx);
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return THC_OK;
+}
+
+int thc_sigma_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma_tau) {
+  using namespace thc;
+  if (!ctx) return fail(nullptr, THC_EINVAL, "ctx is NULL");
+  if (!G_tau || !Sigma_tau) return fail(ctx, THC_EINVAL, "G_tau and Sigma_tau must be non-NULL");
+  if (!G_bmt && !ctx->mirrored) return fail(ctx, THC_EINVAL, "tau grid is not mirror-symmetric: pass G_bmt");
+  if (Sigma_tau == G_tau || (G_bmt && Sigma_tau == G_bmt)) return fail(ctx, THC_EINVAL, "Sigma_tau aliases an input");
+  try {
+    if (ctx->precision == THC_FP64) return fp64_eval(ctx, G_tau, G_bmt, Sigma_tau);
+  } catch (...) {
+    return fail(ctx, THC_ENOMEM, "host allocation failed during eval");
+  }
+  return fail(ctx, THC_ENOTSUP, "precision mode not available");
+}
+
+int thc_sigma_eval_host(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma_tau) {
+  using namespace thc;
+  if (!ctx) return fail(nullptr, THC_EINVAL, "ctx is NULL");
+  if (!G_tau || !Sigma_tau) return fail(ctx, THC_EINVAL, "G_tau and Sigma_tau must be non-NULL");
+  const size_t bytes = sizeof(double) * (size_t)ctx->n_tau * ctx->n * ctx->n;
+  if (!ctx->hG) THC_TRY(ctx_alloc(ctx, (void**)&ctx->hG, bytes, "host-entry G"));
+  if (!ctx->hS) THC_TRY(ctx_alloc(ctx, (void**)&ctx->hS, bytes, "host-entry Sigma"));
+  if (G_bmt && !ctx->hGb) THC_TRY(ctx_alloc(ctx, (void**)&ctx->hGb, bytes, "host-entry G(beta-tau)"));
+  THC_TRY(check_cuda(ctx, cudaMemcpyAsync(ctx->hG, G_tau, bytes, cudaMemcpyHostToDevice, ctx->stream), "H2D G"));
+  if (G_bmt)
+    THC_TRY(check_cuda(ctx, cudaMemcpyAsync(ctx->hGb, G_bmt, bytes, cudaMemcpyHostToDevice, ctx->stream), "H2D Gb"));
+  THC_TRY(thc_sigma_eval(ctx, ctx->hG, G_bmt ? ctx->hGb : nullptr, ctx->hS));
+  THC_TRY(check_cuda(ctx, cudaMemcpyAsync(Sigma_tau, ctx->hS, bytes, cudaMemcpyDeviceToHost, ctx->stream), "D2H Sigma"));
+  return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "host-entry sync");
+}
+
+int thc_energy(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const double* Sigma_tau,
+               const double* tau_weights, double* E_dyn) {
+  using namespace thc;
+  if (!ctx) return fail(nullptr, THC_EINVAL, "ctx is NULL");
+  if (!G_tau || !Sigma_tau || !tau_weights || !E_dyn) return fail(ctx, THC_EINVAL, "NULL argument to thc_energy");
+  if (!G_bmt && !ctx->mirrored) return fail(ctx, THC_EINVAL, "tau grid is not mirror-symmetric: pass G_bmt");
+  return energy_eval(ctx, G_tau, G_bmt, Sigma_tau, tau_weights, E_dyn);
+}
+
+int thc_set_stream(thc_ctx* ctx, void* stream) {
+  if (!ctx) return thc::fail(nullptr, THC_EINVAL, "ctx is NULL");
+  ctx->stream = (cudaStream_t)stream;
+  return THC_OK;
+}
+
+double thc_sigma_flops(const thc_ctx* ctx, double* u_flops) {
+  if (!ctx) return 0.0;
+  const double n = ctx->n, N = ctx->N, nt = ctx->n_tau;
+  double f = 4.0 * N * n * n + 2.0 * N * N * n;  // Y, M X^T, X T2
+  if (ctx->terms & THC_SOX) f += 2.0 * N * n * n * n + 4.0 * N * N * n * n + 2.0 * N * N * n;
+  if (ctx->terms & THC_DIRECT) f += 2.0 * N * n * n + 4.0 * N * N * n + 4.0 * N * N * N;
+  if (u_flops) *u_flops = (ctx->terms & THC_SOX) ? 2.0 * N * N * n * n : 0.0;
+  return nt * f;
+}
+
+int thc_profile(thc_ctx* ctx, int enable) {
+  using namespace thc;
+  if (!ctx) return fail(nullptr, THC_EINVAL, "ctx is NULL");
+  THC_TRY(prof_flush(ctx));
+  if (enable)
+    for (int k = 0; k < K_COUNT; ++k) ctx->prof_stat[k] = ProfStat();
+  ctx->prof_on = enable != 0;
+  return THC_OK;
+}
+
+int thc_profile_get(thc_ctx* ctx, int kclass, const char** name, long long* launches, double* ms, double* flops) {
+  using namespace thc;
+  if (!ctx) return fail(nullptr, THC_EINVAL, "ctx is NULL");
+  if (kclass < 0 || kclass >= K_COUNT) return THC_EINVAL;
+  THC_TRY(prof_flush(ctx));
+  if (name) *name = kernel_class_name(kclass);
+  if (launches) *launches = ctx->prof_stat[kclass].launches;
+  if (ms) *ms = ctx->prof_stat[kclass].ms;
+  if (flops) *flops = ctx->prof_stat[kclass].flops;
+  return THC_OK;
+}
+
+long long thc_launch_count(const thc_ctx* ctx) { return ctx ? ctx->launch_count : 0; }
+
+void thc_destroy(thc_ctx* ctx) {
+  if (!ctx) return;
+  release(ctx);
+  delete ctx;
+}
+
+const char* thc_last_error(const thc_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"

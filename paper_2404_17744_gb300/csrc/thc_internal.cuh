@@ -1,0 +1,107 @@
+// Internal declarations of the THC self-energy library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "thc_sigma.h"
+
+namespace thc {
+// Kernel classes timed by the optional profiler (thc_profile / thc_profile_get).
+enum KernelClass {
+  K_UBUILD = 0,   // U_Pqs build
+  K_PROJECT,      // X^T G(+-tau), G^X(+-tau)
+  K_SOX_A,        // A_Pqv
+  K_SOX_B,        // B_PRv
+  K_SOX_CD,       // fused C_RvP and D_PR
+  K_POLARISATION, // Pi = G^X(tau) o G^X(-tau)^T
+  K_DIRECT_VPI,   // V Pi
+  K_DIRECT_W,     // (V Pi) V with the merge epilogue
+  K_BACK,         // M X^T and X (M X^T)
+  K_ENERGY,       // trace and weighted sum
+  K_SPLIT,        // FP64 <-> BF16 hi/lo conversions
+  K_COUNT
+};
+const char* kernel_class_name(int k);
+
+struct ProfRec {
+  int kclass;
+  cudaEvent_t e0, e1;
+  double flops;
+};
+struct ProfStat {
+  long long launches = 0;
+  double ms = 0.0, flops = 0.0;
+};
+}  // namespace thc
+
+struct thc_ctx {
+  int n = 0, N = 0, n_tau = 0;
+  double beta = 0.0;
+  int precision = THC_FP64, terms = THC_DIRECT | THC_SOX;
+  cudaStream_t stream = nullptr;
+  std::vector<double> tau;
+  bool mirrored = false;  // tau_k + tau_{n_tau-1-k} == beta (within 1e-10 beta)
+
+  // library-owned device memory
+  double *X = nullptr, *V = nullptr;  // copies of the inputs
+  double *U = nullptr;                // U_Pqs, N x n x n (FP64 path)
+  // FP64 per-chunk workspace
+  int tc = 1;   // tau points per chunk
+  int Pb = 1;   // THC points per SOX block
+  double *Y = nullptr, *Ym = nullptr;     // tc x N x n: X^T G(tau), X^T G(-tau)
+  double *GXp = nullptr, *GXm = nullptr;  // tc x N x N: G^X(tau), G^X(-tau); GXm reused for V Pi
+  double *Pi = nullptr;                   // tc x N x N: Pi, then reused for the merged M
+  double *D = nullptr;                    // tc x N x N: D_PR
+  double *T2 = nullptr;                   // tc x N x n: M X^T
+  double *Ablk = nullptr;                 // Pb x n x n: A_Pqv for one P block
+  double *Bblk = nullptr;                 // Pb x N x n: B_PRv for one P block
+  // energy
+  double *e_part = nullptr;   // n_tau partial traces
+  double *e_w = nullptr;      // n_tau weights
+  double *e_out = nullptr;    // 1 scalar
+  // host-buffer entry point staging
+  double *hG = nullptr, *hGb = nullptr, *hS = nullptr;
+
+  std::vector<void*> owned;  // every cudaMalloc of this context
+  std::string err;
+
+  // launch accounting and the optional profiler
+  long long launch_count = 0;
+  bool prof_on = false;
+  std::vector<thc::ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  thc::ProfStat prof_stat[thc::K_COUNT];
+};
+
+namespace thc {
+
+// Records msg on ctx and returns code.
+int fail(thc_ctx* ctx, int code, const std::string& msg);
+int check_cuda(thc_ctx* ctx, cudaError_t e, const char* what);
+int ctx_alloc(thc_ctx* ctx, void** p, size_t bytes, const char* what);
+
+// Bracket one kernel launch: call before the launch, then prof_end after it.
+// Counts the launch; with the profiler on, records CUDA events on ctx->stream.
+int prof_begin(thc_ctx* ctx, int kclass, double flops, thc::ProfRec* rec);
+int prof_end(thc_ctx* ctx, thc::ProfRec* rec, cudaError_t launch_status, const char* what);
+int prof_flush(thc_ctx* ctx);   // synchronises and folds pending events into the stats
+void prof_release(thc_ctx* ctx);
+
+// FP64 path (sigma_fp64.cu)
+size_t fp64_workspace_bytes(int n, int N, int tc, int Pb);
+int fp64_build_U(thc_ctx* ctx);
+int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma);
+int energy_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const double* Sigma,
+                const double* w_host, double* E);
+
+}  // namespace thc
+
+#define THC_TRY(...)           \
+  do {                         \
+    int _rc = (__VA_ARGS__);   \
+    if (_rc != THC_OK) return _rc; \
+  } while (0)

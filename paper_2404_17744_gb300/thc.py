@@ -1,0 +1,162 @@
+"""ctypes binding of include/thc_sigma.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Array arguments
+may be torch tensors (device or pinned host, float64, contiguous) or numpy
+float64 arrays (host); ``None`` passes NULL.  A non-zero return code raises
+ThcError with the library's message.  Loading fails loudly when the library
+has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+THC_OK = 0
+THC_EINVAL = -1
+THC_ENOMEM = -2
+THC_ECUDA = -3
+THC_ETIMEOUT = -4
+THC_ENOTSUP = -5
+
+THC_FP64 = 0
+THC_BF16X3 = 1
+
+THC_DIRECT = 1
+THC_SOX = 2
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libthcsigma.so")
+
+_lib = None
+
+
+class ThcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"thc error {code}: {msg}")
+        self.code = code
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libthcsigma.so and declare the signatures of include/thc_sigma.h."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with `python -m paper_2404_17744_gb300.build`")
+    lib = ctypes.CDLL(p)
+    vp, dp, i, d = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.thc_sigma_init.argtypes = [ctypes.POINTER(vp), i, i, i, d, dp, dp, dp, i, i, vp]
+    lib.thc_sigma_init.restype = i
+    lib.thc_sigma_eval.argtypes = [vp, dp, dp, dp]
+    lib.thc_sigma_eval.restype = i
+    lib.thc_sigma_eval_host.argtypes = [vp, dp, dp, dp]
+    lib.thc_sigma_eval_host.restype = i
+    lib.thc_energy.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(d)]
+    lib.thc_energy.restype = i
+    lib.thc_set_stream.argtypes = [vp, vp]
+    lib.thc_set_stream.restype = i
+    lib.thc_sigma_flops.argtypes = [vp, ctypes.POINTER(d)]
+    lib.thc_sigma_flops.restype = d
+    lib.thc_profile.argtypes = [vp, i]
+    lib.thc_profile.restype = i
+    lib.thc_profile_get.argtypes = [vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.thc_profile_get.restype = i
+    lib.thc_launch_count.argtypes = [vp]
+    lib.thc_launch_count.restype = ctypes.c_longlong
+    lib.thc_destroy.argtypes = [vp]
+    lib.thc_destroy.restype = None
+    lib.thc_last_error.argtypes = [vp]
+    lib.thc_last_error.restype = ctypes.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Raw pointer of a float64 contiguous tensor/array, or NULL for None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch.Tensor
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        return ctypes.c_void_p(a.data_ptr())
+    if hasattr(a, "ctypes"):  # numpy.ndarray
+        if a.dtype.name != "float64" or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous float64 array")
+        return ctypes.c_void_p(a.ctypes.data)
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    raise TypeError(f"cannot pass {type(a)} as a pointer")
+
+
+def _check(rc: int, ctx=None):
+    if rc != THC_OK:
+        raise ThcError(rc, thc_last_error(ctx))
+
+
+def thc_last_error(ctx=None) -> str:
+    return load_library().thc_last_error(ctx).decode()
+
+
+def thc_sigma_init(n_ao, n_thc, n_tau, beta, X, V, tau, precision=THC_FP64,
+                   terms=THC_DIRECT | THC_SOX, stream=None):
+    """Returns the opaque context handle (ctypes.c_void_p)."""
+    lib = load_library()
+    ctx = ctypes.c_void_p()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    rc = lib.thc_sigma_init(ctypes.byref(ctx), int(n_ao), int(n_thc), int(n_tau), float(beta),
+                            _ptr(X), _ptr(V), _ptr(tau), int(precision), int(terms), s)
+    _check(rc, None)
+    return ctx
+
+
+def thc_sigma_eval(ctx, G_tau, G_bmt, Sigma_tau):
+    _check(load_library().thc_sigma_eval(ctx, _ptr(G_tau), _ptr(G_bmt), _ptr(Sigma_tau)), ctx)
+
+
+def thc_sigma_eval_host(ctx, G_tau, G_bmt, Sigma_tau):
+    _check(load_library().thc_sigma_eval_host(ctx, _ptr(G_tau), _ptr(G_bmt), _ptr(Sigma_tau)), ctx)
+
+
+def thc_energy(ctx, G_tau, G_bmt, Sigma_tau, tau_weights) -> float:
+    e = ctypes.c_double()
+    _check(load_library().thc_energy(ctx, _ptr(G_tau), _ptr(G_bmt), _ptr(Sigma_tau), _ptr(tau_weights),
+                                     ctypes.byref(e)), ctx)
+    return e.value
+
+
+def thc_set_stream(ctx, stream):
+    _check(load_library().thc_set_stream(ctx, None if stream is None else ctypes.c_void_p(int(stream))), ctx)
+
+
+def thc_sigma_flops(ctx) -> tuple[float, float]:
+    u = ctypes.c_double()
+    f = load_library().thc_sigma_flops(ctx, ctypes.byref(u))
+    return f, u.value
+
+
+def thc_profile(ctx, enable: bool):
+    _check(load_library().thc_profile(ctx, int(bool(enable))), ctx)
+
+
+def thc_profile_get(ctx, kclass: int):
+    """(name, launches, ms, flops) of kernel class kclass, or None past the last class."""
+    name = ctypes.c_char_p()
+    launches = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    fl = ctypes.c_double()
+    rc = load_library().thc_profile_get(ctx, int(kclass), ctypes.byref(name), ctypes.byref(launches),
+                                        ctypes.byref(ms), ctypes.byref(fl))
+    if rc == THC_EINVAL and kclass >= 0:
+        return None
+    _check(rc, ctx)
+    return name.value.decode(), launches.value, ms.value, fl.value
+
+
+def thc_launch_count(ctx) -> int:
+    return int(load_library().thc_launch_count(ctx))
+
+
+def thc_destroy(ctx):
+    load_library().thc_destroy(ctx)

@@ -1,0 +1,68 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point the header declares, and rejects bad arguments before any
+CUDA call."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_17744_gb300 import build, thc
+    if not os.path.exists(thc.LIB_PATH):
+        build.build()
+    return thc.load_library()
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*[\w\s\*]+?\b(thc_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "thc_sigma_init" in names and "thc_sigma_eval" in names and "thc_energy" in names
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_init_rejects_bad_arguments_without_gpu(lib):
+    from paper_2404_17744_gb300 import thc
+    X = np.zeros((2, 3))
+    V = np.zeros((3, 3))
+    tau = np.array([1.0, 2.0])
+    bad = [
+        dict(n_ao=0, n_thc=3, n_tau=2, beta=3.0),
+        dict(n_ao=2, n_thc=0, n_tau=2, beta=3.0),
+        dict(n_ao=2, n_thc=3, n_tau=0, beta=3.0),
+        dict(n_ao=2, n_thc=3, n_tau=2, beta=-1.0),
+        dict(n_ao=2, n_thc=70000, n_tau=2, beta=3.0),
+    ]
+    for kw in bad:
+        with pytest.raises(thc.ThcError) as ei:
+            thc.thc_sigma_init(kw["n_ao"], kw["n_thc"], kw["n_tau"], kw["beta"], X, V, tau)
+        assert ei.value.code == thc.THC_EINVAL
+        assert thc.thc_last_error(None) != ""
+    with pytest.raises(thc.ThcError):
+        thc.thc_sigma_init(2, 3, 2, 3.0, X, V, tau, precision=7)
+    with pytest.raises(thc.ThcError):
+        thc.thc_sigma_init(2, 3, 2, 3.0, X, V, tau, terms=0)
+    with pytest.raises(thc.ThcError):
+        thc.thc_sigma_init(2, 3, 2, 3.0, None, V, tau)
+
+
+def test_null_context_calls_are_rejected(lib):
+    from paper_2404_17744_gb300 import thc
+    with pytest.raises(thc.ThcError):
+        thc.thc_sigma_eval(None, None, None, None)
+    assert thc.thc_launch_count(None) == 0
+    thc.thc_destroy(None)
