@@ -156,6 +156,32 @@ int thc_profile_get(thc_ctx *ctx, int kclass, const char **name, long long *laun
 /* thc_launch_count -- kernels launched by ctx since init (always counted). */
 long long thc_launch_count(const thc_ctx *ctx);
 
+/*
+ * thc_energy_static -- the E_dyn of thc_energy for callers that cannot
+ * allocate device memory (an external allocator owns the whole GPU, a plugin
+ * may only use the buffers it is handed, or allocation is forbidden after
+ * start-up).  The paper has no counterpart: this is a deployment variant.
+ * It needs no context and calls no cudaMalloc/cudaFree; its scratch (partial
+ * traces, weights, result) is a fixed device array of THC_STATIC_MAX_TAU
+ * tau points that every GPU loading the library holds until exit.
+ *   n_ao, n_tau   sizes; THC_EINVAL if n_tau > THC_STATIC_MAX_TAU
+ *   G_tau, Sigma_tau  dev, n_tau x n_ao x n_ao
+ *   G_bmt         dev G(beta - tau_k), or NULL to read G_tau[n_tau-1-k]
+ *                 (the caller vouches that its grid is mirror-symmetric)
+ *   tau_weights   host, n_tau quadrature weights
+ *   E_dyn         host out; the result equals thc_energy's bit for bit
+ *   stream        cudaStream_t (NULL: legacy default stream); synchronised
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (other streams or threads) race and must be serialised by the
+ * caller.  Failures are described by thc_last_error(NULL).
+ */
+#define THC_STATIC_MAX_TAU 4096
+int thc_energy_static(int n_ao, int n_tau, const double *G_tau, const double *G_bmt,
+                      const double *Sigma_tau, const double *tau_weights, double *E_dyn,
+                      void *stream);
+
 /* thc_destroy -- free everything ctx owns (NULL is a no-op).  Synchronises. */
 void thc_destroy(thc_ctx *ctx);
 

@@ -64,6 +64,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_profile_get.restype = i
     lib.thc_launch_count.argtypes = [vp]
     lib.thc_launch_count.restype = ctypes.c_longlong
+    lib.thc_energy_static.argtypes = [i, i, dp, dp, dp, dp, ctypes.POINTER(d), vp]
+    lib.thc_energy_static.restype = i
     lib.thc_destroy.argtypes = [vp]
     lib.thc_destroy.restype = None
     lib.thc_last_error.argtypes = [vp]
@@ -156,6 +158,15 @@ def thc_profile_get(ctx, kclass: int):
 
 def thc_launch_count(ctx) -> int:
     return int(load_library().thc_launch_count(ctx))
+
+
+def thc_energy_static(n_ao, n_tau, G_tau, G_bmt, Sigma_tau, tau_weights, stream=None) -> float:
+    """E_dyn without a context or any device allocation (fixed static scratch)."""
+    e = ctypes.c_double()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(load_library().thc_energy_static(int(n_ao), int(n_tau), _ptr(G_tau), _ptr(G_bmt), _ptr(Sigma_tau),
+                                            _ptr(tau_weights), ctypes.byref(e), s), None)
+    return e.value
 
 
 def thc_destroy(ctx):
