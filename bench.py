@@ -33,6 +33,12 @@ UNIT = "TFLOP/s"
 # FP64 peak of the GB300: nominal 1.25 TFLOP/s = 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 L2_BYTES = 129 * 1024 * 1024
+# DRAM bytes (read + write) per launch from an ncu capture of the kernel as it
+# stands, keyed by (kernel class, workload); profiles/ holds the capture summary.
+NCU_TRAFFIC = {
+    ("sox_CD", "thc200"): (1.927304e9 + 0.011961e9, "profiles/sox_cd_kernel_thc200s.md (same per-launch shape)"),
+    ("sox_CD", "thc200s"): (1.927304e9 + 0.011961e9, "profiles/sox_cd_kernel_thc200s.md"),
+}
 
 
 def parse():
@@ -273,6 +279,10 @@ def run_ours(args):
         "flops_per_launch": per_launch_flops, "ms_per_launch": dom_stat["ms"] / dom_stat["launches"],
         "traffic": None,
     }
+    tr = NCU_TRAFFIC.get((dom_name, args.workload))
+    if tr:
+        roofline["traffic"] = tr[0]
+        roofline["traffic_source"] = tr[1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",

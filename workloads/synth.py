@@ -157,6 +157,8 @@ def make_sigma_case(n: int, N: int, n_tau: int, beta: float, seed: int,
 WORKLOADS = {
     "thc20":   dict(n=20,   N=60,   n_tau=32,  beta=100.0,  seed=SEED_BASE + 1),
     "thc200":  dict(n=200,  N=1000, n_tau=100, beta=100.0,  seed=SEED_BASE + 2, identity_S=False, n_occ=40),
+    # the same system on 4 tau points: small profiling case (U_Pqs = 320 MB still exceeds L2)
+    "thc200s": dict(n=200,  N=1000, n_tau=4,   beta=100.0,  seed=SEED_BASE + 2, identity_S=False, n_occ=40),
     "thc500":  dict(n=500,  N=2500, n_tau=120, beta=1000.0, seed=SEED_BASE + 3),
     "thc1100": dict(n=1100, N=5500, n_tau=100, beta=1000.0, seed=SEED_BASE + 5),
 }
