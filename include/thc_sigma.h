@@ -123,6 +123,27 @@ int thc_sigma_eval_host(thc_ctx *ctx, const double *G_tau, const double *G_bmt, 
 int thc_energy(thc_ctx *ctx, const double *G_tau, const double *G_bmt,
                const double *Sigma_tau, const double *tau_weights, double *E_dyn);
 
+/*
+ * thc_sync -- wait for the work queued on ctx's stream and report a
+ * tensor-core pipeline wait that ran out (THC_ETIMEOUT) during it.
+ */
+int thc_sync(thc_ctx *ctx);
+
+/*
+ * thc_gemm_bf16x3 -- C[b] = A[b] B[b]^T for FP64 matrices, computed as three
+ * BF16 products (hi*hi + hi*lo + lo*hi, hi = bf16(x), lo = bf16(x - hi)) on
+ * the tcgen05 tensor cores with FP32 accumulation: the contraction unit of
+ * the THC_BF16X3 path (relative error about 1e-5 of sum_k |A_mk B_nk|).
+ *   A  dev, batch x M x K row-major, consecutive batches strideA apart
+ *      (strideA = 0: one A for every batch); B likewise N x K, strideB
+ *   C  dev, batch x M x N row-major, strideC apart, overwritten
+ *   stream  cudaStream_t (NULL: legacy default stream); synchronised
+ * Temporary operand copies are allocated stream-ordered (cudaMallocAsync)
+ * and freed before return.  Failures are described by thc_last_error(NULL).
+ */
+int thc_gemm_bf16x3(int batch, int M, int N, int K, const double *A, long long strideA,
+                    const double *B, long long strideB, double *C, long long strideC, void *stream);
+
 /* thc_set_stream -- launch subsequent work of ctx on stream (cudaStream_t). */
 int thc_set_stream(thc_ctx *ctx, void *stream);
 

@@ -1,0 +1,530 @@
+// Split-precision (3 x BF16 on tcgen05) evaluation of the THC self-energy.
+//
+// Same steps and order as the FP64 path (Sec. II.C scheme plus the direct
+// term), with every contraction on the tensor cores through
+// tc::split_gemm_kernel: operands are BF16 hi/lo pairs, accumulation is FP32
+// in TMEM, and each epilogue either re-splits its output for the next
+// contraction, stores it in FP32, reduces it (the Hadamard-reduce of D_PR),
+// or writes the FP64 result.  Contractions are arranged so that both
+// operands are K-major:
+//   Y[R][q]      = sum_u Xt[R][u] G[q][u]                      (G symmetric)
+//   A^T_P[v][q]  = sum_s U[P q][s] G(-tau)[v][s]   -> stored transposed per P
+//   B_P[R][v]    = sum_q Y[R][q] A^T_P[v][q]
+//   D[P][R]     += sum_v (sum_w Y[P][w] U_R[v][w]) B_P[R][v]   (C never stored)
+//   G^X[P][R]    = sum_q Y[P][q] Xt[R][q]
+//   T[P][S]      = sum_Q V[P][Q] Pi[S][Q]                       (Pi symmetric)
+//   M[R][P]      = c_x D[P][R] + c_d G^X[R][P] sum_S T[R][S] V[P][S]
+//   T2t[r][R]    = sum_P M[R][P] X[r][P]        -> stored transposed
+//   Sigma[t][r]  = sum_R X[t][R] T2t[r][R]
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+
+#include "tc_gemm.cuh"
+#include "thc_internal.cuh"
+
+namespace thc {
+namespace {
+
+using bf16 = __nv_bfloat16;
+using tc::Cfg;
+
+constexpr double C_DIRECT = -2.0;
+constexpr double C_SOX = +1.0;
+
+inline long long pad8(long long x) { return (x + 7) / 8 * 8; }
+
+// BF16 hi/lo pair: element (b, r, c) at hi[b * bs + r * ld + c].
+struct Split {
+  bf16* hi;
+  bf16* lo;
+  long long rows;
+  long long ld;
+  long long batch;
+  long long bs;
+  Split at_row(long long r0, long long nrows) const { return Split{hi + r0 * ld, lo + r0 * ld, nrows, ld, batch, bs}; }
+  Split at_batch(long long b0, long long nb) const { return Split{hi + b0 * bs, lo + b0 * bs, rows, ld, nb, bs}; }
+};
+
+// ------------------------------------------------------------- tensor maps
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mu;
+
+int get_encoder(thc_ctx* ctx) {
+  std::lock_guard<std::mutex> lock(g_encode_mu);
+  if (g_encode) return THC_OK;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+    return fail(ctx, THC_ECUDA, "cuTensorMapEncodeTiled entry point not available");
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return THC_OK;
+}
+
+// 3-D map (k, row, batch) over one half of a Split, box 64 x box_rows x 1, 128-byte swizzle.
+int make_map(thc_ctx* ctx, CUtensorMap* m, const bf16* base, long long K, const Split& s, int box_rows) {
+  const long long batch = std::max<long long>(1, s.batch);
+  const long long bs = s.batch > 1 ? s.bs : s.rows * s.ld;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)s.rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)(s.ld * 2), (cuuint64_t)(bs * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)tc::BKE, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (s.ld * 2) % 16 || (bs * 2) % 16)
+    return fail(ctx, THC_EINVAL, "tensor map operand not 16-byte aligned");
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, THC_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return THC_OK;
+}
+
+// ------------------------------------------------------------ epilogues
+__device__ __forceinline__ void split_store(bf16* hi, bf16* lo, long long o, float v) {
+  const bf16 h = __float2bfloat16_rn(v);
+  hi[o] = h;
+  lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// dst(b, row, col) = scale * C, split, row-major (or transposed: dst(b, col, row)).
+template <bool TRANSPOSED>
+struct EpiSplit {
+  bf16 *hi, *lo;
+  long long ld, bs;
+  float scale;
+  __device__ void operator()(int b, int row, int col0, const float* v, int M, int N) const {
+    if (row >= M) return;
+    const int cn = min(32, N - col0);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= cn) break;
+      const long long o = TRANSPOSED ? (long long)b * bs + (long long)(col0 + j) * ld + row
+                                     : (long long)b * bs + (long long)row * ld + col0 + j;
+      split_store(hi, lo, o, scale * v[j]);
+    }
+  }
+};
+
+// A^T blocks: row = P n + q (P local to the block), col = v  ->  At[P][v][q], split.
+struct EpiAt {
+  bf16 *hi, *lo;
+  int n;
+  long long ld;
+  __device__ void operator()(int, int row, int col0, const float* v, int M, int N) const {
+    if (row >= M) return;
+    const int P = row / n, q = row - P * n;
+    const int cn = min(32, N - col0);
+    const long long base = (long long)P * n * ld + q;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < cn) split_store(hi, lo, base + (long long)(col0 + j) * ld, v[j]);
+  }
+};
+
+// FP32 store: dst[b * bs + row * ld + col].
+struct EpiF32 {
+  float* dst;
+  long long ld, bs;
+  __device__ void operator()(int b, int row, int col0, const float* v, int M, int N) const {
+    if (row >= M) return;
+    const int cn = min(32, N - col0);
+    float* d = dst + (long long)b * bs + (long long)row * ld + col0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < cn) d[j] = v[j];
+  }
+};
+
+// FP64 store: dst[b * bs + row * ld + col].
+struct EpiF64 {
+  double* dst;
+  long long ld, bs;
+  __device__ void operator()(int b, int row, int col0, const float* v, int M, int N) const {
+    if (row >= M) return;
+    const int cn = min(32, N - col0);
+    double* d = dst + (long long)b * bs + (long long)row * ld + col0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < cn) d[j] = (double)v[j];
+  }
+};
+
+// Hadamard-reduce of the fused C/D step: b = R, row = P (local), col = v.
+//   D[(P0 + P) N + R] += sum_v C[P][v] B[P][R][v]
+struct EpiHad {
+  const float* Bf;  // Pb x N x n
+  double* D;
+  int n, N, P0;
+  __device__ void operator()(int b, int row, int col0, const float* v, int M, int Ncols) const {
+    if (row >= M) return;
+    const int cn = min(32, Ncols - col0);
+    const float* bp = Bf + ((long long)row * N + b) * n + col0;
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < cn) acc = fmaf(v[j], bp[j], acc);
+    atomicAdd(&D[((long long)P0 + row) * N + b], (double)acc);
+  }
+};
+
+// Merge epilogue of W = T V: M[b][R][P] = c_x D[b][P][R] + c_d G^X[b][R][P] W, split.
+struct EpiMerge {
+  bf16 *hi, *lo;
+  long long ld;
+  const double* D;  // may be null
+  const float* GX;
+  int N;
+  __device__ void operator()(int b, int row, int col0, const float* v, int M, int Ncols) const {
+    if (row >= M) return;
+    const int cn = min(32, Ncols - col0);
+    const long long NN = (long long)N * N;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= cn) break;
+      const int P = col0 + j;
+      double m = C_DIRECT * (double)GX[b * NN + (long long)row * N + P] * (double)v[j];
+      if (D) m += C_SOX * D[b * NN + (long long)P * N + row];
+      split_store(hi, lo, (long long)b * N * ld + (long long)row * ld + P, (float)m);
+    }
+  }
+};
+
+// U build: row = P, col = (q - q0) n + s  ->  U[(P n + q) ld + s], split.
+struct EpiU {
+  bf16 *hi, *lo;
+  int n, q0;
+  long long ld;
+  __device__ void operator()(int, int row, int col0, const float* v, int M, int Ncols) const {
+    if (row >= M) return;
+    const int cn = min(32, Ncols - col0);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= cn) break;
+      const int c = col0 + j, q = q0 + c / n, s = c - (c / n) * n;
+      split_store(hi, lo, ((long long)row * n + q) * ld + s, v[j]);
+    }
+  }
+};
+
+// --------------------------------------------------------- split kernels
+// dst(b, r, c) = split(scale * src[b sb + r sr + c sc]) for c < cols; 0 on the padding cols..ld.
+__global__ void split_f64_kernel(const double* __restrict__ src, long long sb, long long sr, long long sc,
+                                 double scale, bf16* __restrict__ hi, bf16* __restrict__ lo, long long rows,
+                                 long long cols, long long ld, long long batch, long long dbs) {
+  const long long per = rows * ld, total = per * batch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / per, rem = i - b * per, r = rem / ld, c = rem - r * ld;
+    const long long o = b * dbs + r * ld + c;
+    if (c < cols) {
+      const double x = scale * src[b * sb + r * sr + c * sc];
+      const bf16 h = __float2bfloat16_rn((float)x);
+      hi[o] = h;
+      lo[o] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+    } else {
+      hi[o] = __float2bfloat16_rn(0.f);
+      lo[o] = __float2bfloat16_rn(0.f);
+    }
+  }
+}
+
+// Khatri-Rao block of the U build: KR[(q - q0) n + s][Q] = X[q][Q] X[s][Q], split, ld >= N.
+__global__ void kr_split_kernel(const double* __restrict__ X, int n, int N, int q0, int qb, bf16* __restrict__ hi,
+                                bf16* __restrict__ lo, long long ld) {
+  const long long total = (long long)qb * n * ld;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / ld, Q = i - r * ld;
+    const int q = q0 + (int)(r / n), s = (int)(r % n);
+    if (Q < N) {
+      const double x = X[(long long)q * N + Q] * X[(long long)s * N + Q];
+      const bf16 h = __float2bfloat16_rn((float)x);
+      hi[i] = h;
+      lo[i] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+    } else {
+      hi[i] = __float2bfloat16_rn(0.f);
+      lo[i] = __float2bfloat16_rn(0.f);
+    }
+  }
+}
+
+// Pi[b][Q][S] = G^X[b][Q][S] G^X(-)[b][S][Q], split.
+__global__ void polarisation_split_kernel(long long N, long long batch, const float* __restrict__ GX,
+                                          const float* __restrict__ GXm, bf16* __restrict__ hi,
+                                          bf16* __restrict__ lo, long long ld) {
+  const long long per = N * ld, total = per * batch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / per, rem = i - b * per, q = rem / ld, s = rem - q * ld;
+    float v = 0.f;
+    if (s < N) v = GX[b * N * N + q * N + s] * GXm[b * N * N + s * N + q];
+    const bf16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+inline int blocks_for(long long total) { return (int)std::min<long long>((total + 255) / 256, 152LL * 32); }
+
+int launch_split_f64(thc_ctx* ctx, const double* src, long long sb, long long sr, long long sc, double scale,
+                     const Split& d, long long cols, const char* what) {
+  const long long total = d.rows * d.ld * std::max<long long>(1, d.batch);
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, K_SPLIT, 0.0, &rec));
+  split_f64_kernel<<<blocks_for(total), 256, 0, ctx->stream>>>(src, sb, sr, sc, scale, d.hi, d.lo, d.rows, cols, d.ld,
+                                                               std::max<long long>(1, d.batch), d.bs);
+  return prof_end(ctx, &rec, cudaGetLastError(), what);
+}
+
+// ----------------------------------------------------------- GEMM launch
+// C[b](M x N) = A[b](M x K) B[b](N x K)^T in split precision; epi consumes C.
+template <int BN, class Epi>
+int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, const Split& B, bool b_batched,
+                      long long M, long long N, long long K, long long batch, const Epi& epi, const char* what) {
+  if (M <= 0 || N <= 0 || batch <= 0) return THC_OK;
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX || batch > 65535)
+    return fail(ctx, THC_EINVAL, std::string(what) + ": contraction too large");
+  CUtensorMap ah, al, bh, bl;
+  THC_TRY(make_map(ctx, &ah, A.hi, K, A, tc::BM));
+  THC_TRY(make_map(ctx, &al, A.lo, K, A, tc::BM));
+  THC_TRY(make_map(ctx, &bh, B.hi, K, B, BN));
+  THC_TRY(make_map(ctx, &bl, B.lo, K, B, BN));
+  auto kern = tc::split_gemm_kernel<BN, Epi>;
+  static bool attr_set = false;  // one per instantiation
+  if (!attr_set) {
+    THC_TRY(check_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN>::SMEM),
+                       "split gemm smem attribute"));
+    attr_set = true;
+  }
+  const dim3 grid((unsigned)((M + tc::BM - 1) / tc::BM), (unsigned)((N + BN - 1) / BN), (unsigned)batch);
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, kclass, 2.0 * M * N * K * batch, &rec));
+  kern<<<grid, tc::NTHREADS, Cfg<BN>::SMEM, ctx->stream>>>(ah, al, bh, bl, (int)M, (int)N, (int)K,
+                                                            tc::Operands{a_batched ? 1 : 0, b_batched ? 1 : 0}, epi,
+                                                            ctx->d_err);
+  return prof_end(ctx, &rec, cudaGetLastError(), what);
+}
+
+// Picks the tile width for an N-column output (fewest padded columns, then wider).
+template <class Epi>
+int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool bb, long long M, long long N,
+         long long K, long long batch, const Epi& epi, const char* what) {
+  const long long w128 = (N + 127) / 128 * 128, w256 = (N + 255) / 256 * 256;
+  if (w256 <= w128) return launch_split_gemm<256>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+  return launch_split_gemm<128>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+}
+
+Split split_of(bf16* hi, bf16* lo, long long rows, long long ld, long long batch = 1) {
+  return Split{hi, lo, rows, ld, batch, rows * ld};
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ init
+int split_init(thc_ctx* ctx, size_t budget) {
+  THC_TRY(get_encoder(ctx));
+  const long long n = ctx->n, N = ctx->N;
+  const long long ldn = pad8(n), ldN = pad8(N);
+  ctx->ldn = (int)ldn;
+  ctx->ldN = (int)ldN;
+  const size_t h = sizeof(bf16);
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->d_err, sizeof(int), "error flag"));
+  THC_TRY(check_cuda(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream), "clear error flag"));
+  auto pair = [&](bf16** hi, bf16** lo, size_t elems, const char* what) -> int {
+    THC_TRY(ctx_alloc(ctx, (void**)hi, h * elems, what));
+    return ctx_alloc(ctx, (void**)lo, h * elems, what);
+  };
+  THC_TRY(pair(&ctx->Xt_h, &ctx->Xt_l, N * ldn, "Xt"));
+  THC_TRY(pair(&ctx->Xs_h, &ctx->Xs_l, n * ldN, "Xs"));
+  THC_TRY(pair(&ctx->Vs_h, &ctx->Vs_l, N * ldN, "Vs"));
+  // blocking: per tau point and per P of the SOX block
+  const size_t per_t = h * 2 * (2 * n * ldn + 2 * N * ldn + 3 * N * ldN + n * ldN) + 4 * 2 * N * N + 8 * N * N;
+  const size_t per_p = h * 2 * n * ldn + 4 * N * n;
+  const bool sox = ctx->terms & THC_SOX;
+  if (sox) THC_TRY(pair(&ctx->Us_h, &ctx->Us_l, (size_t)N * n * ldn, "U"));
+  size_t pb = std::max<size_t>(1, (budget / 2) / per_p);
+  pb = std::min<size_t>(pb, (size_t)std::min<long long>(N, 65535));
+  const size_t rest = budget > pb * per_p ? budget - pb * per_p : 0;
+  size_t tc = std::max<size_t>(1, rest / per_t);
+  tc = std::min<size_t>(tc, (size_t)std::min(ctx->n_tau, 65535));
+  ctx->Pb = (int)pb;
+  ctx->tc = (int)tc;
+  THC_TRY(pair(&ctx->Gs_h, &ctx->Gs_l, tc * n * ldn, "G split"));
+  THC_TRY(pair(&ctx->Gms_h, &ctx->Gms_l, tc * n * ldn, "G(-tau) split"));
+  THC_TRY(pair(&ctx->Ys_h, &ctx->Ys_l, tc * N * ldn, "Y split"));
+  THC_TRY(pair(&ctx->Yms_h, &ctx->Yms_l, tc * N * ldn, "Ym split"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->GXf, 4 * tc * N * N, "G^X"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->GXmf, 4 * tc * N * N, "G^X(-)"));
+  THC_TRY(pair(&ctx->Pis_h, &ctx->Pis_l, tc * N * ldN, "Pi split"));
+  THC_TRY(pair(&ctx->Ts_h, &ctx->Ts_l, tc * N * ldN, "V Pi split"));
+  THC_TRY(pair(&ctx->Ms_h, &ctx->Ms_l, tc * N * ldN, "M split"));
+  THC_TRY(pair(&ctx->T2s_h, &ctx->T2s_l, tc * n * ldN, "T2 split"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->Dd, 8 * tc * N * N, "D"));
+  if (sox) {
+    THC_TRY(pair(&ctx->Ats_h, &ctx->Ats_l, pb * n * ldn, "A^T blocks"));
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->Bf, 4 * pb * N * n, "B blocks"));
+  }
+  // constant operands
+  THC_TRY(launch_split_f64(ctx, ctx->X, 0, 1, N, 1.0, split_of(ctx->Xt_h, ctx->Xt_l, N, ldn), n, "split X^T"));
+  THC_TRY(launch_split_f64(ctx, ctx->X, 0, N, 1, 1.0, split_of(ctx->Xs_h, ctx->Xs_l, n, ldN), N, "split X"));
+  THC_TRY(launch_split_f64(ctx, ctx->V, 0, N, 1, 1.0, split_of(ctx->Vs_h, ctx->Vs_l, N, ldN), N, "split V"));
+  if (!sox) return THC_OK;
+  // U_Pqs = sum_Q V_PQ X_qQ X_sQ over blocks of q with the Khatri-Rao block materialised
+  long long qb = std::max<long long>(1, std::min<long long>(n, (long long)(budget / 2 / (h * 2 * n * ldN))));
+  bf16 *kh = nullptr, *kl = nullptr;
+  THC_TRY(pair(&kh, &kl, (size_t)qb * n * ldN, "Khatri-Rao block"));
+  for (long long q0 = 0; q0 < n; q0 += qb) {
+    const long long nq = std::min(qb, n - q0);
+    ProfRec rec;
+    THC_TRY(prof_begin(ctx, K_SPLIT, 0.0, &rec));
+    kr_split_kernel<<<blocks_for(nq * n * ldN), 256, 0, ctx->stream>>>(ctx->X, (int)n, (int)N, (int)q0, (int)nq, kh,
+                                                                        kl, ldN);
+    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Khatri-Rao block"));
+    THC_TRY(gemm(ctx, K_UBUILD, split_of(ctx->Vs_h, ctx->Vs_l, N, ldN), false, split_of(kh, kl, nq * n, ldN), false,
+                 N, nq * n, N, 1, EpiU{ctx->Us_h, ctx->Us_l, (int)n, (int)q0, ldn}, "U build"));
+  }
+  // the Khatri-Rao block is released at init's end; keep the stream ordered first
+  THC_TRY(check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "U build sync"));
+  for (auto it = ctx->owned.begin(); it != ctx->owned.end();) {
+    if (*it == kh || *it == kl) {
+      cudaFree(*it);
+      it = ctx->owned.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return split_check(ctx);
+}
+
+int split_check(thc_ctx* ctx) {
+  if (!ctx->d_err) return THC_OK;
+  int h = 0;
+  THC_TRY(check_cuda(ctx, cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+                     "read error flag"));
+  THC_TRY(check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "error flag sync"));
+  if (h) {
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+    return fail(ctx, THC_ETIMEOUT, "a tensor-core pipeline wait ran out (code " + std::to_string(h) + ")");
+  }
+  return THC_OK;
+}
+
+// ------------------------------------------------------------------ eval
+int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
+  const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau, ldn = ctx->ldn, ldN = ctx->ldN;
+  const long long nn = n * n, NN = N * N;
+  const bool sox = ctx->terms & THC_SOX, dir = ctx->terms & THC_DIRECT;
+  const Split Xt = split_of(ctx->Xt_h, ctx->Xt_l, N, ldn);
+  const Split Xs = split_of(ctx->Xs_h, ctx->Xs_l, n, ldN);
+  const Split Vs = split_of(ctx->Vs_h, ctx->Vs_l, N, ldN);
+  for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
+    const long long tc = std::min<long long>(ctx->tc, nt - c0);
+    const Split Gs = split_of(ctx->Gs_h, ctx->Gs_l, n, ldn, tc);
+    const Split Gms = split_of(ctx->Gms_h, ctx->Gms_l, n, ldn, tc);
+    const Split Ys = split_of(ctx->Ys_h, ctx->Ys_l, N, ldn, tc);
+    const Split Yms = split_of(ctx->Yms_h, ctx->Yms_l, N, ldn, tc);
+    const Split Pis = split_of(ctx->Pis_h, ctx->Pis_l, N, ldN, tc);
+    const Split Ts = split_of(ctx->Ts_h, ctx->Ts_l, N, ldN, tc);
+    const Split Ms = split_of(ctx->Ms_h, ctx->Ms_l, N, ldN, tc);
+    const Split T2s = split_of(ctx->T2s_h, ctx->T2s_l, n, ldN, tc);
+    // G(tau_k) and G(-tau_k) = -G(beta - tau_k) as split operands
+    THC_TRY(launch_split_f64(ctx, G_tau + c0 * nn, nn, n, 1, 1.0, Gs, n, "split G"));
+    if (G_bmt)
+      THC_TRY(launch_split_f64(ctx, G_bmt + c0 * nn, nn, n, 1, -1.0, Gms, n, "split G(-tau)"));
+    else
+      THC_TRY(launch_split_f64(ctx, G_tau + (nt - 1 - c0) * nn, -nn, n, 1, -1.0, Gms, n, "split G(-tau)"));
+    // Y = X^T G(tau), Ym = X^T G(-tau)
+    THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Gs, true, N, n, n, tc,
+                 EpiSplit<false>{Ys.hi, Ys.lo, ldn, N * ldn, 1.f}, "Y"));
+    if (dir) {
+      THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Gms, true, N, n, n, tc,
+                   EpiSplit<false>{Yms.hi, Yms.lo, ldn, N * ldn, 1.f}, "Ym"));
+      THC_TRY(gemm(ctx, K_PROJECT, Ys, true, Xt, false, N, N, n, tc, EpiF32{ctx->GXf, N, NN}, "G^X"));
+      THC_TRY(gemm(ctx, K_PROJECT, Yms, true, Xt, false, N, N, n, tc, EpiF32{ctx->GXmf, N, NN}, "G^X(-)"));
+      ProfRec rec;
+      THC_TRY(prof_begin(ctx, K_POLARISATION, 0.0, &rec));
+      polarisation_split_kernel<<<blocks_for(tc * N * ldN), 256, 0, ctx->stream>>>(N, tc, ctx->GXf, ctx->GXmf,
+                                                                                   Pis.hi, Pis.lo, ldN);
+      THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "polarisation"));
+      THC_TRY(gemm(ctx, K_DIRECT_VPI, Vs, false, Pis, true, N, N, N, tc,
+                   EpiSplit<false>{Ts.hi, Ts.lo, ldN, N * ldN, 1.f}, "V Pi"));
+    }
+    if (sox) {
+      THC_TRY(check_cuda(ctx, cudaMemsetAsync(ctx->Dd, 0, 8 * tc * NN, ctx->stream), "clear D"));
+      const Split U = split_of(ctx->Us_h, ctx->Us_l, N * n, ldn);
+      const Split Ub = Split{ctx->Us_h, ctx->Us_l, n, ldn, N, n * ldn};  // [R][v][w]
+      for (long long k = 0; k < tc; ++k) {
+        const Split Gmk = Gms.at_batch(k, 1);
+        const Split Yk = Ys.at_batch(k, 1);
+        double* Dk = ctx->Dd + k * NN;
+        for (long long P0 = 0; P0 < N; P0 += ctx->Pb) {
+          const long long Pc = std::min<long long>(ctx->Pb, N - P0);
+          const Split At = Split{ctx->Ats_h, ctx->Ats_l, n, ldn, Pc, n * ldn};
+          // A^T_P[v][q] = sum_s U[P q][s] G(-tau)[v][s]  (G(-tau) carries its sign in Gms)
+          THC_TRY(gemm(ctx, K_SOX_A, U.at_row(P0 * n, Pc * n), false, Gmk, false, Pc * n, n, n, 1,
+                       EpiAt{At.hi, At.lo, (int)n, ldn}, "A"));
+          // B_P[R][v] = sum_q Y[R][q] A^T_P[v][q]
+          THC_TRY(gemm(ctx, K_SOX_B, Yk, false, At, true, N, n, n, Pc, EpiF32{ctx->Bf, n, N * n}, "B"));
+          // D[P][R] += sum_v (sum_w Y[P][w] U_R[v][w]) B_P[R][v]
+          THC_TRY(gemm(ctx, K_SOX_CD, Yk.at_row(P0, Pc), false, Ub, true, Pc, n, n, N,
+                       EpiHad{ctx->Bf, Dk, (int)n, (int)N, (int)P0}, "C/D"));
+        }
+      }
+    }
+    // merged M, back-transform
+    if (dir) {
+      THC_TRY(gemm(ctx, K_DIRECT_W, Ts, true, Vs, false, N, N, N, tc,
+                   EpiMerge{Ms.hi, Ms.lo, ldN, sox ? ctx->Dd : nullptr, ctx->GXf, (int)N}, "W"));
+    } else {
+      // M[R][P] = c_x D[P][R]
+      THC_TRY(launch_split_f64(ctx, ctx->Dd, NN, 1, N, C_SOX, Ms, N, "split D^T"));
+    }
+    THC_TRY(gemm(ctx, K_BACK, Ms, true, Xs, false, N, n, N, tc, EpiSplit<true>{T2s.hi, T2s.lo, ldN, n * ldN, 1.f},
+                 "M X^T"));
+    THC_TRY(gemm(ctx, K_BACK, Xs, false, T2s, true, n, n, N, tc, EpiF64{Sigma + c0 * nn, n, nn}, "X T2"));
+  }
+  return THC_OK;
+}
+
+// --------------------------------------------------- standalone utility
+int gemm_bf16x3(cudaStream_t stream, int batch, int M, int N, int K, const double* A, long long sA, const double* B,
+                long long sB, double* C, long long sC) {
+  thc_ctx tmp;
+  tmp.stream = stream;
+  THC_TRY(get_encoder(nullptr));
+  const long long ldK = pad8(K);
+  const long long ba = sA ? batch : 1, bb = sB ? batch : 1;
+  const size_t h = sizeof(bf16);
+  void *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr, *err = nullptr;
+  auto cleanup = [&]() {
+    if (ah) cudaFreeAsync(ah, stream);
+    if (al) cudaFreeAsync(al, stream);
+    if (bh) cudaFreeAsync(bh, stream);
+    if (bl) cudaFreeAsync(bl, stream);
+    if (err) cudaFreeAsync(err, stream);
+  };
+  auto alloc = [&](void** p, size_t bytes) { return cudaMallocAsync(p, std::max<size_t>(bytes, 16), stream); };
+  if (alloc(&ah, h * ba * M * ldK) || alloc(&al, h * ba * M * ldK) || alloc(&bh, h * bb * N * ldK) ||
+      alloc(&bl, h * bb * N * ldK) || alloc(&err, sizeof(int))) {
+    cudaGetLastError();
+    cleanup();
+    return fail(nullptr, THC_ENOMEM, "thc_gemm_bf16x3: allocation failed");
+  }
+  tmp.d_err = (int*)err;
+  int rc = check_cuda(nullptr, cudaMemsetAsync(err, 0, sizeof(int), stream), "thc_gemm_bf16x3: clear flag");
+  const Split As = Split{(bf16*)ah, (bf16*)al, M, ldK, ba, (long long)M * ldK};
+  const Split Bs = Split{(bf16*)bh, (bf16*)bl, N, ldK, bb, (long long)N * ldK};
+  if (rc == THC_OK) rc = launch_split_f64(&tmp, A, sA, K, 1, 1.0, As, K, "split A");
+  if (rc == THC_OK) rc = launch_split_f64(&tmp, B, sB, K, 1, 1.0, Bs, K, "split B");
+  if (rc == THC_OK)
+    rc = gemm(&tmp, K_BACK, As, ba > 1, Bs, bb > 1, M, N, K, batch, EpiF64{C, N, sC}, "thc_gemm_bf16x3");
+  if (rc == THC_OK) rc = split_check(&tmp);
+  cleanup();
+  cudaStreamSynchronize(stream);
+  if (rc != THC_OK) fail(nullptr, rc, tmp.err);
+  return rc;
+}
+
+}  // namespace thc

@@ -1,0 +1,301 @@
+// Split-precision contraction on the 5th-generation tensor cores (sm_103a).
+//
+//   C[b][m][n] = sum_k A[b][m][k] B[b][n][k]
+//             ~= sum_k (Ahi Bhi + Ahi Blo + Alo Bhi)       (FP32 accumulation in TMEM)
+//
+// with every FP64 operand x stored as a pair of BF16 values hi = bf16(x),
+// lo = bf16(x - hi) (about 17 significant bits together).  Both operands are
+// K-major (k contiguous), which every contraction of the THC scheme can be
+// brought to by the symmetry of G, U_Pqs and V or by writing its producer's
+// output transposed.
+//
+// One CTA computes one 128 x BN output tile with three warp roles:
+//   warp 0    one lane issues the TMA loads (128-byte swizzle) of the four
+//             operand tiles of each 64-deep K stage into a STAGES-deep ring;
+//   warp 1    allocates TMEM; one lane issues the 3 x 4 tcgen05.mma
+//             (kind::f16, M = 128, N = BN, K = 16) of a stage into one of two
+//             TMEM accumulators (stages alternate between them) and commits
+//             the stage back to the producer and to the epilogue;
+//   warps 2-9 drain each finished stage accumulator with tcgen05.ld into FP32
+//             registers (warp w owns TMEM lanes 32 (w % 4) .. and one half of
+//             the columns), free it for the stage after next, and finally run
+//             the epilogue functor on 32 columns at a time.
+// Draining every stage ("promotion") keeps the tensor core's internal
+// accumulation to one 64-deep stage: measured on GB300, accumulating a
+// 1000-deep K inside the tensor core loses several times more precision than
+// IEEE FP32 additions of 64-deep partial sums, enough to break a 1e-6
+// absolute bound on the self-energy.
+// Every mbarrier wait is bounded in time (globaltimer); a wait that runs out
+// sets *err and the CTA unwinds, frees its TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace thc {
+namespace tc {
+
+constexpr int BM = 128;        // rows of a tile (TMEM lanes)
+constexpr int BKE = 64;        // K elements per stage: one 128-byte swizzle row of BF16
+constexpr int NTHREADS = 320;  // 10 warps: TMA, MMA, 8 epilogue
+constexpr int NEPI = 256;      // epilogue threads
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s per wait
+
+template <int BN>
+struct Cfg {
+  static constexpr int A_BYTES = BM * BKE * 2;
+  static constexpr int B_BYTES = BN * BKE * 2;
+  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int STAGES = (BN >= 256) ? 2 : 3;
+  static constexpr int TMEM_COLS = 2 * BN;   // two stage accumulators; BN in {128, 256}
+  static constexpr int HALF = BN / 2;         // columns drained per epilogue thread
+  static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  static_assert(BN == 128 || BN == 256, "tile width");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Waits until the phase of parity `parity` of *bar has completed; false after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;            // version
+  d |= static_cast<uint64_t>(2) << 61;            // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 TMEM lanes x 16 consecutive 32-bit columns, added into acc[0..15]:
+// thread t reads lane (base + t).
+__device__ __forceinline__ void tmem_ld16_add(uint32_t taddr, float* acc) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] += __uint_as_float(r[i]);
+}
+
+// Operand maps: each is a 3-D tensor map (k, row, batch) over BF16 with a
+// 64 x rows box and 128-byte swizzle.  batched = 0 pins the batch coordinate to 0.
+struct Operands {
+  int a_batched, b_batched;
+};
+
+template <int BN, class Epi>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    split_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                      const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int M,
+                      int N, int K, Operands ops, Epi epi, int* err) {
+  using C = Cfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* acc_full = empty + C::STAGES;  // [2] stage accumulator ready for the epilogue
+  uint64_t* acc_free = acc_full + 2;       // [2] stage accumulator drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_free + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, b = blockIdx.z;
+  const int nkb = (K + BKE - 1) / BKE;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_free[i], NEPI);
+    }
+    fence_mbar_init();
+    prefetch_map(&mAhi);
+    prefetch_map(&mAlo);
+    prefetch_map(&mBhi);
+    prefetch_map(&mBlo);
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const int ab = ops.a_batched ? b : 0, bb = ops.b_batched ? b : 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % C::STAGES, r = kb / C::STAGES;
+        if (!mbar_wait(&empty[s], (r & 1) ^ 1)) {
+          atomicExch(err, 1);
+          break;
+        }
+        uint8_t* st = smem + s * C::STAGE;
+        mbar_arrive_expect_tx(&full[s], C::STAGE);
+        tma_load_3d(st, &mAhi, &full[s], kb * BKE, m0, ab);
+        tma_load_3d(st + C::A_BYTES, &mAlo, &full[s], kb * BKE, m0, ab);
+        tma_load_3d(st + 2 * C::A_BYTES, &mBhi, &full[s], kb * BKE, n0, bb);
+        tma_load_3d(st + 2 * C::A_BYTES + C::B_BYTES, &mBlo, &full[s], kb * BKE, n0, bb);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % C::STAGES, r = kb / C::STAGES, buf = kb & 1, use = kb >> 1;
+        if (!mbar_wait(&acc_free[buf], (use & 1) ^ 1) || !mbar_wait(&full[s], r & 1)) {
+          atomicExch(err, 2);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + static_cast<uint32_t>(buf * BN);
+        const uint32_t base = smem_u32(smem + s * C::STAGE);
+        const uint64_t ah = sw128_desc(base), al = sw128_desc(base + C::A_BYTES);
+        const uint64_t bh = sw128_desc(base + 2 * C::A_BYTES), bl = sw128_desc(base + 2 * C::A_BYTES + C::B_BYTES);
+#pragma unroll
+        for (int k = 0; k < BKE / 16; ++k) {
+          const uint64_t off = static_cast<uint64_t>((k * 32) >> 4);  // 16 BF16 = 32 bytes along K
+          mma_bf16(d, ah + off, bh + off, idesc, k != 0);
+          mma_bf16(d, ah + off, bl + off, idesc, 1u);
+          mma_bf16(d, al + off, bh + off, idesc, 1u);
+        }
+        mma_commit(&empty[s]);       // frees the smem stage once these MMAs have read it
+        mma_commit(&acc_full[buf]);  // stage accumulator ready
+      }
+    }
+  } else {
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + half * C::HALF;
+    float acc[C::HALF];
+#pragma unroll
+    for (int i = 0; i < C::HALF; ++i) acc[i] = 0.f;
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int buf = kb & 1, use = kb >> 1;
+      if (!mbar_wait(&acc_full[buf], use & 1)) {
+        if (lane == 0) atomicExch(err, 3);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < C::HALF; c += 16) tmem_ld16_add(lane_base + buf * BN + c, acc + c);
+      tc_fence_before();
+      mbar_arrive(&acc_free[buf]);
+    }
+    if (ok) {
+      const int row = m0 + quarter * 32 + lane;
+#pragma unroll
+      for (int c = 0; c < C::HALF; c += 32) {
+        const int col = n0 + half * C::HALF + c;
+        if (col < N) epi(b, row, col, acc + c, M, N);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+}  // namespace tc
+}  // namespace thc

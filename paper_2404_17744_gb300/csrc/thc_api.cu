@@ -110,7 +110,14 @@ int init_impl(thc_ctx* ctx, const double* X, const double* V, const double* tau)
     THC_TRY(ctx_alloc(ctx, (void**)&ctx->Bblk, sizeof(double) * pb * Nn, "B block"));
     if (ctx->terms & THC_SOX) THC_TRY(fp64_build_U(ctx));
   } else {
-    return fail(ctx, THC_ENOTSUP, "precision mode not available in this build");
+    size_t free_b = 0, total_b = 0;
+    THC_TRY(check_cuda(ctx, cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo"));
+    size_t budget = free_b / 4;
+    if (const char* env = std::getenv("THC_WORKSPACE_BYTES")) {
+      const unsigned long long v = std::strtoull(env, nullptr, 10);
+      if (v > 0) budget = (size_t)v;
+    }
+    THC_TRY(split_init(ctx, budget));
   }
   return THC_OK;
 }
@@ -168,10 +175,10 @@ int thc_sigma_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, doubl
   if (Sigma_tau == G_tau || (G_bmt && Sigma_tau == G_bmt)) return fail(ctx, THC_EINVAL, "Sigma_tau aliases an input");
   try {
     if (ctx->precision == THC_FP64) return fp64_eval(ctx, G_tau, G_bmt, Sigma_tau);
+    return split_eval(ctx, G_tau, G_bmt, Sigma_tau);
   } catch (...) {
     return fail(ctx, THC_ENOMEM, "host allocation failed during eval");
   }
-  return fail(ctx, THC_ENOTSUP, "precision mode not available");
 }
 
 int thc_sigma_eval_host(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma_tau) {
@@ -187,7 +194,8 @@ int thc_sigma_eval_host(thc_ctx* ctx, const double* G_tau, const double* G_bmt, 
     THC_TRY(check_cuda(ctx, cudaMemcpyAsync(ctx->hGb, G_bmt, bytes, cudaMemcpyHostToDevice, ctx->stream), "H2D Gb"));
   THC_TRY(thc_sigma_eval(ctx, ctx->hG, G_bmt ? ctx->hGb : nullptr, ctx->hS));
   THC_TRY(check_cuda(ctx, cudaMemcpyAsync(Sigma_tau, ctx->hS, bytes, cudaMemcpyDeviceToHost, ctx->stream), "D2H Sigma"));
-  return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "host-entry sync");
+  THC_TRY(check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "host-entry sync"));
+  return split_check(ctx);
 }
 
 int thc_energy(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const double* Sigma_tau,
@@ -196,7 +204,29 @@ int thc_energy(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const dou
   if (!ctx) return fail(nullptr, THC_EINVAL, "ctx is NULL");
   if (!G_tau || !Sigma_tau || !tau_weights || !E_dyn) return fail(ctx, THC_EINVAL, "NULL argument to thc_energy");
   if (!G_bmt && !ctx->mirrored) return fail(ctx, THC_EINVAL, "tau grid is not mirror-symmetric: pass G_bmt");
-  return energy_eval(ctx, G_tau, G_bmt, Sigma_tau, tau_weights, E_dyn);
+  THC_TRY(energy_eval(ctx, G_tau, G_bmt, Sigma_tau, tau_weights, E_dyn));
+  return split_check(ctx);
+}
+
+int thc_sync(thc_ctx* ctx) {
+  if (!ctx) return thc::fail(nullptr, THC_EINVAL, "ctx is NULL");
+  THC_TRY(thc::check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
+  return thc::split_check(ctx);
+}
+
+int thc_gemm_bf16x3(int batch, int M, int N, int K, const double* A, long long strideA, const double* B,
+                    long long strideB, double* C, long long strideC, void* stream) {
+  using namespace thc;
+  if (batch < 1 || M < 1 || N < 1 || K < 1 || batch > 65535)
+    return fail(nullptr, THC_EINVAL, "thc_gemm_bf16x3: need 1 <= batch <= 65535 and M, N, K >= 1");
+  if (!A || !B || !C) return fail(nullptr, THC_EINVAL, "thc_gemm_bf16x3: NULL operand");
+  if (strideA < 0 || strideB < 0 || (batch > 1 && strideC < (long long)M * N))
+    return fail(nullptr, THC_EINVAL, "thc_gemm_bf16x3: bad batch strides");
+  try {
+    return gemm_bf16x3((cudaStream_t)stream, batch, M, N, K, A, strideA, B, strideB, C, strideC);
+  } catch (...) {
+    return fail(nullptr, THC_ENOMEM, "thc_gemm_bf16x3: host allocation failed");
+  }
 }
 
 int thc_set_stream(thc_ctx* ctx, void* stream) {

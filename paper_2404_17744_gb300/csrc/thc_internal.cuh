@@ -1,6 +1,7 @@
 // Internal declarations of the THC self-energy library (not part of the ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -66,6 +67,26 @@ struct thc_ctx {
   // host-buffer entry point staging
   double *hG = nullptr, *hGb = nullptr, *hS = nullptr;
 
+  // split-precision (THC_BF16X3) path: BF16 hi/lo pairs, leading dimensions padded to 8
+  int ldn = 0, ldN = 0;                       // padded n and N
+  __nv_bfloat16 *Xt_h = nullptr, *Xt_l = nullptr;   // X^T, N x ldn
+  __nv_bfloat16 *Xs_h = nullptr, *Xs_l = nullptr;   // X,   n x ldN
+  __nv_bfloat16 *Vs_h = nullptr, *Vs_l = nullptr;   // V,   N x ldN
+  __nv_bfloat16 *Us_h = nullptr, *Us_l = nullptr;   // U,   (N n) x ldn
+  __nv_bfloat16 *Gs_h = nullptr, *Gs_l = nullptr;   // G(tau),  tc x n x ldn
+  __nv_bfloat16 *Gms_h = nullptr, *Gms_l = nullptr; // G(-tau), tc x n x ldn
+  __nv_bfloat16 *Ys_h = nullptr, *Ys_l = nullptr;   // X^T G(tau),  tc x N x ldn
+  __nv_bfloat16 *Yms_h = nullptr, *Yms_l = nullptr; // X^T G(-tau), tc x N x ldn
+  float *GXf = nullptr, *GXmf = nullptr;            // G^X(+-tau), tc x N x N
+  __nv_bfloat16 *Pis_h = nullptr, *Pis_l = nullptr; // Pi,  tc x N x ldN
+  __nv_bfloat16 *Ts_h = nullptr, *Ts_l = nullptr;   // V Pi, tc x N x ldN
+  __nv_bfloat16 *Ms_h = nullptr, *Ms_l = nullptr;   // merged M, tc x N x ldN
+  __nv_bfloat16 *T2s_h = nullptr, *T2s_l = nullptr; // (M X^T)^T, tc x n x ldN
+  __nv_bfloat16 *Ats_h = nullptr, *Ats_l = nullptr; // A^T blocks, Pb x n x ldn
+  float *Bf = nullptr;                              // B blocks, Pb x N x n
+  double *Dd = nullptr;                             // D, tc x N x N
+  int *d_err = nullptr;                             // device error flag of the tensor-core kernels
+
   std::vector<void*> owned;  // every cudaMalloc of this context
   std::string err;
 
@@ -97,6 +118,13 @@ int fp64_build_U(thc_ctx* ctx);
 int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma);
 int energy_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const double* Sigma,
                 const double* w_host, double* E);
+
+// split-precision path (sigma_split.cu)
+int split_init(thc_ctx* ctx, size_t budget);
+int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma);
+int split_check(thc_ctx* ctx);  // synchronises; THC_ETIMEOUT if a tensor-core wait ran out
+int gemm_bf16x3(cudaStream_t stream, int batch, int M, int N, int K, const double* A, long long sA, const double* B,
+                long long sB, double* C, long long sC);
 
 }  // namespace thc
 

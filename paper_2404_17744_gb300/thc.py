@@ -66,6 +66,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_launch_count.restype = ctypes.c_longlong
     lib.thc_energy_static.argtypes = [i, i, dp, dp, dp, dp, ctypes.POINTER(d), vp]
     lib.thc_energy_static.restype = i
+    lib.thc_sync.argtypes = [vp]
+    lib.thc_sync.restype = i
+    ll = ctypes.c_longlong
+    lib.thc_gemm_bf16x3.argtypes = [i, i, i, i, dp, ll, dp, ll, dp, ll, vp]
+    lib.thc_gemm_bf16x3.restype = i
     lib.thc_destroy.argtypes = [vp]
     lib.thc_destroy.restype = None
     lib.thc_last_error.argtypes = [vp]
@@ -167,6 +172,16 @@ def thc_energy_static(n_ao, n_tau, G_tau, G_bmt, Sigma_tau, tau_weights, stream=
     _check(load_library().thc_energy_static(int(n_ao), int(n_tau), _ptr(G_tau), _ptr(G_bmt), _ptr(Sigma_tau),
                                             _ptr(tau_weights), ctypes.byref(e), s), None)
     return e.value
+
+
+def thc_sync(ctx):
+    _check(load_library().thc_sync(ctx), ctx)
+
+
+def thc_gemm_bf16x3(batch, M, N, K, A, strideA, B, strideB, C, strideC, stream=None):
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(load_library().thc_gemm_bf16x3(int(batch), int(M), int(N), int(K), _ptr(A), int(strideA), _ptr(B),
+                                          int(strideB), _ptr(C), int(strideC), s), None)
 
 
 def thc_destroy(ctx):
