@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="thc200")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-split", action="store_true", help="skip the mixed-precision measurement")
     return p.parse_args()
 
 
@@ -177,6 +178,77 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"bf16": float(d["bf16_tflops"]), "bf16_sustained": float(d["bf16_tflops_sustained"]),
+                "hbm": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"bf16": 1900.0, "bf16_sustained": 1700.0, "hbm": 6800.0, "source": "fallback"}
+
+
+def read_profile(thc, ctx):
+    kernels = {}
+    k = 0
+    while True:
+        r = thc.thc_profile_get(ctx, k)
+        if r is None:
+            break
+        name, nl, ms, fl = r
+        if nl:
+            kernels[name] = {"launches": nl, "ms": ms, "flops": fl,
+                             "tflops": (fl / ms / 1e9) if ms > 0 and fl > 0 else None}
+        k += 1
+    return kernels
+
+
+def measure(args, case, precision, world, dev, stream, X, V, G, S, flush, sampler_on):
+    """Times args.steps Sigma evaluations (+ energy) of one precision mode on `stream`."""
+    import torch
+    from paper_2404_17744_gb300 import thc
+    ctx = thc.thc_sigma_init(case.n, case.N, case.n_tau, case.beta, X, V, case.tau, precision,
+                             thc.THC_DIRECT | thc.THC_SOX, stream.cuda_stream)
+    energies = []
+
+    def step():
+        thc.thc_sigma_eval(ctx, G, None, S)
+        energies.append(thc.thc_energy(ctx, G, None, S, case.tau_w))
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if sampler_on else None
+    thc.thc_profile(ctx, True)
+    launches0 = thc.thc_launch_count(ctx)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for e0, e1 in evs:
+        flush.zero_()                 # L2 flush between timed steps (2x L2 written)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = thc.thc_launch_count(ctx) - launches0
+    clocks = sampler.stop() if sampler else None
+    thc.thc_sync(ctx)
+    kernels = read_profile(thc, ctx)
+    thc.thc_profile(ctx, False)
+    total_ms = float(sum(e0.elapsed_time(e1) for e0, e1 in evs))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return ctx, dict(total_ms=total_ms, kernels=kernels, launches=launches, clocks=clocks,
+                     energy=energies[-1] if energies else None)
+
+
 def run_ours(args):
     import torch
     from paper_2404_17744_gb300 import thc
@@ -191,62 +263,21 @@ def run_ours(args):
     case = synth.make_workload(args.workload)
     stream = torch.cuda.Stream(device=dev)
     flops_step = algorithmic_flops(case.n, case.N, case.n_tau)
+    peaks = measured_peaks()
     with torch.cuda.stream(stream):
         X = torch.from_numpy(case.X).to(dev)
         V = torch.from_numpy(case.V).to(dev)
         G = torch.from_numpy(case.G_tau).to(dev)
         S = torch.empty_like(G)
+        S_split = torch.empty_like(G)
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
         stream.synchronize()
-        ctx = thc.thc_sigma_init(case.n, case.N, case.n_tau, case.beta, X, V, case.tau, thc.THC_FP64,
-                                 thc.THC_DIRECT | thc.THC_SOX, stream.cuda_stream)
+
+        # ---- plain FP64 path (the headline workload)
+        ctx, r64 = measure(args, case, thc.THC_FP64, world, dev, stream, X, V, G, S, flush, rank == 0)
         lib_flops, u_flops = thc.thc_sigma_flops(ctx)
         assert abs(lib_flops - flops_step) < 1e-6 * flops_step
-        energies = []
-
-        def step():
-            thc.thc_sigma_eval(ctx, G, None, S)
-            energies.append(thc.thc_energy(ctx, G, None, S, case.tau_w))
-
-        for _ in range(args.warmup):
-            step()
-        stream.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-        thc.thc_profile(ctx, True)
-        launches0 = thc.thc_launch_count(ctx)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for e0, e1 in evs:
-            flush.zero_()                 # L2 flush between timed steps (2x L2 written)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-        stream.synchronize()
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        launches = thc.thc_launch_count(ctx) - launches0
-        clocks = sampler.stop() if sampler else None
-        ms_steps = [e0.elapsed_time(e1) for e0, e1 in evs]
-        kernels = {}
-        k = 0
-        while True:
-            r = thc.thc_profile_get(ctx, k)
-            if r is None:
-                break
-            name, nl, ms, fl = r
-            if nl:
-                kernels[name] = {"launches": nl, "ms": ms, "tflops": (fl / ms / 1e9) if ms > 0 and fl > 0 else None}
-            k += 1
-        thc.thc_profile(ctx, False)
-        total_ms = float(sum(ms_steps))
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
-        value = world * flops_step * args.steps / (total_ms * 1e-3) / 1e12
+        value = world * flops_step * args.steps / (r64["total_ms"] * 1e-3) / 1e12
 
         # end to end through the host-buffer entry point (H2D of G, D2H of Sigma inside)
         Gh = torch.from_numpy(case.G_tau).pin_memory()
@@ -266,40 +297,67 @@ def run_ours(args):
         e2e_value = world * flops_step * e2e_steps / e2e_dt / 1e12
         thc.thc_destroy(ctx)
 
+        # ---- mixed precision (3 x BF16 on tcgen05), same input; error against the FP64 result
+        split = None
+        if not args.no_split:
+            ctx, rsp = measure(args, case, thc.THC_BF16X3, world, dev, stream, X, V, G, S_split, flush, False)
+            thc.thc_destroy(ctx)
+            stream.synchronize()
+            split = rsp
+            split["value"] = world * flops_step * args.steps / (rsp["total_ms"] * 1e-3) / 1e12
+            split["max_abs_dsigma_vs_fp64"] = float((S_split - S).abs().max().item())
+            split["abs_dE_vs_fp64"] = abs(rsp["energy"] - r64["energy"])
+
     if rank != 0:
         return 0
-    dom = max(kernels.items(), key=lambda kv: kv[1]["ms"] if kv[1]["tflops"] else -1)
-    dom_name, dom_stat = dom
-    per_launch_flops = dom_stat["tflops"] * 1e12 * (dom_stat["ms"] / dom_stat["launches"]) * 1e-3
-    roofline = {
-        "kernel": dom_name, "bound": "alu", "achieved": dom_stat["tflops"], "peak": FP64_PEAK_TFLOPS,
-        "unit": "TFLOP/s", "frac": dom_stat["tflops"] / FP64_PEAK_TFLOPS,
-        "peak_source": "FP64 DFMA nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no measured FP64 peak in "
-                       "MEASURED_PEAKS.json)",
-        "flops_per_launch": per_launch_flops, "ms_per_launch": dom_stat["ms"] / dom_stat["launches"],
-        "traffic": None,
-    }
-    tr = NCU_TRAFFIC.get((dom_name, args.workload))
-    if tr:
-        roofline["traffic"] = tr[0]
-        roofline["traffic_source"] = tr[1]
+
+    def roofline_of(kernels, bound, peak, peak_source, pipe_factor, workload):
+        named = {k: v for k, v in kernels.items() if v["tflops"]}
+        dom_name, st = max(named.items(), key=lambda kv: kv[1]["ms"])
+        achieved = st["tflops"] * pipe_factor
+        r = {"kernel": dom_name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+             "frac": achieved / peak, "peak_source": peak_source,
+             "flops_per_launch": st["flops"] * pipe_factor / st["launches"],
+             "ms_per_launch": st["ms"] / st["launches"], "traffic": None}
+        tr = NCU_TRAFFIC.get((dom_name, workload))
+        if tr:
+            r["traffic"] = tr[0]
+            r["traffic_source"] = tr[1]
+        return r
+
+    roofline = roofline_of(r64["kernels"], "alu", FP64_PEAK_TFLOPS,
+                           "FP64 DFMA nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (MEASURED_PEAKS.json has no "
+                           "FP64 figure)", 1.0, args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": r64["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_desc(case, args.workload), "precision": "fp64", "terms": "direct+sox",
-                   "step": "thc_sigma_eval over all tau + thc_energy", "s_per_sigma_eval": total_ms / args.steps / 1e3,
+                   "step": "thc_sigma_eval over all tau + thc_energy",
+                   "s_per_sigma_eval": r64["total_ms"] / args.steps / 1e3,
                    "fp64_frac_of_peak": value / world / FP64_PEAK_TFLOPS,
-                   "l2": "flushed between timed steps (258 MiB write); U_Pqs (320 MB) exceeds L2",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "E_dyn": energies[-1] if energies else None},
+                   "l2": "flushed between timed steps (258 MiB write); U_Pqs exceeds L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "E_dyn": r64["energy"]},
         "roofline": roofline,
-        "gpu_launches": int(launches),
+        "gpu_launches": int(r64["launches"]),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Gh.numel() * 8),
                 "d2h_bytes_per_step": int(Sh.numel() * 8), "entry": "thc_sigma_eval_host (pinned host buffers)"},
-        "clocks": clocks,
-        "kernels": kernels,
+        "clocks": r64["clocks"],
+        "kernels": {k: {kk: v[kk] for kk in ("launches", "ms", "tflops")} for k, v in r64["kernels"].items()},
     }
+    if split:
+        line["mixed_precision"] = {
+            "precision": "bf16x3 (hi*hi + hi*lo + lo*hi) on tcgen05, FP32 accumulate, FP64 in/out",
+            "value": split["value"], "unit": "TFLOP/s (useful, FP64-equivalent flops)",
+            "ms_per_step": split["total_ms"] / args.steps, "s_per_sigma_eval": split["total_ms"] / args.steps / 1e3,
+            "speedup_vs_fp64": r64["total_ms"] / split["total_ms"],
+            "max_abs_dsigma_vs_fp64": split["max_abs_dsigma_vs_fp64"], "abs_dE_vs_fp64": split["abs_dE_vs_fp64"],
+            "gpu_launches": int(split["launches"]),
+            "roofline": roofline_of(split["kernels"], "tensor", peaks["bf16_sustained"],
+                                    f"BF16 dense sustained, {peaks['source']}; achieved counts the 3 BF16 "
+                                    f"products of every useful multiply-add", 3.0, args.workload + ":bf16x3"),
+            "kernels": {k: {kk: v[kk] for kk in ("launches", "ms", "tflops")} for k, v in split["kernels"].items()},
+        }
     if world == 1 and not args.no_cpu_baseline:
         v, pts, secs = oracle_sample(case)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",

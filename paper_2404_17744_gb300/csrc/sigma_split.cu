@@ -82,128 +82,162 @@ int make_map(thc_ctx* ctx, CUtensorMap* m, const bf16* base, long long K, const 
 }
 
 // ------------------------------------------------------------ epilogues
+// Each functor is run by one warp on a 32 x 32 chunk of the output tile:
+// tile[r][j] = C[row0 + r][col0 + j]; rows >= M and columns >= N are skipped.
+using Tile = float (*)[33];
+
+// Functors without global reads in their epilogue prefetch nothing.
+#define THC_NO_PREFETCH \
+  __device__ void prefetch(int, int, int, int, int, int) const {}
+
 __device__ __forceinline__ void split_store(bf16* hi, bf16* lo, long long o, float v) {
   const bf16 h = __float2bfloat16_rn(v);
   hi[o] = h;
   lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// dst(b, row, col) = scale * C, split, row-major (or transposed: dst(b, col, row)).
+// dst(b, row, col) = scale * C, split; row-major, or transposed dst(b, col, row).
 template <bool TRANSPOSED>
 struct EpiSplit {
+  THC_NO_PREFETCH
   bf16 *hi, *lo;
   long long ld, bs;
   float scale;
-  __device__ void operator()(int b, int row, int col0, const float* v, int M, int N) const {
-    if (row >= M) return;
-    const int cn = min(32, N - col0);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j >= cn) break;
-      const long long o = TRANSPOSED ? (long long)b * bs + (long long)(col0 + j) * ld + row
-                                     : (long long)b * bs + (long long)row * ld + col0 + j;
-      split_store(hi, lo, o, scale * v[j]);
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N) const {
+    if (TRANSPOSED) {  // lanes along rows: dst(b, col, row) is contiguous in row
+      const int row = row0 + lane;
+      if (row >= M) return;
+#pragma unroll 4
+      for (int j = 0; j < 32; ++j)
+        if (col0 + j < N) split_store(hi, lo, (long long)b * bs + (long long)(col0 + j) * ld + row, scale * t[lane][j]);
+    } else {           // lanes along columns
+      const int col = col0 + lane;
+      if (col >= N) return;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r)
+        if (row0 + r < M) split_store(hi, lo, (long long)b * bs + (long long)(row0 + r) * ld + col, scale * t[r][lane]);
     }
   }
 };
 
-// A^T blocks: row = P n + q (P local to the block), col = v  ->  At[P][v][q], split.
+// A^T blocks: row = P n + q (P local to the block), col = v  ->  At[P][v][q], split (lanes along q).
 struct EpiAt {
+  THC_NO_PREFETCH
   bf16 *hi, *lo;
   int n;
   long long ld;
-  __device__ void operator()(int, int row, int col0, const float* v, int M, int N) const {
+  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int N) const {
+    const int row = row0 + lane;
     if (row >= M) return;
     const int P = row / n, q = row - P * n;
-    const int cn = min(32, N - col0);
     const long long base = (long long)P * n * ld + q;
-#pragma unroll
+#pragma unroll 4
     for (int j = 0; j < 32; ++j)
-      if (j < cn) split_store(hi, lo, base + (long long)(col0 + j) * ld, v[j]);
+      if (col0 + j < N) split_store(hi, lo, base + (long long)(col0 + j) * ld, t[lane][j]);
   }
 };
 
-// FP32 store: dst[b * bs + row * ld + col].
+// FP32 store: dst[b * bs + row * ld + col] (lanes along columns).
 struct EpiF32 {
+  THC_NO_PREFETCH
   float* dst;
   long long ld, bs;
-  __device__ void operator()(int b, int row, int col0, const float* v, int M, int N) const {
-    if (row >= M) return;
-    const int cn = min(32, N - col0);
-    float* d = dst + (long long)b * bs + (long long)row * ld + col0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (j < cn) d[j] = v[j];
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N) const {
+    const int col = col0 + lane;
+    if (col >= N) return;
+    float* d = dst + (long long)b * bs + col;
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r)
+      if (row0 + r < M) d[(long long)(row0 + r) * ld] = t[r][lane];
   }
 };
 
-// FP64 store: dst[b * bs + row * ld + col].
+// FP64 store: dst[b * bs + row * ld + col] (lanes along columns).
 struct EpiF64 {
+  THC_NO_PREFETCH
   double* dst;
   long long ld, bs;
-  __device__ void operator()(int b, int row, int col0, const float* v, int M, int N) const {
-    if (row >= M) return;
-    const int cn = min(32, N - col0);
-    double* d = dst + (long long)b * bs + (long long)row * ld + col0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (j < cn) d[j] = (double)v[j];
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N) const {
+    const int col = col0 + lane;
+    if (col >= N) return;
+    double* d = dst + (long long)b * bs + col;
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r)
+      if (row0 + r < M) d[(long long)(row0 + r) * ld] = (double)t[r][lane];
   }
 };
 
 // Hadamard-reduce of the fused C/D step: b = R, row = P (local), col = v.
 //   D[(P0 + P) N + R] += sum_v C[P][v] B[P][R][v]
+// The epilogue warps prefetch their B rows into L2 while the tile is being
+// accumulated; the chunk is then multiplied in place by B (32 coalesced loads
+// in flight per lane) and lane r sums row r into one FP64 atomic.
 struct EpiHad {
   const float* Bf;  // Pb x N x n
   double* D;
   int n, N, P0;
-  __device__ void operator()(int b, int row, int col0, const float* v, int M, int Ncols) const {
-    if (row >= M) return;
-    const int cn = min(32, Ncols - col0);
-    const float* bp = Bf + ((long long)row * N + b) * n + col0;
-    float acc = 0.f;
+  __device__ void prefetch(int b, int row, int col0, int ncols, int M, int Ncols) const {
+    if (row >= M || col0 >= Ncols) return;
+    const float* p = Bf + ((long long)row * N + b) * n + col0;
+    const int cnt = min(ncols, Ncols - col0);
+    for (int c = 0; c < cnt; c += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + c));
+  }
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols) const {
+    const int col = col0 + lane;
+    float bv[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (j < cn) acc = fmaf(v[j], bp[j], acc);
-    atomicAdd(&D[((long long)P0 + row) * N + b], (double)acc);
+    for (int r = 0; r < 32; ++r) {
+      const int P = row0 + r;
+      bv[r] = (P < M && col < Ncols) ? __ldg(Bf + ((long long)P * N + b) * n + col) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) t[r][lane] *= bv[r];
+    __syncwarp();
+    float sum = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sum += t[lane][j];
+    if (row0 + lane < M) atomicAdd(&D[((long long)P0 + row0 + lane) * N + b], (double)sum);
   }
 };
 
-// Merge epilogue of W = T V: M[b][R][P] = c_x D[b][P][R] + c_d G^X[b][R][P] W, split.
+// Merge epilogue of W = T V: M[b][R][P] = c_x D[b][P][R] + c_d G^X[b][R][P] W, split (lanes along P).
 struct EpiMerge {
+  THC_NO_PREFETCH
   bf16 *hi, *lo;
   long long ld;
   const double* D;  // may be null
   const float* GX;
   int N;
-  __device__ void operator()(int b, int row, int col0, const float* v, int M, int Ncols) const {
-    if (row >= M) return;
-    const int cn = min(32, Ncols - col0);
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols) const {
+    const int P = col0 + lane;
+    if (P >= Ncols) return;
     const long long NN = (long long)N * N;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j >= cn) break;
-      const int P = col0 + j;
-      double m = C_DIRECT * (double)GX[b * NN + (long long)row * N + P] * (double)v[j];
-      if (D) m += C_SOX * D[b * NN + (long long)P * N + row];
-      split_store(hi, lo, (long long)b * N * ld + (long long)row * ld + P, (float)m);
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+      const int R = row0 + r;
+      if (R >= M) break;
+      double m = C_DIRECT * (double)GX[b * NN + (long long)R * N + P] * (double)t[r][lane];
+      if (D) m += C_SOX * D[b * NN + (long long)P * N + R];
+      split_store(hi, lo, (long long)b * N * ld + (long long)R * ld + P, (float)m);
     }
   }
 };
 
-// U build: row = P, col = (q - q0) n + s  ->  U[(P n + q) ld + s], split.
+// U build: row = P, col = (q - q0) n + s  ->  U[(P n + q) ld + s], split (lanes along s).
 struct EpiU {
+  THC_NO_PREFETCH
   bf16 *hi, *lo;
   int n, q0;
   long long ld;
-  __device__ void operator()(int, int row, int col0, const float* v, int M, int Ncols) const {
-    if (row >= M) return;
-    const int cn = min(32, Ncols - col0);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j >= cn) break;
-      const int c = col0 + j, q = q0 + c / n, s = c - (c / n) * n;
-      split_store(hi, lo, ((long long)row * n + q) * ld + s, v[j]);
+  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int Ncols) const {
+    const int c = col0 + lane;
+    if (c >= Ncols) return;
+    const int q = q0 + c / n, s = c - (c / n) * n;
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+      const int P = row0 + r;
+      if (P >= M) break;
+      split_store(hi, lo, ((long long)P * n + q) * ld + s, t[r][lane]);
     }
   }
 };

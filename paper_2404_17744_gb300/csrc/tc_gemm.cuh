@@ -18,8 +18,9 @@
 //             the stage back to the producer and to the epilogue;
 //   warps 2-9 drain each finished stage accumulator with tcgen05.ld into FP32
 //             registers (warp w owns TMEM lanes 32 (w % 4) .. and one half of
-//             the columns), free it for the stage after next, and finally run
-//             the epilogue functor on 32 columns at a time.
+//             the columns), free it for the stage after next, and finally hand
+//             32 x 32 chunks, staged in shared memory, to the epilogue functor,
+//             which the whole warp runs with coalesced global accesses.
 // Draining every stage ("promotion") keeps the tensor core's internal
 // accumulation to one 64-deep stage: measured on GB300, accumulating a
 // 1000-deep K inside the tensor core loses several times more precision than
@@ -266,6 +267,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float acc[C::HALF];
 #pragma unroll
     for (int i = 0; i < C::HALF; ++i) acc[i] = 0.f;
+    // warm L2 with whatever the epilogue will read while the tile accumulates
+    epi.prefetch(b, m0 + quarter * 32 + lane, n0 + half * C::HALF, C::HALF, M, N);
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
       const int buf = kb & 1, use = kb >> 1;
@@ -281,11 +284,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_arrive(&acc_free[buf]);
     }
     if (ok) {
-      const int row = m0 + quarter * 32 + lane;
+      // Every MMA has completed (the last acc_full wait), so the stage ring is
+      // free: each epilogue warp stages 32 x 32 chunks of its accumulators
+      // there and the functor walks them with lanes along the destination's
+      // contiguous dimension (coalesced global accesses).
+      float(*tile)[33] = reinterpret_cast<float(*)[33]>(smem + (warp - 2) * (32 * 33 * 4));
+      const int row0 = m0 + quarter * 32;
 #pragma unroll
       for (int c = 0; c < C::HALF; c += 32) {
-        const int col = n0 + half * C::HALF + c;
-        if (col < N) epi(b, row, col, acc + c, M, N);
+        const int col0 = n0 + half * C::HALF + c;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tile[lane][j] = acc[c + j];
+        __syncwarp();
+        if (col0 < N) epi(b, row0, col0, tile, lane, M, N);
+        __syncwarp();
       }
     }
   }
