@@ -1,0 +1,503 @@
+// Dyson step of the self-consistency loop on the GPU, in FP64 (Sec. II.A,
+// Eq. Dyson in a non-orthogonal AO basis):
+//
+//   Sigma(tau_k) --fit--> sigma_l --> Sigma(i w_m)
+//   G(i w_m) = [(i w_m + mu) S - F - Sigma(i w_m)]^{-1}      for every sampled w_m
+//   mu such that the electron count per spin Tr[gamma S] = n_elec,
+//       gamma = -G(beta^-) = -sum_l u_l(beta) g_l
+//   G(i w_m) --fit--> g_l --> G(tau_k)
+//
+// The tau <-> i w transforms are the sparse-sampling matrices of an IR basis
+// (supplied by the caller); they run in the DFMA contraction tile.  The
+// inversions are an in-place Gauss-Jordan elimination, one CTA per
+// frequency: Im[(i w + mu) S - F - Sigma(i w)] = w S - Im Sigma(i w) is
+// definite for a causal self-energy, so every leading principal minor is
+// non-singular and no pivoting is needed.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "dfma_tile.cuh"
+#include "thc_internal.cuh"
+#include "thc_dyson.h"
+
+struct thc_dyson {
+  int n = 0, n_tau = 0, n_iw = 0, L = 0;
+  double beta = 0.0;
+  cudaStream_t stream = nullptr;
+  std::vector<double> iw;          // host copy of the frequencies
+  std::vector<double> cre, cim;    // c_m = sum_l u_l(beta) fit_iw[l, m]
+  std::vector<double> parity;      // p_l = u_l(0) / u_l(beta) (+-1)
+  std::vector<double> ubeta;
+  // device
+  double *S = nullptr, *F = nullptr;
+  double *U_tau = nullptr, *fit_tau = nullptr;          // n_tau x L, L x n_tau
+  double *Uiw_re = nullptr, *Uiw_im = nullptr;          // n_iw x L
+  double *fit_re = nullptr, *fit_im = nullptr;          // L x n_iw
+  double *ubeta_d = nullptr, *parity_d = nullptr;       // L
+  double *sig_l = nullptr;                              // L x n^2
+  double *Siw = nullptr;                                // n_iw x n^2 x 2 (interleaved complex)
+  double *Giw = nullptr;                                // n_iw x n^2 x 2
+  double *g_l = nullptr;                                // L x n^2 (real part)
+  double *tr = nullptr;                                 // n_iw x 2 partial traces
+  double *scal = nullptr;                               // small scalar scratch
+  int evals = 0;                                        // N(mu) evaluations of the last solve
+  std::vector<void*> owned;
+  std::string err;
+};
+
+namespace {
+
+using thc::f64::BM;
+using thc::f64::BN;
+using thc::f64::NT;
+using thc::f64::View;
+
+int dfail(thc_dyson* d, int code, const std::string& msg) {
+  if (d) d->err = msg;
+  return thc::fail(nullptr, code, msg);
+}
+
+int dcheck(thc_dyson* d, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return THC_OK;
+  return dfail(d, e == cudaErrorMemoryAllocation ? THC_ENOMEM : THC_ECUDA,
+               std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int dalloc(thc_dyson* d, double** p, size_t count, const char* what) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(double) * std::max<size_t>(count, 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return dfail(d, THC_ENOMEM, std::string("cudaMalloc ") + what);
+  }
+  d->owned.push_back(*p);
+  return THC_OK;
+}
+
+// C(b) (+)= alpha * A(b) B(b) in the DFMA tile.
+struct AccEpi {
+  double* p;
+  long long sb, sr, sc;
+  double alpha;
+  bool accumulate;
+  __device__ __forceinline__ void operator()(long long b, long long m, long long c, double v) const {
+    double* q = p + b * sb + m * sr + c * sc;
+    *q = accumulate ? fma(alpha, v, *q) : alpha * v;
+  }
+};
+
+template <bool AK, bool BK_>
+int gemm(thc_dyson* d, long long M, long long Nn, long long K, const View& a, const View& b, const AccEpi& e,
+         const char* what) {
+  const dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((Nn + BN - 1) / BN), 1);
+  thc::f64::gemm_kernel<AK, BK_><<<grid, NT, 0, d->stream>>>(M, Nn, K, a, b, e);
+  return dcheck(d, cudaGetLastError(), what);
+}
+
+// A_m = (i w_m + mu) S - F - Sigma(i w_m), interleaved complex.
+__global__ void build_kernel(int n, int n_iw, const double* __restrict__ iw, double mu, const double* __restrict__ S,
+                             const double* __restrict__ F, const double* __restrict__ Siw, double* __restrict__ A) {
+  const long long nn = (long long)n * n, total = nn * n_iw;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long m = i / nn, e = i - m * nn;
+    const double s = S[e];
+    A[2 * i] = mu * s - F[e] - Siw[2 * i];
+    A[2 * i + 1] = iw[m] * s - Siw[2 * i + 1];
+  }
+}
+
+// In-place Gauss-Jordan inverse of the n x n complex matrix of this CTA (no pivoting).
+// Row k and column k of the current step are staged in shared memory.
+__global__ void __launch_bounds__(1024) gj_invert_kernel(int n, double2* __restrict__ A0) {
+  extern __shared__ double2 sh[];
+  double2* rowk = sh;      // n
+  double2* colk = sh + n;  // n
+  double2* A = A0 + (long long)blockIdx.x * n * n;
+  const long long nn = (long long)n * n;
+  for (int k = 0; k < n; ++k) {
+    // pivot reciprocal and the scaled pivot row (the pivot entry becomes 1/p)
+    const double2 p = A[(long long)k * n + k];
+    const double den = p.x * p.x + p.y * p.y;
+    const double2 ip = make_double2(p.x / den, -p.y / den);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double2 a = (j == k) ? make_double2(1.0, 0.0) : A[(long long)k * n + j];
+      rowk[j] = make_double2(a.x * ip.x - a.y * ip.y, a.x * ip.y + a.y * ip.x);
+      colk[j] = A[(long long)j * n + k];
+    }
+    __syncthreads();
+    for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int i = (int)(e / n), j = (int)(e - (long long)i * n);
+      if (i == k) {
+        A[e] = rowk[j];
+      } else {
+        const double2 f = colk[i], r = rowk[j];
+        double2 a = (j == k) ? make_double2(0.0, 0.0) : A[e];
+        a.x -= f.x * r.x - f.y * r.y;
+        a.y -= f.x * r.y + f.y * r.x;
+        A[e] = a;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// t_m = Tr[G_m S] = sum_ij G_m[i][j] S[j][i] (complex), one CTA per m.
+__global__ void trace_gs_kernel(int n, const double2* __restrict__ G, const double* __restrict__ S,
+                                double* __restrict__ t) {
+  const long long m = blockIdx.x, nn = (long long)n * n;
+  const double2* g = G + m * nn;
+  double re = 0.0, im = 0.0;
+  for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+    const long long i = e / n, j = e - i * n;
+    const double s = S[j * n + i];
+    re = fma(g[e].x, s, re);
+    im = fma(g[e].y, s, im);
+  }
+  __shared__ double r1[32], r2[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = re;
+    r2[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    re = threadIdx.x < (blockDim.x >> 5) ? r1[threadIdx.x] : 0.0;
+    im = threadIdx.x < (blockDim.x >> 5) ? r2[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (threadIdx.x == 0) {
+      t[2 * m] = re;
+      t[2 * m + 1] = im;
+    }
+  }
+}
+
+// out[0] = sum_l p_l sum_ij a_l[i][j] b_l[j][i]; out[1] = sum_l ub_l sum_ij a_l[i][j] M[j][i]; one CTA.
+__global__ void coef_contract_kernel(int n, int L, const double* __restrict__ a, const double* __restrict__ b,
+                                     const double* __restrict__ p, const double* __restrict__ ub,
+                                     const double* __restrict__ M, double* __restrict__ out) {
+  const long long nn = (long long)n * n;
+  double s1 = 0.0, s2 = 0.0;
+  for (long long e = threadIdx.x; e < nn * L; e += blockDim.x) {
+    const long long l = e / nn, r = e - l * nn, i = r / n, j = r - i * n;
+    const double av = a[e];
+    s1 = fma(p[l] * av, b[l * nn + j * n + i], s1);
+    if (M) s2 = fma(ub[l] * av, M[j * n + i], s2);
+  }
+  __shared__ double r1[32], r2[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = s1;
+    r2[threadIdx.x >> 5] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s1 = threadIdx.x < (blockDim.x >> 5) ? r1[threadIdx.x] : 0.0;
+    s2 = threadIdx.x < (blockDim.x >> 5) ? r2[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (threadIdx.x == 0) {
+      out[0] = s1;
+      out[1] = s2;
+    }
+  }
+}
+
+int blocks_for(long long total) { return (int)std::min<long long>((total + 255) / 256, 152LL * 32); }
+
+// sigma_l = fit_tau Sigma(tau);  Sigma(i w) = U_iw sigma_l  (interleaved complex)
+int sigma_to_iw(thc_dyson* d, const double* Sig_tau) {
+  const long long n2 = (long long)d->n * d->n, L = d->L, nt = d->n_tau, nw = d->n_iw;
+  THC_TRY(gemm<true, false>(d, L, n2, nt, View{d->fit_tau, 0, nt, 1}, View{Sig_tau, 0, n2, 1},
+                            AccEpi{d->sig_l, 0, n2, 1, 1.0, false}, "sigma_l"));
+  THC_TRY(gemm<true, false>(d, nw, n2, L, View{d->Uiw_re, 0, L, 1}, View{d->sig_l, 0, n2, 1},
+                            AccEpi{d->Siw, 0, 2 * n2, 2, 1.0, false}, "Sigma(iw) re"));
+  return gemm<true, false>(d, nw, n2, L, View{d->Uiw_im, 0, L, 1}, View{d->sig_l, 0, n2, 1},
+                           AccEpi{d->Siw + 1, 0, 2 * n2, 2, 1.0, false}, "Sigma(iw) im");
+}
+
+// G(i w_m) for all m at chemical potential mu; returns the electron count per spin.
+int dyson_at(thc_dyson* d, double mu, double* n_out) {
+  const long long n = d->n, nn = n * n, nw = d->n_iw;
+  double* iw_d = d->scal + 8;  // frequencies live after 8 scalar slots
+  build_kernel<<<blocks_for(nn * nw), 256, 0, d->stream>>>((int)n, (int)nw, iw_d, mu, d->S, d->F, d->Siw, d->Giw);
+  THC_TRY(dcheck(d, cudaGetLastError(), "Dyson matrices"));
+  const size_t shm = 2 * sizeof(double2) * n;
+  gj_invert_kernel<<<(unsigned)nw, 1024, shm, d->stream>>>((int)n, reinterpret_cast<double2*>(d->Giw));
+  THC_TRY(dcheck(d, cudaGetLastError(), "Gauss-Jordan"));
+  trace_gs_kernel<<<(unsigned)nw, 256, 0, d->stream>>>((int)n, reinterpret_cast<const double2*>(d->Giw), d->S, d->tr);
+  THC_TRY(dcheck(d, cudaGetLastError(), "Tr[G S]"));
+  std::vector<double> t(2 * nw);
+  THC_TRY(dcheck(d, cudaMemcpyAsync(t.data(), d->tr, sizeof(double) * 2 * nw, cudaMemcpyDeviceToHost, d->stream),
+                 "copy traces"));
+  THC_TRY(dcheck(d, cudaStreamSynchronize(d->stream), "Dyson sync"));
+  // Tr[gamma S] = -Re sum_m c_m t_m
+  double acc = 0.0;
+  for (long long m = 0; m < nw; ++m) acc += d->cre[m] * t[2 * m] - d->cim[m] * t[2 * m + 1];
+  *n_out = -acc;
+  d->evals += 1;
+  return THC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int thc_dyson_init(thc_dyson** out, int n_ao, int n_tau, int n_iw, int n_l, double beta, const double* S,
+                   const double* F, const double* U_tau, const double* fit_tau, const double* U_iw,
+                   const double* fit_iw, const double* iw, const double* u_beta, const double* u_zero, void* stream) {
+  if (!out) return thc::fail(nullptr, THC_EINVAL, "thc_dyson_init: NULL out-pointer");
+  *out = nullptr;
+  if (n_ao < 1 || n_tau < 1 || n_iw < 1 || n_l < 1 || !(beta > 0))
+    return thc::fail(nullptr, THC_EINVAL, "thc_dyson_init: sizes must be >= 1 and beta > 0");
+  if (n_ao > 1500) return thc::fail(nullptr, THC_EINVAL, "thc_dyson_init: n_ao above 1500 is not supported");
+  if (!S || !F || !U_tau || !fit_tau || !U_iw || !fit_iw || !iw || !u_beta || !u_zero)
+    return thc::fail(nullptr, THC_EINVAL, "thc_dyson_init: NULL argument");
+  thc_dyson* d = new (std::nothrow) thc_dyson();
+  if (!d) return thc::fail(nullptr, THC_ENOMEM, "thc_dyson_init: host allocation");
+  d->n = n_ao;
+  d->n_tau = n_tau;
+  d->n_iw = n_iw;
+  d->L = n_l;
+  d->beta = beta;
+  d->stream = (cudaStream_t)stream;
+  auto bail = [&](int rc) {
+    for (void* p : d->owned) cudaFree(p);
+    delete d;
+    return rc;
+  };
+  const size_t n2 = (size_t)n_ao * n_ao, L = n_l;
+  // host-side constants of the transforms
+  d->iw.assign(iw, iw + n_iw);
+  d->ubeta.assign(u_beta, u_beta + L);
+  d->parity.resize(L);
+  for (size_t l = 0; l < L; ++l) d->parity[l] = (u_zero[l] * u_beta[l] >= 0.0) ? 1.0 : -1.0;
+  d->cre.assign(n_iw, 0.0);
+  d->cim.assign(n_iw, 0.0);
+  for (int m = 0; m < n_iw; ++m)
+    for (size_t l = 0; l < L; ++l) {
+      d->cre[m] += u_beta[l] * fit_iw[2 * (l * n_iw + m)];
+      d->cim[m] += u_beta[l] * fit_iw[2 * (l * n_iw + m) + 1];
+    }
+  std::vector<double> a(n_iw * L), b(n_iw * L), c(L * n_iw), e(L * n_iw);
+  for (size_t i = 0; i < (size_t)n_iw * L; ++i) {
+    a[i] = U_iw[2 * i];
+    b[i] = U_iw[2 * i + 1];
+    c[i] = fit_iw[2 * i];
+    e[i] = fit_iw[2 * i + 1];
+  }
+  int rc = THC_OK;
+  auto up = [&](double** dst, const double* src, size_t cnt, const char* what) {
+    if (rc != THC_OK) return;
+    rc = dalloc(d, dst, cnt, what);
+    if (rc == THC_OK) rc = dcheck(d, cudaMemcpyAsync(*dst, src, sizeof(double) * cnt, cudaMemcpyDefault, d->stream), what);
+  };
+  up(&d->S, S, n2, "S");
+  up(&d->F, F, n2, "F");
+  up(&d->U_tau, U_tau, (size_t)n_tau * L, "U_tau");
+  up(&d->fit_tau, fit_tau, L * n_tau, "fit_tau");
+  up(&d->Uiw_re, a.data(), a.size(), "U_iw re");
+  up(&d->Uiw_im, b.data(), b.size(), "U_iw im");
+  up(&d->fit_re, c.data(), c.size(), "fit_iw re");
+  up(&d->fit_im, e.data(), e.size(), "fit_iw im");
+  up(&d->ubeta_d, d->ubeta.data(), L, "u(beta)");
+  up(&d->parity_d, d->parity.data(), L, "parity");
+  if (rc == THC_OK) rc = dalloc(d, &d->sig_l, L * n2, "sigma_l");
+  if (rc == THC_OK) rc = dalloc(d, &d->g_l, L * n2, "g_l");
+  if (rc == THC_OK) rc = dalloc(d, &d->Siw, 2 * n2 * n_iw, "Sigma(iw)");
+  if (rc == THC_OK) rc = dalloc(d, &d->Giw, 2 * n2 * n_iw, "G(iw)");
+  if (rc == THC_OK) rc = dalloc(d, &d->tr, 2 * (size_t)n_iw, "traces");
+  if (rc == THC_OK) rc = dalloc(d, &d->scal, 8 + (size_t)n_iw, "scalars");
+  if (rc == THC_OK)
+    rc = dcheck(d, cudaMemcpyAsync(d->scal + 8, iw, sizeof(double) * n_iw, cudaMemcpyDefault, d->stream), "iw");
+  if (rc == THC_OK) rc = dcheck(d, cudaStreamSynchronize(d->stream), "dyson init sync");
+  if (rc != THC_OK) return bail(rc);
+  *out = d;
+  return THC_OK;
+}
+
+int thc_dyson_solve(thc_dyson* d, const double* Sigma_tau, double n_elec, double* mu, double tol, double* G_tau) {
+  if (!d) return thc::fail(nullptr, THC_EINVAL, "thc_dyson_solve: NULL context");
+  if (!mu || !G_tau) return dfail(d, THC_EINVAL, "thc_dyson_solve: NULL argument");
+  const long long n2 = (long long)d->n * d->n, L = d->L, nt = d->n_tau, nw = d->n_iw;
+  d->evals = 0;
+  if (Sigma_tau) {
+    THC_TRY(sigma_to_iw(d, Sigma_tau));
+  } else {
+    THC_TRY(dcheck(d, cudaMemsetAsync(d->Siw, 0, sizeof(double) * 2 * n2 * nw, d->stream), "zero Sigma"));
+  }
+  if (!(tol > 0)) tol = 1e-10;
+  // N(mu) is increasing: bracket the target, then secant steps safeguarded by bisection
+  double m0 = *mu, n0 = 0.0;
+  THC_TRY(dyson_at(d, m0, &n0));
+  double lo, hi, nlo, nhi;
+  double step = 0.25;
+  if (std::fabs(n0 - n_elec) <= tol) {
+    lo = hi = m0;
+    nlo = nhi = n0;
+  } else if (n0 < n_elec) {
+    lo = m0, nlo = n0;
+    hi = m0 + step;
+    THC_TRY(dyson_at(d, hi, &nhi));
+    while (nhi < n_elec && d->evals < 60) {
+      lo = hi, nlo = nhi, step *= 2, hi += step;
+      THC_TRY(dyson_at(d, hi, &nhi));
+    }
+  } else {
+    hi = m0, nhi = n0;
+    lo = m0 - step;
+    THC_TRY(dyson_at(d, lo, &nlo));
+    while (nlo > n_elec && d->evals < 60) {
+      hi = lo, nhi = nlo, step *= 2, lo -= step;
+      THC_TRY(dyson_at(d, lo, &nlo));
+    }
+  }
+  double m = lo, nm = nlo;
+  if (lo != hi) {
+    for (int it = 0; it < 100; ++it) {
+      double x = lo + (n_elec - nlo) * (hi - lo) / (nhi - nlo);  // secant in the bracket
+      if (!(x > lo && x < hi) || it % 3 == 2) x = 0.5 * (lo + hi);
+      THC_TRY(dyson_at(d, x, &nm));
+      m = x;
+      if (std::fabs(nm - n_elec) <= tol || hi - lo < 1e-15) break;
+      if (nm < n_elec) lo = x, nlo = nm;
+      else hi = x, nhi = nm;
+    }
+  }
+  if (std::fabs(nm - n_elec) > 1e3 * tol)
+    return dfail(d, THC_EINVAL, "thc_dyson_solve: chemical potential search did not converge");
+  *mu = m;
+  // g_l = Re[fit_iw G(iw)] ;  G(tau) = U_tau g
+  THC_TRY(gemm<true, false>(d, L, n2, nw, View{d->fit_re, 0, nw, 1}, View{d->Giw, 0, 2 * n2, 2},
+                            AccEpi{d->g_l, 0, n2, 1, 1.0, false}, "g_l re"));
+  THC_TRY(gemm<true, false>(d, L, n2, nw, View{d->fit_im, 0, nw, 1}, View{d->Giw + 1, 0, 2 * n2, 2},
+                            AccEpi{d->g_l, 0, n2, 1, -1.0, true}, "g_l im"));
+  THC_TRY(gemm<true, false>(d, nt, n2, L, View{d->U_tau, 0, L, 1}, View{d->g_l, 0, n2, 1},
+                            AccEpi{G_tau, 0, n2, 1, 1.0, false}, "G(tau)"));
+  return dcheck(d, cudaStreamSynchronize(d->stream), "dyson solve sync");
+}
+
+int thc_dyson_energy(thc_dyson* d, const double* G_tau, const double* Sigma_tau, double* E_dyn, double* gamma_F,
+                     double* n_per_spin) {
+  if (!d) return thc::fail(nullptr, THC_EINVAL, "thc_dyson_energy: NULL context");
+  if (!G_tau || !Sigma_tau || !E_dyn) return dfail(d, THC_EINVAL, "thc_dyson_energy: NULL argument");
+  const long long n2 = (long long)d->n * d->n, L = d->L, nt = d->n_tau;
+  // coefficients of G and Sigma
+  THC_TRY(gemm<true, false>(d, L, n2, nt, View{d->fit_tau, 0, nt, 1}, View{G_tau, 0, n2, 1},
+                            AccEpi{d->g_l, 0, n2, 1, 1.0, false}, "g_l"));
+  THC_TRY(gemm<true, false>(d, L, n2, nt, View{d->fit_tau, 0, nt, 1}, View{Sigma_tau, 0, n2, 1},
+                            AccEpi{d->sig_l, 0, n2, 1, 1.0, false}, "sigma_l"));
+  // E_dyn = -int Tr[G(beta - tau) Sigma(tau)] = -sum_l p_l Tr[g_l sigma_l];  Tr[G(beta^-) F], Tr[G(beta^-) S]
+  double h[4];
+  coef_contract_kernel<<<1, 1024, 0, d->stream>>>((int)d->n, (int)L, d->g_l, d->sig_l, d->parity_d, d->ubeta_d, d->F,
+                                                  d->scal);
+  THC_TRY(dcheck(d, cudaGetLastError(), "energy contraction"));
+  coef_contract_kernel<<<1, 1024, 0, d->stream>>>((int)d->n, (int)L, d->g_l, d->sig_l, d->parity_d, d->ubeta_d, d->S,
+                                                  d->scal + 2);
+  THC_TRY(dcheck(d, cudaGetLastError(), "count contraction"));
+  THC_TRY(dcheck(d, cudaMemcpyAsync(h, d->scal, sizeof(double) * 4, cudaMemcpyDeviceToHost, d->stream), "copy"));
+  THC_TRY(dcheck(d, cudaStreamSynchronize(d->stream), "energy sync"));
+  *E_dyn = -h[0];
+  if (gamma_F) *gamma_F = -h[1];     // Tr[gamma F], gamma = -G(beta^-)
+  if (n_per_spin) *n_per_spin = -h[3];
+  return THC_OK;
+}
+
+int thc_dyson_evals(const thc_dyson* d) { return d ? d->evals : 0; }
+
+// ---------------------------------------------------------- vector utilities
+namespace {
+constexpr int kDotBlocks = 256;
+
+// partial[b] = sum over the grid-stride slice of block b (fixed order), then one block sums them.
+__global__ void dot_partial_kernel(long long len, const double* __restrict__ x, const double* __restrict__ y,
+                                   double* __restrict__ part) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    acc = fma(x[i], y[i], acc);
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  }
+}
+
+__global__ void sum_kernel(int cnt, const double* __restrict__ part, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < cnt; i += 32) acc += part[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x == 0) out[0] = acc;
+}
+
+struct VecList {
+  const double* p[16];
+  double c[16];
+  int k;
+};
+
+__global__ void lincomb_kernel(long long len, VecList v, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < v.k; ++j) acc = fma(v.c[j], v.p[j][i], acc);
+    out[i] = acc;
+  }
+}
+}  // namespace
+
+int thc_vec_dot(long long len, const double* x, const double* y, double* scratch, double* out, void* stream) {
+  if (len < 0 || !x || !y || !scratch || !out) return thc::fail(nullptr, THC_EINVAL, "thc_vec_dot: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(len, x, y, scratch);
+  sum_kernel<<<1, 32, 0, s>>>(kDotBlocks, scratch, scratch + kDotBlocks);
+  double h = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&h, scratch + kDotBlocks, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return thc::check_cuda(nullptr, e, "thc_vec_dot");
+  *out = h;
+  return THC_OK;
+}
+
+int thc_vec_lincomb(int k, const double* coeffs, const double* const* vecs, long long len, double* out, void* stream) {
+  if (k < 1 || k > 16 || len < 0 || !coeffs || !vecs || !out)
+    return thc::fail(nullptr, THC_EINVAL, "thc_vec_lincomb: need 1 <= k <= 16 and non-NULL arguments");
+  VecList v;
+  v.k = k;
+  for (int j = 0; j < k; ++j) {
+    if (!vecs[j]) return thc::fail(nullptr, THC_EINVAL, "thc_vec_lincomb: NULL vector");
+    v.p[j] = vecs[j];
+    v.c[j] = coeffs[j];
+  }
+  lincomb_kernel<<<(int)std::min<long long>((len + 255) / 256, 152LL * 16), 256, 0, (cudaStream_t)stream>>>(len, v,
+                                                                                                           out);
+  return thc::check_cuda(nullptr, cudaGetLastError(), "thc_vec_lincomb");
+}
+
+const char* thc_dyson_last_error(const thc_dyson* d) { return d ? d->err.c_str() : ""; }
+
+void thc_dyson_destroy(thc_dyson* d) {
+  if (!d) return;
+  if (d->stream) cudaStreamSynchronize(d->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : d->owned) cudaFree(p);
+  delete d;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+"""Pins of the IR basis (an input built in workloads.ir) and of the oracle's
+self-consistent loop (oracle/scf_oracle.py), against facts that do not come
+from the code under test:
+
+* single-pole functions: G(tau) = -e^{-e tau}/(1 + e^{-beta e}) has the exact
+  transform 1/(i w_n - e); the basis must reproduce both;
+* Dyson with Sigma = 0 gives the analytic noninteracting G; G(0+) + G(beta-) = -S^{-1};
+* the IR-coefficient energy of Sigma[G0] at G0 equals the finite-temperature
+  MP2 closed form; the Matsubara-sum route (Eq. E2b) equals the tau route;
+* the converged loop energy does not depend on the mixing scheme, and the
+  electron count is conserved.
+"""
+import functools
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import scf_oracle as so
+from oracle import thc_oracle as o
+from workloads import ir, synth
+
+
+@functools.lru_cache(maxsize=None)
+def grid_for(beta, wmax):
+    return ir.make_loop_grid(beta, wmax)
+
+
+def _pole(e, beta, tau):
+    if e >= 0:
+        return -np.exp(-e * tau) / (1 + np.exp(-beta * e))
+    return -np.exp(e * (beta - tau)) / (1 + np.exp(beta * e))
+
+
+@pytest.mark.parametrize("beta,wmax", [(50.0, 10.0), (100.0, 10.0)])
+def test_ir_basis_single_poles(beta, wmax):
+    g = grid_for(beta, wmax)
+    assert len(g.tau) == g.basis.L and len(g.iw) >= g.basis.L
+    assert np.abs(g.tau + g.tau[::-1] - beta).max() < 1e-12 * beta
+    assert np.abs(g.iw + g.iw[::-1]).max() < 1e-12
+    assert np.linalg.cond(g.U_tau) < 1e3 and np.linalg.cond(g.U_iw) < 1e3
+    for e in (-1.9, -0.2, 0.0, 0.4, 2.5):
+        gl = g.fit_tau @ _pole(e, beta, g.tau)
+        assert np.abs(g.U_iw @ gl - 1.0 / (1j * g.iw - e)).max() < 1e-8
+        tt = np.array([0.0, 0.1, beta / 3, beta - 0.05, beta])
+        assert np.abs(g.basis.u(tt).T @ gl - _pole(e, beta, tt)).max() < 1e-8
+        back = (g.U_tau @ (g.fit_iw @ (1.0 / (1j * g.iw - e)))).real
+        assert np.abs(back - _pole(e, beta, g.tau)).max() < 1e-8
+
+
+def _case(beta=50.0):
+    return synth.make_sigma_case(6, 14, 4, beta, 31, identity_S=False, n_occ=3)
+
+
+def _sigma_at(case, G):
+    U = o.thc_U(case.X, case.V)
+    nt = G.shape[0]
+    return np.stack([o.sigma_sox_thc(case.X, U, G[k], -G[nt - 1 - k]) +
+                     o.sigma_direct_thc(case.X, case.V, G[k], -G[nt - 1 - k]) for k in range(nt)])
+
+
+def test_dyson_noninteracting_and_boundary_identity():
+    case = _case()
+    g = grid_for(50.0, 10.0)
+    G, mu = so.solve_dyson(g, case.S, case.F, None, 3.0, 0.0)
+    # the count is exact at the returned mu, and mu sits in the gap
+    n_exact = np.sum(1.0 / (1.0 + np.exp(50.0 * (case.eps - mu))))
+    assert abs(n_exact - 3.0) < 2e-8
+    assert np.abs(G - o.g0_tau(case.F, case.S, mu, 50.0, g.tau)).max() < 5e-9
+    gl = g.fit_tau @ G.reshape(len(g.tau), -1)
+    G0p, Gbm = (g.u_zero @ gl).reshape(6, 6), (g.u_beta @ gl).reshape(6, 6)
+    assert np.abs(G0p + Gbm + np.linalg.inv(case.S)).max() < 5e-9
+
+
+def test_ir_energy_matches_finite_T_mp2_and_matsubara_route():
+    case = _case()
+    g = grid_for(50.0, 10.0)
+    G, mu = so.solve_dyson(g, case.S, case.F, None, 3.0, 0.0)
+    Sig = _sigma_at(case, G)
+    E_ir = so.energy_ir(g, G, Sig)
+    eps, C = scipy.linalg.eigh(case.F, case.S)
+    cd, cx = o.mp2_finite_T(o.mo_eri(o.eri_from_thc(case.X, case.V), C), eps - mu, 50.0)
+    assert abs(E_ir - (cd + cx)) < 1e-11
+    assert abs(so.energy_matsubara(g, G, Sig, n_max=4000) - E_ir) < 5e-9
+
+
+def test_loop_converged_energy_independent_of_mixing():
+    case = _case()
+    g = grid_for(50.0, 10.0)
+    r1 = so.run_loop(case, g, 3.0, tol=1e-11)
+    r2 = so.run_loop(case, g, 3.0, tol=1e-11, damping=0.7, n_damp=4, diis_size=4)
+    assert r1["converged"] and r2["converged"]
+    assert abs(r1["E"] - r2["E"]) < 1e-9
+    for h in r1["history"]:
+        assert abs(h["n"] - 3.0) < 1e-9
+    assert np.abs(r1["Sigma"] - np.swapaxes(r1["Sigma"], 1, 2)).max() < 1e-12
+    # the self-consistent energy differs from the first (one-shot) one: the loop did work
+    assert abs(r1["history"][0]["E"] - r1["E"]) > 1e-4
+
+
+def test_planted_wrong_parity_fails_energy_pin(monkeypatch):
+    case = _case()
+    g = grid_for(50.0, 10.0)
+    G, mu = so.solve_dyson(g, case.S, case.F, None, 3.0, 0.0)
+    Sig = _sigma_at(case, G)
+    eps, C = scipy.linalg.eigh(case.F, case.S)
+    cd, cx = o.mp2_finite_T(o.mo_eri(o.eri_from_thc(case.X, case.V), C), eps - mu, 50.0)
+    monkeypatch.setattr(so, "parity", lambda grid: np.ones(grid.basis.L))
+    assert abs(so.energy_ir(g, G, Sig) - (cd + cx)) > 1e-6
