@@ -1,0 +1,165 @@
+"""Self-consistent GF2 loop on the GPU (Sec. II.A of arXiv:2404.17744).
+
+Each iteration: Sigma[G] with thc_sigma_eval (FP64 or 3 x BF16 tensor
+cores), the Galitskii-Migdal energy, damping then DIIS on the self-energy,
+and the Dyson step with the chemical potential re-optimised at fixed
+electron count (thc_dyson_solve).  Every array operation runs in the
+library's kernels; this module holds the host-side control: the iteration,
+the convergence test and the small DIIS system (at most 16 x 16).
+
+Monitor energy with a fixed one-body matrix F:  E = 2 Tr[gamma F] + E_dyn.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+
+from . import thc
+
+
+@dataclasses.dataclass
+class IterationRecord:
+    iter: int
+    E: float
+    E_dyn: float
+    mu: float
+    n_per_spin: float
+    residual: float
+    seconds: float
+    sigma_seconds: float
+    dyson_evals: int
+    proposal: str = ""
+
+
+class GF2Loop:
+    """Fully self-consistent GF2 with THC self-energies on one GPU.
+
+    grid: an object with tau, iw, U_tau, fit_tau, U_iw, fit_iw, u_beta, u_zero
+    and basis.beta / basis.L (workloads.ir.LoopGrid); the tau points must be
+    mirror-symmetric.  X, V, F, S are numpy FP64 arrays.
+    """
+
+    def __init__(self, X, V, F, S, grid, n_elec, precision=thc.THC_FP64, device="cuda:0", stream=None,
+                 damping=0.5, n_damp=2, diis_size=6):
+        import torch
+        self.torch = torch
+        self.dev = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
+        self.n, self.N = X.shape
+        self.grid = grid
+        self.n_tau = len(grid.tau)
+        self.n_elec = float(n_elec)
+        self.damping, self.n_damp, self.diis_size = damping, n_damp, min(diis_size, 16)
+        with torch.cuda.stream(self.stream):
+            self.X = torch.from_numpy(np.ascontiguousarray(X)).to(self.dev)
+            self.V = torch.from_numpy(np.ascontiguousarray(V)).to(self.dev)
+            self.F = torch.from_numpy(np.ascontiguousarray(F)).to(self.dev)
+            self.S = torch.from_numpy(np.ascontiguousarray(S)).to(self.dev)
+            shape = (self.n_tau, self.n, self.n)
+            self.G = torch.empty(shape, dtype=torch.float64, device=self.dev)
+            self.Sig_out = torch.empty_like(self.G)
+            self.Sig_in = torch.zeros_like(self.G)
+            self.scratch = torch.empty(512, dtype=torch.float64, device=self.dev)
+        s = self.stream.cuda_stream
+        self.ctx = thc.thc_sigma_init(self.n, self.N, self.n_tau, grid.basis.beta, self.X, self.V,
+                                      np.ascontiguousarray(grid.tau), precision, thc.THC_DIRECT | thc.THC_SOX, s)
+        self.dy = thc.thc_dyson_init(self.n, self.n_tau, len(grid.iw), grid.basis.L, grid.basis.beta, self.S, self.F,
+                                     grid.U_tau, grid.fit_tau, grid.U_iw, grid.fit_iw, grid.iw, grid.u_beta,
+                                     grid.u_zero, s)
+        self.mu = 0.0
+        self.history: list[tuple] = []   # (Sigma_out, residual) device tensors for DIIS
+        self.records: list[IterationRecord] = []
+
+    def close(self):
+        if self.ctx is not None:
+            thc.thc_destroy(self.ctx)
+            self.ctx = None
+        if self.dy is not None:
+            thc.thc_dyson_destroy(self.dy)
+            self.dy = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ pieces
+    def _len(self):
+        return self.n_tau * self.n * self.n
+
+    def _dot(self, a, b):
+        return thc.thc_vec_dot(self._len(), a, b, self.scratch, self.stream.cuda_stream)
+
+    def _lincomb(self, coeffs, vecs, out):
+        thc.thc_vec_lincomb(coeffs, vecs, self._len(), out, self.stream.cuda_stream)
+
+    def dyson(self, sigma=None):
+        self.mu = thc.thc_dyson_solve(self.dy, sigma, self.n_elec, self.mu, 1e-11, self.G)
+        return thc.thc_dyson_evals(self.dy)
+
+    def sigma(self):
+        thc.thc_sigma_eval(self.ctx, self.G, None, self.Sig_out)
+        thc.thc_sync(self.ctx)
+
+    def energy(self):
+        e_dyn, trgf, n = thc.thc_dyson_energy(self.dy, self.G, self.Sig_out)
+        return 2.0 * trgf + e_dyn, e_dyn, n
+
+    def mix(self, it):
+        """Next input self-energy from the history (damping, then DIIS)."""
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            r = torch.empty_like(self.G)
+        self._lincomb([1.0, -1.0], [self.Sig_out, self.Sig_in], r)
+        out = self.Sig_out.clone()
+        self.history.append((out, r))
+        self.history = self.history[-self.diis_size:]
+        res = float(np.sqrt(self._dot(r, r)))
+        if it <= self.n_damp:
+            a = self.damping
+            self._lincomb([a, 1.0 - a], [self.Sig_out, self.Sig_in], self.Sig_in)
+            return res
+        k = len(self.history)
+        B = np.empty((k + 1, k + 1))
+        for i in range(k):
+            for j in range(i, k):
+                B[i, j] = B[j, i] = self._dot(self.history[i][1], self.history[j][1])
+        B[k, :k] = B[:k, k] = -1.0
+        B[k, k] = 0.0
+        rhs = np.zeros(k + 1)
+        rhs[k] = -1.0
+        c = np.linalg.lstsq(B, rhs, rcond=None)[0][:k]
+        self._lincomb(list(c), [h[0] for h in self.history], self.Sig_in)
+        return res
+
+    # --------------------------------------------------------------- run
+    def run(self, tol=1e-8, max_iter=60, proposer=None, log=None):
+        """Iterates until |E_k - E_{k-1}| < tol.  proposer(loop, it) may replace Sig_in
+        before the Dyson step and returns a label (learned proposals); it is judged by the
+        exact Sigma of the next iteration like any other input."""
+        self.dyson(None)
+        E_prev = None
+        converged = False
+        for it in range(1, max_iter + 1):
+            t0 = time.perf_counter()
+            self.sigma()
+            t_sig = time.perf_counter() - t0
+            E, E_dyn, n = self.energy()
+            done = E_prev is not None and abs(E - E_prev) < tol
+            res = 0.0 if done else self.mix(it)
+            label = ""
+            if not done and proposer is not None:
+                label = proposer(self, it) or ""
+            evals = 0 if done else self.dyson(self.Sig_in)
+            rec = IterationRecord(it, E, E_dyn, self.mu, n, res, time.perf_counter() - t0, t_sig, evals, label)
+            self.records.append(rec)
+            if log:
+                log(rec)
+            if done:
+                converged = True
+                break
+            E_prev = E
+        return converged

@@ -73,6 +73,23 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_gemm_bf16x3.restype = i
     lib.thc_destroy.argtypes = [vp]
     lib.thc_destroy.restype = None
+    # self-consistency loop (include/thc_dyson.h)
+    lib.thc_dyson_init.argtypes = [ctypes.POINTER(vp), i, i, i, i, d, dp, dp, dp, dp, dp, dp, dp, dp, dp, vp]
+    lib.thc_dyson_init.restype = i
+    lib.thc_dyson_solve.argtypes = [vp, dp, d, ctypes.POINTER(d), d, dp]
+    lib.thc_dyson_solve.restype = i
+    lib.thc_dyson_energy.argtypes = [vp, dp, dp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.thc_dyson_energy.restype = i
+    lib.thc_dyson_evals.argtypes = [vp]
+    lib.thc_dyson_evals.restype = i
+    lib.thc_dyson_last_error.argtypes = [vp]
+    lib.thc_dyson_last_error.restype = ctypes.c_char_p
+    lib.thc_dyson_destroy.argtypes = [vp]
+    lib.thc_dyson_destroy.restype = None
+    lib.thc_vec_dot.argtypes = [ctypes.c_longlong, dp, dp, dp, ctypes.POINTER(d), vp]
+    lib.thc_vec_dot.restype = i
+    lib.thc_vec_lincomb.argtypes = [i, ctypes.POINTER(d), ctypes.POINTER(vp), ctypes.c_longlong, dp, vp]
+    lib.thc_vec_lincomb.restype = i
     lib.thc_last_error.argtypes = [vp]
     lib.thc_last_error.restype = ctypes.c_char_p
     if path is None:
@@ -186,3 +203,70 @@ def thc_gemm_bf16x3(batch, M, N, K, A, strideA, B, strideB, C, strideC, stream=N
 
 def thc_destroy(ctx):
     load_library().thc_destroy(ctx)
+
+
+# ---------------------------------------------------------------- loop ABI
+def _interleaved(z):
+    """complex128 array -> contiguous float64 (re, im) interleaving, as the ABI expects."""
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(z, dtype=np.complex128)).view(np.float64)
+
+
+def _stream(stream):
+    return None if stream is None else ctypes.c_void_p(int(stream))
+
+
+def _dcheck(rc, d):
+    if rc != THC_OK:
+        msg = load_library().thc_dyson_last_error(d).decode() if d else thc_last_error(None)
+        raise ThcError(rc, msg)
+
+
+def thc_dyson_init(n_ao, n_tau, n_iw, n_l, beta, S, F, U_tau, fit_tau, U_iw, fit_iw, iw, u_beta, u_zero,
+                   stream=None):
+    import numpy as np
+    d = ctypes.c_void_p()
+    keep = [np.ascontiguousarray(x, dtype=np.float64) for x in (U_tau, fit_tau, iw, u_beta, u_zero)]
+    ziw, zfit = _interleaved(U_iw), _interleaved(fit_iw)
+    rc = load_library().thc_dyson_init(ctypes.byref(d), int(n_ao), int(n_tau), int(n_iw), int(n_l), float(beta),
+                                       _ptr(S), _ptr(F), _ptr(keep[0]), _ptr(keep[1]), _ptr(ziw), _ptr(zfit),
+                                       _ptr(keep[2]), _ptr(keep[3]), _ptr(keep[4]), _stream(stream))
+    _dcheck(rc, None)
+    return d
+
+
+def thc_dyson_solve(d, Sigma_tau, n_elec, mu, tol, G_tau) -> float:
+    m = ctypes.c_double(mu)
+    _dcheck(load_library().thc_dyson_solve(d, _ptr(Sigma_tau), float(n_elec), ctypes.byref(m), float(tol),
+                                           _ptr(G_tau)), d)
+    return m.value
+
+
+def thc_dyson_energy(d, G_tau, Sigma_tau):
+    """(E_dyn, Tr[gamma F], Tr[gamma S])."""
+    e, f, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _dcheck(load_library().thc_dyson_energy(d, _ptr(G_tau), _ptr(Sigma_tau), ctypes.byref(e), ctypes.byref(f),
+                                            ctypes.byref(n)), d)
+    return e.value, f.value, n.value
+
+
+def thc_dyson_evals(d) -> int:
+    return int(load_library().thc_dyson_evals(d))
+
+
+def thc_dyson_destroy(d):
+    load_library().thc_dyson_destroy(d)
+
+
+def thc_vec_dot(length, x, y, scratch, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(load_library().thc_vec_dot(int(length), _ptr(x), _ptr(y), _ptr(scratch), ctypes.byref(out),
+                                      _stream(stream)), None)
+    return out.value
+
+
+def thc_vec_lincomb(coeffs, vecs, length, out, stream=None):
+    k = len(coeffs)
+    c = (ctypes.c_double * k)(*[float(x) for x in coeffs])
+    ptrs = (ctypes.c_void_p * k)(*[_ptr(v).value for v in vecs])
+    _check(load_library().thc_vec_lincomb(k, c, ptrs, int(length), _ptr(out), _stream(stream)), None)

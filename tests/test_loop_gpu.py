@@ -1,0 +1,122 @@
+"""GPU parity of the self-consistency loop (Dyson step, energies, full loop)
+against the FP64 oracle loop, through the C ABI (include/thc_dyson.h).
+
+Bars: G(tau) and mu of one Dyson step within 1e-9; energies of the same
+(G, Sigma) within 1e-12; converged loop energy within 1e-9 (FP64) and within
+1e-5 Ha (3 x BF16 self-energy) of the oracle loop.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import scf_oracle as so
+from oracle import thc_oracle as o
+from workloads import ir, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@functools.lru_cache(maxsize=None)
+def grid_for(beta, wmax):
+    return ir.make_loop_grid(beta, wmax)
+
+
+def _dyson(case, g):
+    from paper_2404_17744_gb300 import thc
+    dev = torch.device("cuda:0")
+    S = torch.from_numpy(case.S).to(dev)
+    F = torch.from_numpy(case.F).to(dev)
+    d = thc.thc_dyson_init(case.n, len(g.tau), len(g.iw), g.basis.L, g.basis.beta, S, F, g.U_tau, g.fit_tau, g.U_iw,
+                           g.fit_iw, g.iw, g.u_beta, g.u_zero, torch.cuda.current_stream(dev).cuda_stream)
+    return d
+
+
+def test_dyson_step_matches_oracle():
+    from paper_2404_17744_gb300 import thc
+    case = synth.make_sigma_case(9, 25, 4, 50.0, 41, identity_S=False, n_occ=4)
+    g = grid_for(50.0, 10.0)
+    G0, mu0 = so.solve_dyson(g, case.S, case.F, None, 4.0, 0.0)
+    U = o.thc_U(case.X, case.V)
+    nt = len(g.tau)
+    Sig = np.stack([o.sigma_sox_thc(case.X, U, G0[k], -G0[nt - 1 - k]) +
+                    o.sigma_direct_thc(case.X, case.V, G0[k], -G0[nt - 1 - k]) for k in range(nt)])
+    G_ref, mu_ref = so.solve_dyson(g, case.S, case.F, Sig, 4.0, mu0)
+    d = _dyson(case, g)
+    try:
+        dev = torch.device("cuda:0")
+        Gd = torch.empty((nt, case.n, case.n), dtype=torch.float64, device=dev)
+        Sd = torch.from_numpy(Sig).to(dev)
+        # the inversions and transforms at exactly the oracle's mu (a tolerance that accepts the
+        # starting point returns after one evaluation) ...
+        assert thc.thc_dyson_solve(d, None, 4.0, mu0, 10.0, Gd) == mu0
+        assert np.abs(Gd.cpu().numpy() - G0).max() < 1e-10
+        assert thc.thc_dyson_solve(d, Sd, 4.0, mu_ref, 10.0, Gd) == mu_ref
+        assert np.abs(Gd.cpu().numpy() - G_ref).max() < 1e-10
+        # ... and the search: the count is fixed; inside the gap mu (and G at large tau) move
+        # only as far as the count's tolerance allows
+        mu = thc.thc_dyson_solve(d, Sd, 4.0, 0.0, 1e-12, Gd)
+        E_check, _, n_check = thc.thc_dyson_energy(d, Gd, Sd)
+        assert abs(n_check - 4.0) < 1e-9
+        assert abs(mu - mu_ref) < 1e-4
+        E, trgf, n = thc.thc_dyson_energy(d, Gd, Sd)
+        assert abs(E - so.energy_ir(g, Gd.cpu().numpy(), Sig)) < 1e-12
+        assert abs(n - 4.0) < 1e-9
+    finally:
+        thc.thc_dyson_destroy(d)
+
+
+def test_vector_utilities():
+    from paper_2404_17744_gb300 import thc
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(5)
+    a, b, c = (rng.standard_normal(100003) for _ in range(3))
+    ta, tb, tc = (torch.from_numpy(x).to(dev) for x in (a, b, c))
+    scratch = torch.empty(512, dtype=torch.float64, device=dev)
+    assert abs(thc.thc_vec_dot(len(a), ta, tb, scratch) - a @ b) < 1e-10
+    out = torch.empty_like(ta)
+    thc.thc_vec_lincomb([0.5, -2.0, 3.0], [ta, tb, tc], len(a), out)
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - (0.5 * a - 2 * b + 3 * c)).max() < 1e-13
+    thc.thc_vec_lincomb([2.0, 1.0], [ta, tb], len(a), ta)   # output aliases an input
+    torch.cuda.synchronize()
+    assert np.abs(ta.cpu().numpy() - (2 * a + b)).max() < 1e-13
+
+
+def _loop(case, g, n_elec, precision, tol=1e-10):
+    from paper_2404_17744_gb300 import scf
+    L = scf.GF2Loop(case.X, case.V, case.F, case.S, g, n_elec, precision=precision)
+    try:
+        conv = L.run(tol=tol, max_iter=80)
+        return conv, L.records
+    finally:
+        L.close()
+
+
+@pytest.mark.parametrize("n,N,beta,n_occ,seed", [(6, 14, 50.0, 3, 31), (20, 60, 100.0, 8, 17745)])
+def test_fp64_loop_matches_oracle_loop(n, N, beta, n_occ, seed):
+    from paper_2404_17744_gb300 import thc
+    case = synth.make_sigma_case(n, N, 4, beta, seed, identity_S=False, n_occ=n_occ)
+    g = grid_for(beta, 10.0)
+    ref = so.run_loop(case, g, float(n_occ), tol=1e-10)
+    conv, recs = _loop(case, g, float(n_occ), thc.THC_FP64)
+    assert conv and ref["converged"]
+    print(f"oracle E {ref['E']:.12f} ({ref['iters']} it)  GPU E {recs[-1].E:.12f} ({len(recs)} it)")
+    assert abs(recs[-1].E - ref["E"]) < 1e-9
+    assert abs(len(recs) - ref["iters"]) <= 2
+    assert abs(recs[-1].mu - ref["mu"]) < 1e-4          # mu is loose inside the gap
+    assert abs(recs[-1].n_per_spin - n_occ) < 1e-9
+    for r, h in zip(recs[:5], ref["history"][:5]):
+        assert abs(r.E - h["E"]) < 1e-9
+
+
+def test_split_loop_reaches_fp64_energy():
+    from paper_2404_17744_gb300 import thc
+    case = synth.make_sigma_case(20, 60, 4, 100.0, 17745, identity_S=False, n_occ=8)
+    g = grid_for(100.0, 10.0)
+    c1, r64 = _loop(case, g, 8.0, thc.THC_FP64, tol=1e-9)
+    c2, rsp = _loop(case, g, 8.0, thc.THC_BF16X3, tol=1e-9)
+    assert c1 and c2
+    print(f"FP64 E {r64[-1].E:.10f} ({len(r64)} it), split E {rsp[-1].E:.10f} ({len(rsp)} it)")
+    assert abs(r64[-1].E - rsp[-1].E) < 1e-5
