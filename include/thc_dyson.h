@@ -51,8 +51,9 @@ int thc_dyson_init(thc_dyson **d, int n_ao, int n_tau, int n_iw, int n_l, double
  *   mu         in: starting guess; out: the chemical potential found
  *   tol        tolerance on the electron count (<= 0: 1e-10)
  *   G_tau      dev out, n_tau x n_ao x n_ao
- * The count N(mu) is monotonic; the search brackets it and takes secant steps
- * safeguarded by bisection (each trial is a full set of n_iw complex
+ * The count N(mu) is monotonic; the search takes secant steps from the
+ * starting guess (first step 1e-3), kept inside a bracket once one is known
+ * and safeguarded by bisection (each trial is a full set of n_iw complex
  * inversions).  THC_EINVAL if it does not converge.  Synchronises.
  */
 int thc_dyson_solve(thc_dyson *d, const double *Sigma_tau, double n_elec, double *mu, double tol,

@@ -341,42 +341,40 @@ int thc_dyson_solve(thc_dyson* d, const double* Sigma_tau, double n_elec, double
     THC_TRY(dcheck(d, cudaMemsetAsync(d->Siw, 0, sizeof(double) * 2 * n2 * nw, d->stream), "zero Sigma"));
   }
   if (!(tol > 0)) tol = 1e-10;
-  // N(mu) is increasing: bracket the target, then secant steps safeguarded by bisection
-  double m0 = *mu, n0 = 0.0;
-  THC_TRY(dyson_at(d, m0, &n0));
-  double lo, hi, nlo, nhi;
-  double step = 0.25;
-  if (std::fabs(n0 - n_elec) <= tol) {
-    lo = hi = m0;
-    nlo = nhi = n0;
-  } else if (n0 < n_elec) {
-    lo = m0, nlo = n0;
-    hi = m0 + step;
-    THC_TRY(dyson_at(d, hi, &nhi));
-    while (nhi < n_elec && d->evals < 60) {
-      lo = hi, nlo = nhi, step *= 2, hi += step;
-      THC_TRY(dyson_at(d, hi, &nhi));
+  // N(mu) is increasing.  Secant steps from the starting guess (a small first
+  // step: mu moves little between iterations), kept inside a bracket once one
+  // is known and replaced by bisection when they leave it or stall.
+  double m = *mu, nm = 0.0;
+  THC_TRY(dyson_at(d, m, &nm));
+  double lo = -INFINITY, hi = INFINITY, nlo = 0.0, nhi = 0.0;
+  auto note = [&](double x, double nx) {
+    if (nx < n_elec) {
+      if (x > lo) lo = x, nlo = nx;
+    } else if (x < hi) {
+      hi = x, nhi = nx;
     }
-  } else {
-    hi = m0, nhi = n0;
-    lo = m0 - step;
-    THC_TRY(dyson_at(d, lo, &nlo));
-    while (nlo > n_elec && d->evals < 60) {
-      hi = lo, nhi = nlo, step *= 2, lo -= step;
-      THC_TRY(dyson_at(d, lo, &nlo));
+  };
+  note(m, nm);
+  double mp = m, np_ = nm;
+  double step = (nm < n_elec ? 1.0 : -1.0) * 1e-3;
+  for (int it = 0; it < 200 && std::fabs(nm - n_elec) > tol; ++it) {
+    double x;
+    if (it == 0) {
+      x = m + step;
+    } else if (np_ != nm && std::isfinite(lo) && std::isfinite(hi) && it % 4 == 3) {
+      x = 0.5 * (lo + hi);  // guaranteed progress every fourth step
+    } else {
+      const double slope = (nm - np_) / (m - mp);
+      x = (slope > 0 && std::isfinite(slope)) ? m + (n_elec - nm) / slope : m + 4 * (m - mp);
+      const double cap = std::max(0.5, 4 * std::fabs(m - mp));
+      x = std::min(std::max(x, m - cap), m + cap);
     }
-  }
-  double m = lo, nm = nlo;
-  if (lo != hi) {
-    for (int it = 0; it < 100; ++it) {
-      double x = lo + (n_elec - nlo) * (hi - lo) / (nhi - nlo);  // secant in the bracket
-      if (!(x > lo && x < hi) || it % 3 == 2) x = 0.5 * (lo + hi);
-      THC_TRY(dyson_at(d, x, &nm));
-      m = x;
-      if (std::fabs(nm - n_elec) <= tol || hi - lo < 1e-15) break;
-      if (nm < n_elec) lo = x, nlo = nm;
-      else hi = x, nhi = nm;
-    }
+    if (std::isfinite(lo) && std::isfinite(hi) && !(x > lo && x < hi)) x = 0.5 * (lo + hi);
+    if (std::isfinite(lo) && std::isfinite(hi) && hi - lo < 1e-15) break;
+    mp = m, np_ = nm;
+    m = x;
+    THC_TRY(dyson_at(d, m, &nm));
+    note(m, nm);
   }
   if (std::fabs(nm - n_elec) > 1e3 * tol)
     return dfail(d, THC_EINVAL, "thc_dyson_solve: chemical potential search did not converge");

@@ -137,9 +137,9 @@ class GF2Loop:
 
     # --------------------------------------------------------------- run
     def run(self, tol=1e-8, max_iter=60, proposer=None, log=None):
-        """Iterates until |E_k - E_{k-1}| < tol.  proposer(loop, it) may replace Sig_in
-        before the Dyson step and returns a label (learned proposals); it is judged by the
-        exact Sigma of the next iteration like any other input."""
+        """Iterates until |E_k - E_{k-1}| < tol.  proposer(loop, it, residual) may replace
+        Sig_in before the Dyson step and returns a label (learned proposals); it is judged
+        by the exact Sigma of the next iteration like any other input."""
         self.dyson(None)
         E_prev = None
         converged = False
@@ -152,7 +152,7 @@ class GF2Loop:
             res = 0.0 if done else self.mix(it)
             label = ""
             if not done and proposer is not None:
-                label = proposer(self, it) or ""
+                label = proposer(self, it, res) or ""
             evals = 0 if done else self.dyson(self.Sig_in)
             rec = IterationRecord(it, E, E_dyn, self.mu, n, res, time.perf_counter() - t0, t_sig, evals, label)
             self.records.append(rec)
@@ -163,3 +163,68 @@ class GF2Loop:
                 break
             E_prev = E
         return converged
+
+
+class LearnedProposer:
+    """Learned Sigma proposals for GF2Loop.run (include/thc_learned.h).
+
+    Every iteration the exact Sigma_out is observed.  From the third iterate
+    on, while the residual is above `active_above`, the network is retrained
+    on the trajectory and its proposal replaces the DIIS input.  A proposal is
+    judged by the next iteration's exact residual: if that is not below the
+    residual the proposal was made at, the proposal counts as rejected, the
+    loop continues from DIIS (which keeps the evaluated pair in its history)
+    and proposals pause for `cooldown` iterations.
+    """
+
+    def __init__(self, loop, hidden=512, max_hist=6, steps=150, batch=8192, lr=2e-3, seed=17744,
+                 active_above=1e-5, cooldown=2):
+        g = loop.grid
+        L = g.basis.L
+        rng = np.random.default_rng(seed)
+        # He initialisation; the last layer starts small, so early proposals stay near the latest iterate
+        self.W1 = (rng.standard_normal((hidden, 2 * L)) * np.sqrt(2.0 / (2 * L))).astype(np.float32)
+        self.b1 = np.zeros(hidden, np.float32)
+        self.W2 = (rng.standard_normal((L, hidden)) * np.sqrt(1.0 / hidden) * 0.1).astype(np.float32)
+        self.b2 = np.zeros(L, np.float32)
+        self.p = thc.thc_proposer_init(loop.n, loop.n_tau, L, g.U_tau, g.fit_tau, hidden, max_hist, self.W1, self.b1,
+                                       self.W2, self.b2, loop.stream.cuda_stream)
+        self.steps, self.batch, self.lr = steps, batch, lr
+        self.active_above, self.cooldown = active_above, cooldown
+        self.pending = None          # residual at which the last proposal was made
+        self.pause = 0
+        self.accepted = self.rejected = 0
+        self.losses = []
+
+    def close(self):
+        if self.p is not None:
+            thc.thc_proposer_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __call__(self, loop, it, residual):
+        thc.thc_proposer_observe(self.p, loop.Sig_out)
+        label = ""
+        if self.pending is not None:
+            if residual < self.pending:
+                self.accepted += 1
+                label = "accepted; "
+            else:
+                self.rejected += 1
+                self.pause = self.cooldown
+                label = "rejected; "
+            self.pending = None
+        if self.pause > 0:
+            self.pause -= 1
+            return label + "paused"
+        if thc.thc_proposer_count(self.p) < 3 or residual < self.active_above:
+            return label.rstrip("; ")
+        self.losses.append(thc.thc_proposer_train(self.p, self.steps, self.batch, self.lr))
+        thc.thc_proposer_propose(self.p, loop.Sig_in)
+        self.pending = residual
+        return label + "proposed"

@@ -90,6 +90,34 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_vec_dot.restype = i
     lib.thc_vec_lincomb.argtypes = [i, ctypes.POINTER(d), ctypes.POINTER(vp), ctypes.c_longlong, dp, vp]
     lib.thc_vec_lincomb.restype = i
+    # learned proposals (include/thc_learned.h)
+    fp = ctypes.c_void_p
+    lib.thc_mlp_init.argtypes = [ctypes.POINTER(vp), i, i, i, i, fp, fp, fp, fp, vp]
+    lib.thc_mlp_init.restype = i
+    lib.thc_mlp_forward.argtypes = [vp, i, fp, fp]
+    lib.thc_mlp_forward.restype = i
+    lib.thc_mlp_gradients.argtypes = [vp, i, fp, fp, ctypes.POINTER(d), fp, fp, fp, fp]
+    lib.thc_mlp_gradients.restype = i
+    lib.thc_mlp_train.argtypes = [vp, i, fp, fp, i, i, d, ctypes.POINTER(d)]
+    lib.thc_mlp_train.restype = i
+    lib.thc_mlp_get_weights.argtypes = [vp, fp, fp, fp, fp]
+    lib.thc_mlp_get_weights.restype = i
+    lib.thc_mlp_destroy.argtypes = [vp]
+    lib.thc_mlp_destroy.restype = None
+    lib.thc_proposer_init.argtypes = [ctypes.POINTER(vp), i, i, i, dp, dp, i, i, fp, fp, fp, fp, vp]
+    lib.thc_proposer_init.restype = i
+    lib.thc_proposer_observe.argtypes = [vp, dp]
+    lib.thc_proposer_observe.restype = i
+    lib.thc_proposer_count.argtypes = [vp]
+    lib.thc_proposer_count.restype = i
+    lib.thc_proposer_train.argtypes = [vp, i, i, d, ctypes.POINTER(d)]
+    lib.thc_proposer_train.restype = i
+    lib.thc_proposer_propose.argtypes = [vp, dp]
+    lib.thc_proposer_propose.restype = i
+    lib.thc_proposer_last_error.argtypes = [vp]
+    lib.thc_proposer_last_error.restype = ctypes.c_char_p
+    lib.thc_proposer_destroy.argtypes = [vp]
+    lib.thc_proposer_destroy.restype = None
     lib.thc_last_error.argtypes = [vp]
     lib.thc_last_error.restype = ctypes.c_char_p
     if path is None:
@@ -97,17 +125,17 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     return lib
 
 
-def _ptr(a):
-    """Raw pointer of a float64 contiguous tensor/array, or NULL for None."""
+def _ptr(a, dtype="float64"):
+    """Raw pointer of a contiguous tensor/array of `dtype`, or NULL for None."""
     if a is None:
         return None
     if hasattr(a, "data_ptr"):  # torch.Tensor
-        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
-            raise TypeError("expected a contiguous float64 tensor")
+        if str(a.dtype) != "torch." + dtype or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {dtype} tensor")
         return ctypes.c_void_p(a.data_ptr())
     if hasattr(a, "ctypes"):  # numpy.ndarray
-        if a.dtype.name != "float64" or not a.flags["C_CONTIGUOUS"]:
-            raise TypeError("expected a C-contiguous float64 array")
+        if a.dtype.name != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {dtype} array")
         return ctypes.c_void_p(a.ctypes.data)
     if isinstance(a, int):
         return ctypes.c_void_p(a)
@@ -270,3 +298,85 @@ def thc_vec_lincomb(coeffs, vecs, length, out, stream=None):
     c = (ctypes.c_double * k)(*[float(x) for x in coeffs])
     ptrs = (ctypes.c_void_p * k)(*[_ptr(v).value for v in vecs])
     _check(load_library().thc_vec_lincomb(k, c, ptrs, int(length), _ptr(out), _stream(stream)), None)
+
+
+# ------------------------------------------------------ learned proposals ABI
+def _f32(a):
+    return _ptr(a, "float32")
+
+
+def _lcheck(rc, fn, h):
+    if rc != THC_OK:
+        msg = fn(h).decode() if h else thc_last_error(None)
+        raise ThcError(rc, msg or thc_last_error(None))
+
+
+def thc_mlp_init(d_in, hidden, d_out, max_batch, W1, b1, W2, b2, stream=None):
+    m = ctypes.c_void_p()
+    rc = load_library().thc_mlp_init(ctypes.byref(m), int(d_in), int(hidden), int(d_out), int(max_batch), _f32(W1),
+                                     _f32(b1), _f32(W2), _f32(b2), _stream(stream))
+    _check(rc, None)
+    return m
+
+
+def thc_mlp_forward(m, batch, X, Y):
+    _check(load_library().thc_mlp_forward(m, int(batch), _f32(X), _f32(Y)), None)
+
+
+def thc_mlp_gradients(m, batch, X, T, gW1=None, gb1=None, gW2=None, gb2=None) -> float:
+    loss = ctypes.c_double()
+    _check(load_library().thc_mlp_gradients(m, int(batch), _f32(X), _f32(T), ctypes.byref(loss), _f32(gW1), _f32(gb1),
+                                            _f32(gW2), _f32(gb2)), None)
+    return loss.value
+
+
+def thc_mlp_train(m, n_samples, X, T, steps, batch, lr) -> float:
+    loss = ctypes.c_double()
+    _check(load_library().thc_mlp_train(m, int(n_samples), _f32(X), _f32(T), int(steps), int(batch), float(lr),
+                                        ctypes.byref(loss)), None)
+    return loss.value
+
+
+def thc_mlp_get_weights(m, W1=None, b1=None, W2=None, b2=None):
+    _check(load_library().thc_mlp_get_weights(m, _f32(W1), _f32(b1), _f32(W2), _f32(b2)), None)
+
+
+def thc_mlp_destroy(m):
+    load_library().thc_mlp_destroy(m)
+
+
+def thc_proposer_init(n_ao, n_tau, n_l, U_tau, fit_tau, hidden, max_hist, W1, b1, W2, b2, stream=None):
+    import numpy as np
+    p = ctypes.c_void_p()
+    Ut, Ft = np.ascontiguousarray(U_tau, dtype=np.float64), np.ascontiguousarray(fit_tau, dtype=np.float64)
+    lib = load_library()
+    rc = lib.thc_proposer_init(ctypes.byref(p), int(n_ao), int(n_tau), int(n_l), _ptr(Ut), _ptr(Ft), int(hidden),
+                               int(max_hist), _f32(W1), _f32(b1), _f32(W2), _f32(b2), _stream(stream))
+    _lcheck(rc, lib.thc_proposer_last_error, None)
+    return p
+
+
+def thc_proposer_observe(p, Sigma_tau):
+    lib = load_library()
+    _lcheck(lib.thc_proposer_observe(p, _ptr(Sigma_tau)), lib.thc_proposer_last_error, p)
+
+
+def thc_proposer_count(p) -> int:
+    return int(load_library().thc_proposer_count(p))
+
+
+def thc_proposer_train(p, steps, batch, lr) -> float:
+    lib = load_library()
+    loss = ctypes.c_double()
+    _lcheck(lib.thc_proposer_train(p, int(steps), int(batch), float(lr), ctypes.byref(loss)),
+            lib.thc_proposer_last_error, p)
+    return loss.value
+
+
+def thc_proposer_propose(p, Sigma_tau):
+    lib = load_library()
+    _lcheck(lib.thc_proposer_propose(p, _ptr(Sigma_tau)), lib.thc_proposer_last_error, p)
+
+
+def thc_proposer_destroy(p):
+    load_library().thc_proposer_destroy(p)

@@ -226,3 +226,28 @@ def test_golden_thc20_regression():
     assert abs(o.energy_dyn_tau(case.G_bmt, Sx, case.tau_w) - g["E_dyn_sox"]) < 1e-13
     for k, i, j, d, x in g["samples"]:
         assert abs(Sd[k, i, j] - d) < 1e-14 and abs(Sx[k, i, j] - x) < 1e-14
+
+
+def test_mlp_oracle_gradients_against_finite_differences():
+    """Backpropagation of the proposal network's loss equals central differences."""
+    from oracle import mlp_oracle as mo
+    rng = np.random.default_rng(3)
+    B, din, H, dout = 7, 6, 9, 4
+    X = rng.standard_normal((B, din))
+    T = rng.standard_normal((B, dout))
+    W1 = rng.standard_normal((H, din)) * 0.5
+    b1 = rng.standard_normal(H) * 0.1
+    W2 = rng.standard_normal((dout, H)) * 0.5
+    b2 = rng.standard_normal(dout) * 0.1
+    loss, gW1, gb1, gW2, gb2 = mo.loss_and_grads(X, T, W1, b1, W2, b2)
+    h = 1e-6
+    for P, G in ((W1, gW1), (b1, gb1), (W2, gW2), (b2, gb2)):
+        flat = P.reshape(-1)
+        for i in range(0, flat.size, max(1, flat.size // 11)):
+            old = flat[i]
+            flat[i] = old + h
+            lp = mo.loss_and_grads(X, T, W1, b1, W2, b2)[0]
+            flat[i] = old - h
+            lm = mo.loss_and_grads(X, T, W1, b1, W2, b2)[0]
+            flat[i] = old
+            assert abs((lp - lm) / (2 * h) - G.reshape(-1)[i]) < 1e-7
