@@ -144,6 +144,23 @@ int thc_sync(thc_ctx *ctx);
 int thc_gemm_bf16x3(int batch, int M, int N, int K, const double *A, long long strideA,
                     const double *B, long long strideB, double *C, long long strideC, void *stream);
 
+/*
+ * thc_sigma_tune -- THC_BF16X3 contexts: run one evaluation on G_tau (dev;
+ * G_bmt as for thc_sigma_eval) with the autotuner on, which times both
+ * tensor-core tile widths for every contraction shape not yet in the table
+ * and keeps the faster; the evaluation's output is discarded.  Later
+ * evaluations of any context use the table.  No-op for THC_FP64.  Synchronises.
+ */
+int thc_sigma_tune(thc_ctx *ctx, const double *G_tau, const double *G_bmt);
+
+/* thc_autotune_save / thc_autotune_load -- write / merge the tile table
+ * (text, one shape per line: class M N K batch width). */
+int thc_autotune_save(const char *path);
+int thc_autotune_load(const char *path);
+
+/* thc_autotune_entries -- number of shapes in the tile table. */
+int thc_autotune_entries(void);
+
 /* thc_set_stream -- launch subsequent work of ctx on stream (cudaStream_t). */
 int thc_set_stream(thc_ctx *ctx, void *stream);
 

@@ -19,6 +19,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -341,12 +343,59 @@ int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, 
   return prof_end(ctx, &rec, cudaGetLastError(), what);
 }
 
-// Picks the tile width for an N-column output (fewest padded columns, then wider).
+// ------------------------------------------------------------- autotuner
+// Tile width (BN = 128 or 256 output columns) per contraction shape.  A shape
+// not in the table gets the width with the fewest padded columns (ties: 256);
+// a context in tuning mode times both widths on its first encounter of a
+// shape (CUDA events on its stream) and records the faster.  Timing runs the
+// contraction twice, so the outputs of a tuning evaluation are discarded.
+struct ShapeKey {
+  int kclass;
+  long long M, N, K, batch;
+  bool operator<(const ShapeKey& o) const {
+    if (kclass != o.kclass) return kclass < o.kclass;
+    if (M != o.M) return M < o.M;
+    if (N != o.N) return N < o.N;
+    if (K != o.K) return K < o.K;
+    return batch < o.batch;
+  }
+};
+std::map<ShapeKey, int> g_tile_table;
+std::mutex g_tile_mu;
+
 template <class Epi>
 int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool bb, long long M, long long N,
          long long K, long long batch, const Epi& epi, const char* what) {
-  const long long w128 = (N + 127) / 128 * 128, w256 = (N + 255) / 256 * 256;
-  if (w256 <= w128) return launch_split_gemm<256>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+  const ShapeKey key{kclass, M, N, K, batch};
+  int bn = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    auto it = g_tile_table.find(key);
+    if (it != g_tile_table.end()) bn = it->second;
+  }
+  if (!bn && ctx->tuning && !ctx->prof_on) {
+    cudaEvent_t e[3];
+    for (auto& x : e) THC_TRY(check_cuda(ctx, cudaEventCreate(&x), "tuning event"));
+    float t128 = 0.f, t256 = 0.f;
+    int rc = check_cuda(ctx, cudaEventRecord(e[0], ctx->stream), "tuning event");
+    if (rc == THC_OK) rc = launch_split_gemm<128>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+    if (rc == THC_OK) rc = check_cuda(ctx, cudaEventRecord(e[1], ctx->stream), "tuning event");
+    if (rc == THC_OK) rc = launch_split_gemm<256>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+    if (rc == THC_OK) rc = check_cuda(ctx, cudaEventRecord(e[2], ctx->stream), "tuning event");
+    if (rc == THC_OK) rc = check_cuda(ctx, cudaEventSynchronize(e[2]), "tuning sync");
+    if (rc == THC_OK) rc = check_cuda(ctx, cudaEventElapsedTime(&t128, e[0], e[1]), "tuning time");
+    if (rc == THC_OK) rc = check_cuda(ctx, cudaEventElapsedTime(&t256, e[1], e[2]), "tuning time");
+    for (auto& x : e) cudaEventDestroy(x);
+    THC_TRY(rc);
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    g_tile_table[key] = (t256 <= t128) ? 256 : 128;
+    return THC_OK;
+  }
+  if (!bn) {
+    const long long w128 = (N + 127) / 128 * 128, w256 = (N + 255) / 256 * 256;
+    bn = (w256 <= w128) ? 256 : 128;
+  }
+  if (bn == 256) return launch_split_gemm<256>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
   return launch_split_gemm<128>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
 }
 
@@ -520,6 +569,36 @@ int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* S
     THC_TRY(gemm(ctx, K_BACK, Xs, false, T2s, true, n, n, N, tc, EpiF64{Sigma + c0 * nn, n, nn}, "X T2"));
   }
   return THC_OK;
+}
+
+// ------------------------------------------------------- autotuner cache
+// Text file, one shape per line: kclass M N K batch BN.
+int autotune_save(const char* path) {
+  std::lock_guard<std::mutex> lock(g_tile_mu);
+  FILE* f = std::fopen(path, "w");
+  if (!f) return fail(nullptr, THC_EINVAL, std::string("cannot write ") + path);
+  for (const auto& kv : g_tile_table)
+    std::fprintf(f, "%d %lld %lld %lld %lld %d\n", kv.first.kclass, kv.first.M, kv.first.N, kv.first.K,
+                 kv.first.batch, kv.second);
+  std::fclose(f);
+  return THC_OK;
+}
+
+int autotune_load(const char* path) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(nullptr, THC_EINVAL, std::string("cannot read ") + path);
+  std::lock_guard<std::mutex> lock(g_tile_mu);
+  ShapeKey k;
+  int bn;
+  while (std::fscanf(f, "%d %lld %lld %lld %lld %d", &k.kclass, &k.M, &k.N, &k.K, &k.batch, &bn) == 6)
+    if (bn == 128 || bn == 256) g_tile_table[k] = bn;
+  std::fclose(f);
+  return THC_OK;
+}
+
+int autotune_entries() {
+  std::lock_guard<std::mutex> lock(g_tile_mu);
+  return (int)g_tile_table.size();
 }
 
 // --------------------------------------------------- standalone utility

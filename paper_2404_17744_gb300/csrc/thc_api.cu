@@ -53,6 +53,22 @@ void release(thc_ctx* ctx) {
   ctx->owned.clear();
 }
 
+// budget 0 -> THC_WORKSPACE_BYTES if set, else a quarter of the free device memory
+int default_budget(thc_ctx* ctx, size_t* budget) {
+  if (*budget > 0) return THC_OK;
+  if (const char* env = std::getenv("THC_WORKSPACE_BYTES")) {
+    const unsigned long long v = std::strtoull(env, nullptr, 10);
+    if (v > 0) {
+      *budget = (size_t)v;
+      return THC_OK;
+    }
+  }
+  size_t free_b = 0, total_b = 0;
+  THC_TRY(thc::check_cuda(ctx, cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo"));
+  *budget = free_b / 4;
+  return THC_OK;
+}
+
 int choose_blocking(thc_ctx* ctx, size_t budget) {
   const size_t d = sizeof(double);
   const size_t n = ctx->n, N = ctx->N;
@@ -68,7 +84,7 @@ int choose_blocking(thc_ctx* ctx, size_t budget) {
   return THC_OK;
 }
 
-int init_impl(thc_ctx* ctx, const double* X, const double* V, const double* tau) {
+int init_impl(thc_ctx* ctx, const double* X, const double* V, const double* tau, size_t budget_in) {
   using namespace thc;
   const size_t n = ctx->n, N = ctx->N, nt = ctx->n_tau;
   ctx->tau.assign(tau, tau + nt);
@@ -110,13 +126,8 @@ int init_impl(thc_ctx* ctx, const double* X, const double* V, const double* tau)
     THC_TRY(ctx_alloc(ctx, (void**)&ctx->Bblk, sizeof(double) * pb * Nn, "B block"));
     if (ctx->terms & THC_SOX) THC_TRY(fp64_build_U(ctx));
   } else {
-    size_t free_b = 0, total_b = 0;
-    THC_TRY(check_cuda(ctx, cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo"));
-    size_t budget = free_b / 4;
-    if (const char* env = std::getenv("THC_WORKSPACE_BYTES")) {
-      const unsigned long long v = std::strtoull(env, nullptr, 10);
-      if (v > 0) budget = (size_t)v;
-    }
+    size_t budget = budget_in;
+    THC_TRY(default_budget(ctx, &budget));
     THC_TRY(split_init(ctx, budget));
   }
   return THC_OK;
@@ -124,20 +135,18 @@ int init_impl(thc_ctx* ctx, const double* X, const double* V, const double* tau)
 
 }  // namespace
 
-extern "C" {
+namespace thc {
 
-int thc_sigma_init(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, const double* X, const double* V,
-                   const double* tau, int precision, int terms, void* stream) {
-  using namespace thc;
-  g_init_error.clear();
-  if (!out) return fail(nullptr, THC_EINVAL, "ctx out-pointer is NULL");
+int ctx_create(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, const double* X, const double* V,
+               const double* tau, int precision, int terms, cudaStream_t stream, size_t budget) {
   *out = nullptr;
   if (n_ao < 1 || n_thc < 1 || n_tau < 1 || !(beta > 0.0))
     return fail(nullptr, THC_EINVAL, "need n_ao, n_thc, n_tau >= 1 and beta > 0");
   if (n_thc > 65535) return fail(nullptr, THC_EINVAL, "n_thc above 65535 is not supported");
   if (!X || !V || !tau) return fail(nullptr, THC_EINVAL, "X, V and tau must be non-NULL");
   if (precision != THC_FP64 && precision != THC_BF16X3) return fail(nullptr, THC_EINVAL, "unknown precision");
-  if (terms <= 0 || terms > (THC_DIRECT | THC_SOX)) return fail(nullptr, THC_EINVAL, "terms must be a non-empty subset of THC_DIRECT|THC_SOX");
+  if (terms <= 0 || terms > (THC_DIRECT | THC_SOX))
+    return fail(nullptr, THC_EINVAL, "terms must be a non-empty subset of THC_DIRECT|THC_SOX");
   thc_ctx* ctx = nullptr;
   try {
     ctx = new thc_ctx();
@@ -150,10 +159,10 @@ int thc_sigma_init(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, c
   ctx->beta = beta;
   ctx->precision = precision;
   ctx->terms = terms;
-  ctx->stream = (cudaStream_t)stream;
+  ctx->stream = stream;
   int rc;
   try {
-    rc = init_impl(ctx, X, V, tau);
+    rc = init_impl(ctx, X, V, tau, budget);
   } catch (...) {
     rc = fail(ctx, THC_ENOMEM, "host allocation failed during init");
   }
@@ -165,6 +174,23 @@ int thc_sigma_init(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, c
   }
   *out = ctx;
   return THC_OK;
+}
+
+void ctx_destroy(thc_ctx* ctx) {
+  if (!ctx) return;
+  release(ctx);
+  delete ctx;
+}
+
+}  // namespace thc
+
+extern "C" {
+
+int thc_sigma_init(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, const double* X, const double* V,
+                   const double* tau, int precision, int terms, void* stream) {
+  g_init_error.clear();
+  if (!out) return thc::fail(nullptr, THC_EINVAL, "ctx out-pointer is NULL");
+  return thc::ctx_create(out, n_ao, n_thc, n_tau, beta, X, V, tau, precision, terms, (cudaStream_t)stream, 0);
 }
 
 int thc_sigma_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma_tau) {
@@ -269,11 +295,33 @@ int thc_profile_get(thc_ctx* ctx, int kclass, const char** name, long long* laun
 
 long long thc_launch_count(const thc_ctx* ctx) { return ctx ? ctx->launch_count : 0; }
 
-void thc_destroy(thc_ctx* ctx) {
-  if (!ctx) return;
-  release(ctx);
-  delete ctx;
+void thc_destroy(thc_ctx* ctx) { thc::ctx_destroy(ctx); }
+
+int thc_sigma_tune(thc_ctx* ctx, const double* G_tau, const double* G_bmt) {
+  using namespace thc;
+  if (!ctx) return fail(nullptr, THC_EINVAL, "ctx is NULL");
+  if (!G_tau) return fail(ctx, THC_EINVAL, "G_tau must be non-NULL");
+  if (ctx->precision != THC_BF16X3) return THC_OK;  // the FP64 path has one tile shape
+  const size_t bytes = sizeof(double) * (size_t)ctx->n_tau * ctx->n * ctx->n;
+  if (!ctx->hS) THC_TRY(ctx_alloc(ctx, (void**)&ctx->hS, bytes, "tuning output"));
+  ctx->tuning = true;
+  int rc = thc_sigma_eval(ctx, G_tau, G_bmt, ctx->hS);
+  ctx->tuning = false;
+  THC_TRY(rc);
+  return thc_sync(ctx);
 }
+
+int thc_autotune_save(const char* path) {
+  if (!path) return thc::fail(nullptr, THC_EINVAL, "thc_autotune_save: NULL path");
+  return thc::autotune_save(path);
+}
+
+int thc_autotune_load(const char* path) {
+  if (!path) return thc::fail(nullptr, THC_EINVAL, "thc_autotune_load: NULL path");
+  return thc::autotune_load(path);
+}
+
+int thc_autotune_entries(void) { return thc::autotune_entries(); }
 
 const char* thc_last_error(const thc_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_init_error.c_str();

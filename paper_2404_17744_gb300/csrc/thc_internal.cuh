@@ -89,6 +89,7 @@ struct thc_ctx {
 
   std::vector<void*> owned;  // every cudaMalloc of this context
   std::string err;
+  bool tuning = false;       // split path: time the tile widths of unseen contraction shapes
 
   // launch accounting and the optional profiler
   long long launch_count = 0;
@@ -118,6 +119,17 @@ int fp64_build_U(thc_ctx* ctx);
 int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma);
 int energy_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const double* Sigma,
                 const double* w_host, double* E);
+
+// Context creation with an explicit workspace budget (0: a quarter of the free memory,
+// or THC_WORKSPACE_BYTES); the batched API gives every molecule its own budget.
+int ctx_create(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, const double* X, const double* V,
+               const double* tau, int precision, int terms, cudaStream_t stream, size_t budget);
+void ctx_destroy(thc_ctx* ctx);
+
+// autotuner table of the split contractions (sigma_split.cu)
+int autotune_save(const char* path);
+int autotune_load(const char* path);
+int autotune_entries();
 
 // split-precision path (sigma_split.cu)
 int split_init(thc_ctx* ctx, size_t budget);

@@ -118,6 +118,29 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_proposer_last_error.restype = ctypes.c_char_p
     lib.thc_proposer_destroy.argtypes = [vp]
     lib.thc_proposer_destroy.restype = None
+    # batched evaluation (include/thc_batch.h) and the autotuner
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    IP = ctypes.POINTER(ctypes.c_int)
+    lib.thc_batch_init.argtypes = [ctypes.POINTER(vp), i, IP, IP, i, d, PP, PP, dp, i, i, ctypes.c_ulonglong, i, vp]
+    lib.thc_batch_init.restype = i
+    lib.thc_batch_eval.argtypes = [vp, PP, PP]
+    lib.thc_batch_eval.restype = i
+    lib.thc_batch_graph_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+    lib.thc_batch_graph_info.restype = i
+    lib.thc_batch_flops.argtypes = [vp]
+    lib.thc_batch_flops.restype = d
+    lib.thc_batch_last_error.argtypes = [vp]
+    lib.thc_batch_last_error.restype = ctypes.c_char_p
+    lib.thc_batch_destroy.argtypes = [vp]
+    lib.thc_batch_destroy.restype = None
+    lib.thc_sigma_tune.argtypes = [vp, dp, dp]
+    lib.thc_sigma_tune.restype = i
+    lib.thc_autotune_save.argtypes = [ctypes.c_char_p]
+    lib.thc_autotune_save.restype = i
+    lib.thc_autotune_load.argtypes = [ctypes.c_char_p]
+    lib.thc_autotune_load.restype = i
+    lib.thc_autotune_entries.argtypes = []
+    lib.thc_autotune_entries.restype = i
     lib.thc_last_error.argtypes = [vp]
     lib.thc_last_error.restype = ctypes.c_char_p
     if path is None:
@@ -380,3 +403,59 @@ def thc_proposer_propose(p, Sigma_tau):
 
 def thc_proposer_destroy(p):
     load_library().thc_proposer_destroy(p)
+
+
+# --------------------------------------------------------- batched ABI
+def _ptr_array(xs):
+    return (ctypes.c_void_p * len(xs))(*[_ptr(x).value for x in xs])
+
+
+def thc_batch_init(n_ao, n_thc, n_tau, beta, X, V, tau, precision=THC_BF16X3, n_streams=4, budget_per_molecule=0,
+                   tune=True, stream=None):
+    import numpy as np
+    b = ctypes.c_void_p()
+    k = len(n_ao)
+    na = (ctypes.c_int * k)(*[int(x) for x in n_ao])
+    nt = (ctypes.c_int * k)(*[int(x) for x in n_thc])
+    t = np.ascontiguousarray(tau, dtype=np.float64)
+    lib = load_library()
+    rc = lib.thc_batch_init(ctypes.byref(b), k, na, nt, int(n_tau), float(beta), _ptr_array(X), _ptr_array(V),
+                            _ptr(t), int(precision), int(n_streams), int(budget_per_molecule), int(bool(tune)),
+                            _stream(stream))
+    _lcheck(rc, lib.thc_batch_last_error, None)
+    return b
+
+
+def thc_batch_eval(b, G_tau, Sigma_tau):
+    lib = load_library()
+    _lcheck(lib.thc_batch_eval(b, _ptr_array(G_tau), _ptr_array(Sigma_tau)), lib.thc_batch_last_error, b)
+
+
+def thc_batch_graph_info(b):
+    k, n = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load_library().thc_batch_graph_info(b, ctypes.byref(k), ctypes.byref(n)), None)
+    return k.value, n.value
+
+
+def thc_batch_flops(b) -> float:
+    return float(load_library().thc_batch_flops(b))
+
+
+def thc_batch_destroy(b):
+    load_library().thc_batch_destroy(b)
+
+
+def thc_sigma_tune(ctx, G_tau, G_bmt=None):
+    _check(load_library().thc_sigma_tune(ctx, _ptr(G_tau), _ptr(G_bmt)), ctx)
+
+
+def thc_autotune_save(path):
+    _check(load_library().thc_autotune_save(str(path).encode()), None)
+
+
+def thc_autotune_load(path):
+    _check(load_library().thc_autotune_load(str(path).encode()), None)
+
+
+def thc_autotune_entries() -> int:
+    return int(load_library().thc_autotune_entries())
