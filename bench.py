@@ -271,6 +271,47 @@ def loop_measure(case, precision, stream, tol=1e-8, proposer=None):
             "dyson_evals_per_iteration": float(np.mean([r.dyson_evals for r in recs[:-1]])) if len(recs) > 1 else 0.0}
 
 
+def batch_measure(cases, precision, steps, warmup, stream):
+    """Batched evaluation of `cases` in one CUDA graph: useful TFLOP/s and seconds per batch."""
+    import torch
+    from paper_2404_17744_gb300 import thc
+    dev = stream.device
+    with torch.cuda.stream(stream):
+        X = [torch.from_numpy(c.X).to(dev) for c in cases]
+        V = [torch.from_numpy(c.V).to(dev) for c in cases]
+        G = [torch.from_numpy(c.G_tau).to(dev) for c in cases]
+        S = [torch.empty_like(g) for g in G]
+        stream.synchronize()
+        c0 = cases[0]
+        t0 = time.perf_counter()
+        b = thc.thc_batch_init([c.n for c in cases], [c.N for c in cases], c0.n_tau, c0.beta, X, V, c0.tau,
+                               precision, 4, 0, True, stream.cuda_stream)
+        t_init = time.perf_counter() - t0
+        try:
+            t0 = time.perf_counter()
+            thc.thc_batch_eval(b, G, S)          # warm-up + autotune + capture + first launch
+            stream.synchronize()
+            t_first = time.perf_counter() - t0
+            for _ in range(max(0, warmup - 1)):
+                thc.thc_batch_eval(b, G, S)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                thc.thc_batch_eval(b, G, S)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            kernels, nodes = thc.thc_batch_graph_info(b)
+            flops = thc.thc_batch_flops(b)
+        finally:
+            thc.thc_batch_destroy(b)
+    return {"molecules": len(cases), "n_ao": [int(c.n) for c in cases], "n_tau": int(c0.n_tau),
+            "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (useful)", "s_per_batch_eval": ms / 1e3,
+            "graph_kernels": int(kernels), "graph_nodes": int(nodes), "init_s": t_init,
+            "first_eval_s_incl_tuning_and_capture": t_first, "flops_per_eval": flops}
+
+
 def run_ours(args):
     import torch
     from paper_2404_17744_gb300 import thc
@@ -329,6 +370,14 @@ def run_ours(args):
             split["value"] = world * flops_step * args.steps / (rsp["total_ms"] * 1e-3) / 1e12
             split["max_abs_dsigma_vs_fp64"] = float((S_split - S).abs().max().item())
             split["abs_dE_vs_fp64"] = abs(rsp["energy"] - r64["energy"])
+
+        batched = None
+        if not args.no_split:
+            from workloads import batch as wb
+            bcases = wb.make_batch(16, 50, 200, 32, 100.0, seed=17748)
+            batched = batch_measure(bcases, thc.THC_BF16X3, args.steps, args.warmup, stream)
+            batched["workload"] = ("16 molecules, n_ao uniform in [50, 200], n_thc = 5 n_ao, 32 Gauss-Legendre tau "
+                                   "points, beta = 100, 3xBF16, 4 worker streams, one CUDA-graph launch per eval")
 
         loop = None
         if not args.no_loop:
@@ -393,6 +442,8 @@ def run_ours(args):
                                     f"products of every useful multiply-add", 3.0, args.workload + ":bf16x3"),
             "kernels": {k: {kk: v[kk] for kk in ("launches", "ms", "tflops")} for k, v in split["kernels"].items()},
         }
+    if batched:
+        line["batched"] = batched
     if loop:
         line["scgf2_loop"] = loop
         line["config"]["s_per_scgf2_iteration_fp64"] = loop["fp64"]["s_per_iteration"]
@@ -406,10 +457,34 @@ def run_ours(args):
     return 0
 
 
+def run_batch64(args):
+    """64 molecules, n_ao uniform in [50, 400], n_thc = 5 n_ao, 100 tau points: one graph per evaluation."""
+    import torch
+    from paper_2404_17744_gb300 import thc
+    from workloads import batch as wb
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(device=torch.device("cuda", local))
+    cases = wb.make_batch(64, 50, 400, 100, 100.0, seed=17747)
+    r = batch_measure(cases, thc.THC_BF16X3, args.steps, args.warmup, stream)
+    line = {"metric": METRIC, "value": r["value"] * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["s_per_batch_eval"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+            "config": {"workload": "batch64: 64 molecules, n_ao uniform in [50, 400], n_thc = 5 n_ao, 100 "
+                                   "Gauss-Legendre tau points, beta = 100; 3xBF16 tensor cores; one CUDA-graph "
+                                   "launch per evaluation over 4 worker streams; tile widths from the autotuner"},
+            "gpu_launches": r["graph_kernels"] * args.steps, "batched": r}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch64(args)
     return run_ours(args)
 
 
