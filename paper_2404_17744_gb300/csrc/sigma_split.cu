@@ -85,12 +85,14 @@ int make_map(thc_ctx* ctx, CUtensorMap* m, const bf16* base, long long K, const 
 
 // ------------------------------------------------------------ epilogues
 // Each functor is run by one warp on a 32 x 32 chunk of the output tile:
-// tile[r][j] = C[row0 + r][col0 + j]; rows >= M and columns >= N are skipped.
-using Tile = float (*)[33];
+// t(r, j) = C[row0 + r][col0 + j]; rows >= M and columns >= N are skipped.
+using Tile = tc::TileRef;
 
-// Functors without global reads in their epilogue prefetch nothing.
-#define THC_NO_PREFETCH \
-  __device__ void prefetch(int, int, int, int, int, int) const {}
+// Functors without global reads in their epilogue prefetch and stage nothing.
+#define THC_NO_PREFETCH                                                      \
+  static constexpr bool kStagesRows = false;                                 \
+  __device__ void prefetch(int, int, int, int, int, int) const {}            \
+  __device__ void stage_rows(int, int, int, int, int, int, float*) const {}
 
 __device__ __forceinline__ void split_store(bf16* hi, bf16* lo, long long o, float v) {
   const bf16 h = __float2bfloat16_rn(v);
@@ -105,19 +107,19 @@ struct EpiSplit {
   bf16 *hi, *lo;
   long long ld, bs;
   float scale;
-  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N) const {
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N, const float*, int) const {
     if (TRANSPOSED) {  // lanes along rows: dst(b, col, row) is contiguous in row
       const int row = row0 + lane;
       if (row >= M) return;
 #pragma unroll 4
       for (int j = 0; j < 32; ++j)
-        if (col0 + j < N) split_store(hi, lo, (long long)b * bs + (long long)(col0 + j) * ld + row, scale * t[lane][j]);
+        if (col0 + j < N) split_store(hi, lo, (long long)b * bs + (long long)(col0 + j) * ld + row, scale * t(lane, j));
     } else {           // lanes along columns
       const int col = col0 + lane;
       if (col >= N) return;
 #pragma unroll 4
       for (int r = 0; r < 32; ++r)
-        if (row0 + r < M) split_store(hi, lo, (long long)b * bs + (long long)(row0 + r) * ld + col, scale * t[r][lane]);
+        if (row0 + r < M) split_store(hi, lo, (long long)b * bs + (long long)(row0 + r) * ld + col, scale * t(r, lane));
     }
   }
 };
@@ -128,14 +130,14 @@ struct EpiAt {
   bf16 *hi, *lo;
   int n;
   long long ld;
-  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int N) const {
+  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int N, const float*, int) const {
     const int row = row0 + lane;
     if (row >= M) return;
     const int P = row / n, q = row - P * n;
     const long long base = (long long)P * n * ld + q;
 #pragma unroll 4
     for (int j = 0; j < 32; ++j)
-      if (col0 + j < N) split_store(hi, lo, base + (long long)(col0 + j) * ld, t[lane][j]);
+      if (col0 + j < N) split_store(hi, lo, base + (long long)(col0 + j) * ld, t(lane, j));
   }
 };
 
@@ -144,13 +146,13 @@ struct EpiF32 {
   THC_NO_PREFETCH
   float* dst;
   long long ld, bs;
-  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N) const {
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N, const float*, int) const {
     const int col = col0 + lane;
     if (col >= N) return;
     float* d = dst + (long long)b * bs + col;
 #pragma unroll 4
     for (int r = 0; r < 32; ++r)
-      if (row0 + r < M) d[(long long)(row0 + r) * ld] = t[r][lane];
+      if (row0 + r < M) d[(long long)(row0 + r) * ld] = t(r, lane);
   }
 };
 
@@ -159,45 +161,61 @@ struct EpiF64 {
   THC_NO_PREFETCH
   double* dst;
   long long ld, bs;
-  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N) const {
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N, const float*, int) const {
     const int col = col0 + lane;
     if (col >= N) return;
     double* d = dst + (long long)b * bs + col;
 #pragma unroll 4
     for (int r = 0; r < 32; ++r)
-      if (row0 + r < M) d[(long long)(row0 + r) * ld] = (double)t[r][lane];
+      if (row0 + r < M) d[(long long)(row0 + r) * ld] = (double)t(r, lane);
   }
 };
 
 // Hadamard-reduce of the fused C/D step: b = R, row = P (local), col = v.
-//   D[(P0 + P) N + R] += sum_v C[P][v] B[P][R][v]
-// The epilogue warps prefetch their B rows into L2 while the tile is being
-// accumulated; the chunk is then multiplied in place by B (32 coalesced loads
-// in flight per lane) and lane r sums row r into one FP64 atomic.
+//   D[(P0 + P) N + R] += sum_v C[P][v] B[R][P][v]
+// B is stored R-major ([R][P][v], P local to the block).  While a tile
+// accumulates, every epilogue thread copies its row of B into shared memory
+// with 16-byte cp.async (rows of n % 4 != 0 floats are read from global memory
+// in the functor instead); the chunk is then multiplied in place and lane r
+// sums row r into one FP64 atomic.
 struct EpiHad {
-  const float* Bf;  // Pb x N x n
+  const float* Bf;  // N x Pc x n
   double* D;
-  int n, N, P0;
-  __device__ void prefetch(int b, int row, int col0, int ncols, int M, int Ncols) const {
-    if (row >= M || col0 >= Ncols) return;
-    const float* p = Bf + ((long long)row * N + b) * n + col0;
-    const int cnt = min(ncols, Ncols - col0);
-    for (int c = 0; c < cnt; c += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + c));
+  int n, N, P0, Pc;
+  static constexpr bool kStagesRows = true;
+  __device__ void prefetch(int, int, int, int, int, int) const {}
+  __device__ void stage_rows(int b, int row, int col0, int ncols, int M, int Ncols, float* dst) const {
+    if (row >= M || col0 >= Ncols || (n & 3)) return;
+    const float* src = Bf + ((long long)b * Pc + row) * n + col0;
+    const int cnt = min(ncols, Ncols - col0);  // a multiple of 4 when n is
+    for (int c = 0; c < cnt; c += 4) tc::cp_async16(dst + c, src + c);
   }
-  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols) const {
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols, const float* rows,
+                             int rstride) const {
     const int col = col0 + lane;
-    float bv[32];
+    if (!(n & 3)) {
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) {
+        const int P = row0 + r;
+        t(r, lane) = (P < M && col < Ncols) ? t(r, lane) * rows[r * rstride + lane] : 0.f;
+      }
+    } else {
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const int P = row0 + r;
-      bv[r] = (P < M && col < Ncols) ? __ldg(Bf + ((long long)P * N + b) * n + col) : 0.f;
+      for (int r0 = 0; r0 < 32; r0 += 16) {  // two passes of 16 loads in flight
+        float bv[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int P = row0 + r0 + r;
+          bv[r] = (P < M && col < Ncols) ? __ldg(Bf + ((long long)b * Pc + P) * n + col) : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r) t(r0 + r, lane) *= bv[r];
+      }
     }
-#pragma unroll
-    for (int r = 0; r < 32; ++r) t[r][lane] *= bv[r];
     __syncwarp();
     float sum = 0.f;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) sum += t[lane][j];
+    for (int j = 0; j < 32; ++j) sum += t(lane, j);
     if (row0 + lane < M) atomicAdd(&D[((long long)P0 + row0 + lane) * N + b], (double)sum);
   }
 };
@@ -210,7 +228,7 @@ struct EpiMerge {
   const double* D;  // may be null
   const float* GX;
   int N;
-  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols) const {
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols, const float*, int) const {
     const int P = col0 + lane;
     if (P >= Ncols) return;
     const long long NN = (long long)N * N;
@@ -218,7 +236,7 @@ struct EpiMerge {
     for (int r = 0; r < 32; ++r) {
       const int R = row0 + r;
       if (R >= M) break;
-      double m = C_DIRECT * (double)GX[b * NN + (long long)R * N + P] * (double)t[r][lane];
+      double m = C_DIRECT * (double)GX[b * NN + (long long)R * N + P] * (double)t(r, lane);
       if (D) m += C_SOX * D[b * NN + (long long)P * N + R];
       split_store(hi, lo, (long long)b * N * ld + (long long)R * ld + P, (float)m);
     }
@@ -231,7 +249,7 @@ struct EpiU {
   bf16 *hi, *lo;
   int n, q0;
   long long ld;
-  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int Ncols) const {
+  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int Ncols, const float*, int) const {
     const int c = col0 + lane;
     if (c >= Ncols) return;
     const int q = q0 + c / n, s = c - (c / n) * n;
@@ -239,7 +257,7 @@ struct EpiU {
     for (int r = 0; r < 32; ++r) {
       const int P = row0 + r;
       if (P >= M) break;
-      split_store(hi, lo, ((long long)P * n + q) * ld + s, t[r][lane]);
+      split_store(hi, lo, ((long long)P * n + q) * ld + s, t(r, lane));
     }
   }
 };
@@ -316,28 +334,36 @@ int launch_split_f64(thc_ctx* ctx, const double* src, long long sb, long long sr
 
 // ----------------------------------------------------------- GEMM launch
 // C[b](M x N) = A[b](M x K) B[b](N x K)^T in split precision; epi consumes C.
-template <int BN, class Epi>
+template <int BN, bool MULTI, class Epi>
 int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, const Split& B, bool b_batched,
                       long long M, long long N, long long K, long long batch, const Epi& epi, const char* what) {
   if (M <= 0 || N <= 0 || batch <= 0) return THC_OK;
-  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX || batch > 65535)
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX || batch > INT32_MAX)
     return fail(ctx, THC_EINVAL, std::string(what) + ": contraction too large");
   CUtensorMap ah, al, bh, bl;
   THC_TRY(make_map(ctx, &ah, A.hi, K, A, tc::BM));
   THC_TRY(make_map(ctx, &al, A.lo, K, A, tc::BM));
   THC_TRY(make_map(ctx, &bh, B.hi, K, B, BN));
   THC_TRY(make_map(ctx, &bl, B.lo, K, B, BN));
-  auto kern = tc::split_gemm_kernel<BN, Epi>;
+  auto kern = tc::split_gemm_kernel<BN, MULTI, Epi>;
+  using CfgE = Cfg<BN, Epi::kStagesRows ? BN / 2 : 0>;
   static bool attr_set = false;  // one per instantiation
   if (!attr_set) {
-    THC_TRY(check_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN>::SMEM),
+    THC_TRY(check_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgE::SMEM),
                        "split gemm smem attribute"));
     attr_set = true;
   }
-  const dim3 grid((unsigned)((M + tc::BM - 1) / tc::BM), (unsigned)((N + BN - 1) / BN), (unsigned)batch);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    THC_TRY(check_cuda(ctx, cudaGetDevice(&dev), "device"));
+    THC_TRY(check_cuda(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count"));
+  }
+  const long long tiles = ((M + tc::BM - 1) / tc::BM) * ((N + BN - 1) / BN) * batch;
+  const dim3 grid((unsigned)std::min<long long>(tiles, sms), 1, 1);  // persistent: one CTA per SM at most
   ProfRec rec;
   THC_TRY(prof_begin(ctx, kclass, 2.0 * M * N * K * batch, &rec));
-  kern<<<grid, tc::NTHREADS, Cfg<BN>::SMEM, ctx->stream>>>(ah, al, bh, bl, (int)M, (int)N, (int)K,
+  kern<<<grid, tc::NTHREADS, CfgE::SMEM, ctx->stream>>>(ah, al, bh, bl, (int)M, (int)N, (int)K, (int)batch,
                                                             tc::Operands{a_batched ? 1 : 0, b_batched ? 1 : 0}, epi,
                                                             ctx->d_err);
   return prof_end(ctx, &rec, cudaGetLastError(), what);
@@ -363,9 +389,20 @@ struct ShapeKey {
 std::map<ShapeKey, int> g_tile_table;
 std::mutex g_tile_mu;
 
+// K up to kSingleChunkK accumulates inside TMEM (single-chunk mode); longer K
+// is promoted to FP32 registers every stage, with BN = 128 so the register
+// accumulator does not spill.
+constexpr long long kSingleChunkK = 256;
+
 template <class Epi>
 int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool bb, long long M, long long N,
          long long K, long long batch, const Epi& epi, const char* what) {
+  // Functors that stage an input row per output row (the fused C/D contraction) run
+  // promoted at BN = 128: their rows are copied in while the stages drain.
+  if constexpr (Epi::kStagesRows) {
+    return launch_split_gemm<128, true>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+  } else {
+  if (K > kSingleChunkK) return launch_split_gemm<128, true>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
   const ShapeKey key{kclass, M, N, K, batch};
   int bn = 0;
   {
@@ -378,9 +415,9 @@ int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool
     for (auto& x : e) THC_TRY(check_cuda(ctx, cudaEventCreate(&x), "tuning event"));
     float t128 = 0.f, t256 = 0.f;
     int rc = check_cuda(ctx, cudaEventRecord(e[0], ctx->stream), "tuning event");
-    if (rc == THC_OK) rc = launch_split_gemm<128>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+    if (rc == THC_OK) rc = launch_split_gemm<128, false>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
     if (rc == THC_OK) rc = check_cuda(ctx, cudaEventRecord(e[1], ctx->stream), "tuning event");
-    if (rc == THC_OK) rc = launch_split_gemm<256>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+    if (rc == THC_OK) rc = launch_split_gemm<256, false>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
     if (rc == THC_OK) rc = check_cuda(ctx, cudaEventRecord(e[2], ctx->stream), "tuning event");
     if (rc == THC_OK) rc = check_cuda(ctx, cudaEventSynchronize(e[2]), "tuning sync");
     if (rc == THC_OK) rc = check_cuda(ctx, cudaEventElapsedTime(&t128, e[0], e[1]), "tuning time");
@@ -395,8 +432,9 @@ int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool
     const long long w128 = (N + 127) / 128 * 128, w256 = (N + 255) / 256 * 256;
     bn = (w256 <= w128) ? 256 : 128;
   }
-  if (bn == 256) return launch_split_gemm<256>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
-  return launch_split_gemm<128>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+  if (bn == 256) return launch_split_gemm<256, false>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+  return launch_split_gemm<128, false>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
+  }
 }
 
 Split split_of(bf16* hi, bf16* lo, long long rows, long long ld, long long batch = 1) {
@@ -548,11 +586,11 @@ int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* S
           // A^T_P[v][q] = sum_s U[P q][s] G(-tau)[v][s]  (G(-tau) carries its sign in Gms)
           THC_TRY(gemm(ctx, K_SOX_A, U.at_row(P0 * n, Pc * n), false, Gmk, false, Pc * n, n, n, 1,
                        EpiAt{At.hi, At.lo, (int)n, ldn}, "A"));
-          // B_P[R][v] = sum_q Y[R][q] A^T_P[v][q]
-          THC_TRY(gemm(ctx, K_SOX_B, Yk, false, At, true, N, n, n, Pc, EpiF32{ctx->Bf, n, N * n}, "B"));
+          // B_P[R][v] = sum_q Y[R][q] A^T_P[v][q], stored R-major: Bf[R][P][v]
+          THC_TRY(gemm(ctx, K_SOX_B, Yk, false, At, true, N, n, n, Pc, EpiF32{ctx->Bf, Pc * n, n}, "B"));
           // D[P][R] += sum_v (sum_w Y[P][w] U_R[v][w]) B_P[R][v]
           THC_TRY(gemm(ctx, K_SOX_CD, Yk.at_row(P0, Pc), false, Ub, true, Pc, n, n, N,
-                       EpiHad{ctx->Bf, Dk, (int)n, (int)N, (int)P0}, "C/D"));
+                       EpiHad{ctx->Bf, Dk, (int)n, (int)N, (int)P0, (int)Pc}, "C/D"));
         }
       }
     }

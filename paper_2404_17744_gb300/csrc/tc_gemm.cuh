@@ -9,7 +9,13 @@
 // brought to by the symmetry of G, U_Pqs and V or by writing its producer's
 // output transposed.
 //
-// One CTA computes one 128 x BN output tile with three warp roles:
+// The kernel is persistent: one CTA per SM walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... of all batches (tile order: row block fastest,
+// so consecutive tiles share their B operand), and every role counts K stages
+// with one running counter across tiles.  The producer therefore loads the
+// next tile while the current one drains and stores, and the MMA warp runs
+// ahead into the two TMEM stage buffers during the store phase.
+// Each tile is 128 x BN, computed by three warp roles:
 //   warp 0    one lane issues the TMA loads (128-byte swizzle) of the four
 //             operand tiles of each 64-deep K stage into a STAGES-deep ring;
 //   warp 1    allocates TMEM; one lane issues the 3 x 4 tcgen05.mma
@@ -19,13 +25,21 @@
 //   warps 2-9 drain each finished stage accumulator with tcgen05.ld into FP32
 //             registers (warp w owns TMEM lanes 32 (w % 4) .. and one half of
 //             the columns), free it for the stage after next, and finally hand
-//             32 x 32 chunks, staged in shared memory, to the epilogue functor,
-//             which the whole warp runs with coalesced global accesses.
+//             32 x 32 chunks, staged in a private XOR-swizzled shared-memory
+//             tile, to the epilogue functor, which the whole warp runs with
+//             coalesced global accesses.  A functor that reads one input value
+//             per output element (kStagesRows) has those rows copied into
+//             shared memory with cp.async while its tile accumulates.
 // Draining every stage ("promotion") keeps the tensor core's internal
 // accumulation to one 64-deep stage: measured on GB300, accumulating a
 // 1000-deep K inside the tensor core loses several times more precision than
 // IEEE FP32 additions of 64-deep partial sums, enough to break a 1e-6
-// absolute bound on the self-energy.
+// absolute bound on the self-energy.  Up to K = 256 the in-TMEM accumulation
+// measured as accurate as promotion, so contractions that short run in the
+// single-chunk mode (MULTI = false): the whole K accumulates in one TMEM
+// buffer, tiles alternate between the two buffers (the epilogue of one tile
+// overlaps the MMAs of the next), and the epilogue streams 32-column slices
+// straight from TMEM without a register accumulator.
 // Every mbarrier wait is bounded in time (globaltimer); a wait that runs out
 // sets *err and the CTA unwinds, frees its TMEM and returns.
 #pragma once
@@ -44,17 +58,31 @@ constexpr int NTHREADS = 320;  // 10 warps: TMA, MMA, 8 epilogue
 constexpr int NEPI = 256;      // epilogue threads
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s per wait
 
-template <int BN>
+template <int BN, int ROWS = 0>
 struct Cfg {
+  // ROWS: FP32 values per output row the epilogue functor stages (0 or BN / 2)
   static constexpr int A_BYTES = BM * BKE * 2;
   static constexpr int B_BYTES = BN * BKE * 2;
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int STAGES = (BN >= 256) ? 2 : 3;
-  static constexpr int TMEM_COLS = 2 * BN;   // two stage accumulators; BN in {128, 256}
-  static constexpr int HALF = BN / 2;         // columns drained per epilogue thread
-  static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int TMEM_COLS = 2 * BN;   // two accumulators; BN in {128, 256}
+  static constexpr int HALF = BN / 2;         // columns per epilogue thread
+  static constexpr int STAGING = 8 * 32 * 32 * 4;      // one swizzled 32 x 32 FP32 tile per epilogue warp
+  static constexpr int ROW_STAGING = 8 * 32 * ROWS * 4;  // staged functor inputs, 32 rows per epilogue warp
+  static constexpr int FIXED = STAGING + ROW_STAGING + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int STAGES = ((232448 - FIXED) / STAGE) >= 3 ? 3 : 2;
+  static constexpr int SMEM = STAGES * STAGE + FIXED;
+  static_assert(SMEM <= 232448, "shared memory per CTA");
   static_assert(BN == 128 || BN == 256, "tile width");
+  static_assert(ROWS == 0 || ROWS == BN / 2, "staged row width");
 };
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -171,29 +199,39 @@ __device__ __forceinline__ void tmem_ld16_add(uint32_t taddr, float* acc) {
   for (int i = 0; i < 16; ++i) acc[i] += __uint_as_float(r[i]);
 }
 
+// A 32 x 32 FP32 tile with XOR swizzle: element (r, c) at r * 32 + (c ^ r), so
+// that both row walks (fixed r) and column walks (fixed c) are bank-conflict free.
+struct TileRef {
+  float* p;
+  __device__ __forceinline__ float& operator()(int r, int c) const { return p[r * 32 + (c ^ r)]; }
+};
+
 // Operand maps: each is a 3-D tensor map (k, row, batch) over BF16 with a
 // 64 x rows box and 128-byte swizzle.  batched = 0 pins the batch coordinate to 0.
 struct Operands {
   int a_batched, b_batched;
 };
 
-template <int BN, class Epi>
+template <int BN, bool MULTI, class Epi>
 __global__ void __launch_bounds__(NTHREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                       const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int M,
-                      int N, int K, Operands ops, Epi epi, int* err) {
-  using C = Cfg<BN>;
+                      int N, int K, int batch, Operands ops, Epi epi, int* err) {
+  using C = Cfg<BN, Epi::kStagesRows ? BN / 2 : 0>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  float* staging = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE);
+  float* row_staging = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + C::STAGING);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STAGING + C::ROW_STAGING);
   uint64_t* empty = full + C::STAGES;
   uint64_t* acc_full = empty + C::STAGES;  // [2] stage accumulator ready for the epilogue
   uint64_t* acc_free = acc_full + 2;       // [2] stage accumulator drained
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_free + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, b = blockIdx.z;
   const int nkb = (K + BKE - 1) / BKE;
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  const long long tiles = (long long)tm * tn * batch;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -221,82 +259,152 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      const int ab = ops.a_batched ? b : 0, bb = ops.b_batched ? b : 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % C::STAGES, r = kb / C::STAGES;
-        if (!mbar_wait(&empty[s], (r & 1) ^ 1)) {
-          atomicExch(err, 1);
-          break;
+      long long g = 0;  // running K-stage counter across tiles
+      bool ok = true;
+      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const int mt = (int)(t % tm), nt = (int)((t / tm) % tn), b = (int)(t / ((long long)tm * tn));
+        const int ab = ops.a_batched ? b : 0, bb = ops.b_batched ? b : 0;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % C::STAGES);
+          const uint32_t r = (uint32_t)(g / C::STAGES);
+          if (!mbar_wait(&empty[s], (r & 1) ^ 1)) {
+            atomicExch(err, 1);
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * C::STAGE;
+          mbar_arrive_expect_tx(&full[s], C::STAGE);
+          tma_load_3d(st, &mAhi, &full[s], kb * BKE, mt * BM, ab);
+          tma_load_3d(st + C::A_BYTES, &mAlo, &full[s], kb * BKE, mt * BM, ab);
+          tma_load_3d(st + 2 * C::A_BYTES, &mBhi, &full[s], kb * BKE, nt * BN, bb);
+          tma_load_3d(st + 2 * C::A_BYTES + C::B_BYTES, &mBlo, &full[s], kb * BKE, nt * BN, bb);
         }
-        uint8_t* st = smem + s * C::STAGE;
-        mbar_arrive_expect_tx(&full[s], C::STAGE);
-        tma_load_3d(st, &mAhi, &full[s], kb * BKE, m0, ab);
-        tma_load_3d(st + C::A_BYTES, &mAlo, &full[s], kb * BKE, m0, ab);
-        tma_load_3d(st + 2 * C::A_BYTES, &mBhi, &full[s], kb * BKE, n0, bb);
-        tma_load_3d(st + 2 * C::A_BYTES + C::B_BYTES, &mBlo, &full[s], kb * BKE, n0, bb);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % C::STAGES, r = kb / C::STAGES, buf = kb & 1, use = kb >> 1;
-        if (!mbar_wait(&acc_free[buf], (use & 1) ^ 1) || !mbar_wait(&full[s], r & 1)) {
-          atomicExch(err, 2);
-          break;
+      long long g = 0, local = 0;  // K stages and tiles handled by this CTA
+      bool ok = true;
+      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++local) {
+        if (!MULTI) {  // one accumulator per tile, alternating between the two buffers
+          const int buf = (int)(local & 1);
+          if (!mbar_wait(&acc_free[buf], ((uint32_t)(local >> 1) & 1) ^ 1)) {
+            atomicExch(err, 2);
+            break;
+          }
         }
-        tc_fence_after();
-        const uint32_t d = tmem + static_cast<uint32_t>(buf * BN);
-        const uint32_t base = smem_u32(smem + s * C::STAGE);
-        const uint64_t ah = sw128_desc(base), al = sw128_desc(base + C::A_BYTES);
-        const uint64_t bh = sw128_desc(base + 2 * C::A_BYTES), bl = sw128_desc(base + 2 * C::A_BYTES + C::B_BYTES);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % C::STAGES);
+          const int buf = MULTI ? (int)(g & 1) : (int)(local & 1);
+          const uint32_t r = (uint32_t)(g / C::STAGES), use = (uint32_t)(g >> 1);
+          if ((MULTI && !mbar_wait(&acc_free[buf], (use & 1) ^ 1)) || !mbar_wait(&full[s], r & 1)) {
+            atomicExch(err, 2);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + static_cast<uint32_t>(buf * BN);
+          const uint32_t base = smem_u32(smem + s * C::STAGE);
+          const uint64_t ah = sw128_desc(base), al = sw128_desc(base + C::A_BYTES);
+          const uint64_t bh = sw128_desc(base + 2 * C::A_BYTES), bl = sw128_desc(base + 2 * C::A_BYTES + C::B_BYTES);
 #pragma unroll
-        for (int k = 0; k < BKE / 16; ++k) {
-          const uint64_t off = static_cast<uint64_t>((k * 32) >> 4);  // 16 BF16 = 32 bytes along K
-          mma_bf16(d, ah + off, bh + off, idesc, k != 0);
-          mma_bf16(d, ah + off, bl + off, idesc, 1u);
-          mma_bf16(d, al + off, bh + off, idesc, 1u);
+          for (int k = 0; k < BKE / 16; ++k) {
+            const uint64_t off = static_cast<uint64_t>((k * 32) >> 4);  // 16 BF16 = 32 bytes along K
+            mma_bf16(d, ah + off, bh + off, idesc, (MULTI ? k : (kb | k)) != 0);
+            mma_bf16(d, ah + off, bl + off, idesc, 1u);
+            mma_bf16(d, al + off, bh + off, idesc, 1u);
+          }
+          mma_commit(&empty[s]);  // frees the smem stage once these MMAs have read it
+          if (MULTI || kb == nkb - 1) mma_commit(&acc_full[buf]);  // accumulator ready
         }
-        mma_commit(&empty[s]);       // frees the smem stage once these MMAs have read it
-        mma_commit(&acc_full[buf]);  // stage accumulator ready
       }
+    }
+  } else if (!MULTI) {
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const TileRef tile{staging + (warp - 2) * 32 * 32};
+    long long local = 0;
+    auto prefetch_tile = [&](long long tt) {  // L2 warm-up of what the epilogue of tile tt reads
+      if (tt >= tiles) return;
+      const int pm = (int)(tt % tm), pn = (int)((tt / tm) % tn), pb = (int)(tt / ((long long)tm * tn));
+      epi.prefetch(pb, pm * BM + quarter * 32 + lane, pn * BN + half * C::HALF, C::HALF, M, N);
+    };
+    prefetch_tile(blockIdx.x);
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
+      const int mt = (int)(t % tm), nt = (int)((t / tm) % tn), b = (int)(t / ((long long)tm * tn));
+      const int m0 = mt * BM, n0 = nt * BN, buf = (int)(local & 1);
+      // one tile ahead: by the time this CTA stores tile t + gridDim.x its inputs are in L2
+      prefetch_tile(t + gridDim.x);
+      if (!mbar_wait(&acc_full[buf], (uint32_t)(local >> 1) & 1)) {
+        if (lane == 0) atomicExch(err, 3);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t src = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + buf * BN + half * C::HALF;
+      const int row0 = m0 + quarter * 32;
+#pragma unroll 1
+      for (int c = 0; c < C::HALF; c += 32) {
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        tmem_ld16_add(src + c, v);
+        tmem_ld16_add(src + c + 16, v + 16);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tile(lane, j) = v[j];
+        __syncwarp();
+        const int col0 = n0 + half * C::HALF + c;
+        if (col0 < N) epi(b, row0, col0, tile, lane, M, N, nullptr, 0);
+        __syncwarp();
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_free[buf]);
     }
   } else {
     const int quarter = warp & 3, half = (warp - 2) >> 2;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + half * C::HALF;
-    float acc[C::HALF];
-#pragma unroll
-    for (int i = 0; i < C::HALF; ++i) acc[i] = 0.f;
-    // warm L2 with whatever the epilogue will read while the tile accumulates
-    epi.prefetch(b, m0 + quarter * 32 + lane, n0 + half * C::HALF, C::HALF, M, N);
+    const TileRef tile{staging + (warp - 2) * 32 * 32};
+    long long g = 0;
     bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int buf = kb & 1, use = kb >> 1;
-      if (!mbar_wait(&acc_full[buf], use & 1)) {
-        if (lane == 0) atomicExch(err, 3);
-        ok = false;
-        break;
+    for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      const int mt = (int)(t % tm), nt = (int)((t / tm) % tn), b = (int)(t / ((long long)tm * tn));
+      const int m0 = mt * BM, n0 = nt * BN;
+      float* rows = row_staging + (warp - 2) * 32 * C::HALF;
+      if constexpr (Epi::kStagesRows) {
+        // copy this thread's functor inputs into shared memory while the tile accumulates
+        epi.stage_rows(b, m0 + quarter * 32 + lane, n0 + half * C::HALF, C::HALF, M, N, rows + lane * C::HALF);
+        cp_async_commit();
+      } else {
+        // warm L2 with whatever the epilogue will read while the tile accumulates
+        epi.prefetch(b, m0 + quarter * 32 + lane, n0 + half * C::HALF, C::HALF, M, N);
       }
-      tc_fence_after();
+      float acc[C::HALF];
 #pragma unroll
-      for (int c = 0; c < C::HALF; c += 16) tmem_ld16_add(lane_base + buf * BN + c, acc + c);
-      tc_fence_before();
-      mbar_arrive(&acc_free[buf]);
-    }
-    if (ok) {
-      // Every MMA has completed (the last acc_full wait), so the stage ring is
-      // free: each epilogue warp stages 32 x 32 chunks of its accumulators
-      // there and the functor walks them with lanes along the destination's
-      // contiguous dimension (coalesced global accesses).
-      float(*tile)[33] = reinterpret_cast<float(*)[33]>(smem + (warp - 2) * (32 * 33 * 4));
+      for (int i = 0; i < C::HALF; ++i) acc[i] = 0.f;
+      for (int kb = 0; kb < nkb; ++kb, ++g) {
+        const int buf = (int)(g & 1);
+        const uint32_t use = (uint32_t)(g >> 1);
+        if (!mbar_wait(&acc_full[buf], use & 1)) {
+          if (lane == 0) atomicExch(err, 3);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < C::HALF; c += 16) tmem_ld16_add(lane_base + buf * BN + c, acc + c);
+        tc_fence_before();
+        mbar_arrive(&acc_free[buf]);
+      }
+      if (!ok) break;
+      if constexpr (Epi::kStagesRows) cp_async_wait_all();
+      __syncwarp();
       const int row0 = m0 + quarter * 32;
 #pragma unroll
       for (int c = 0; c < C::HALF; c += 32) {
         const int col0 = n0 + half * C::HALF + c;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) tile[lane][j] = acc[c + j];
+        for (int j = 0; j < 32; ++j) tile(lane, j) = acc[c + j];
         __syncwarp();
-        if (col0 < N) epi(b, row0, col0, tile, lane, M, N);
+        if (col0 < N) epi(b, row0, col0, tile, lane, M, N, rows + c, C::HALF);
         __syncwarp();
       }
     }

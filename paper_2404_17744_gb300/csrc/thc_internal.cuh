@@ -83,7 +83,7 @@ struct thc_ctx {
   __nv_bfloat16 *Ms_h = nullptr, *Ms_l = nullptr;   // merged M, tc x N x ldN
   __nv_bfloat16 *T2s_h = nullptr, *T2s_l = nullptr; // (M X^T)^T, tc x n x ldN
   __nv_bfloat16 *Ats_h = nullptr, *Ats_l = nullptr; // A^T blocks, Pb x n x ldn
-  float *Bf = nullptr;                              // B blocks, Pb x N x n
+  float *Bf = nullptr;                              // B block, R-major: N x Pc x n
   double *Dd = nullptr;                             // D, tc x N x N
   int *d_err = nullptr;                             // device error flag of the tensor-core kernels
 
