@@ -9,14 +9,18 @@
 //
 // The tau <-> i w transforms are the sparse-sampling matrices of an IR basis
 // (supplied by the caller); they run in the DFMA contraction tile.  The
-// inversions are an in-place Gauss-Jordan elimination, one CTA per
-// frequency: Im[(i w + mu) S - F - Sigma(i w)] = w S - Im Sigma(i w) is
+// inversions are an in-place Gauss-Jordan elimination, a cluster of two CTAs
+// per frequency (each owns half of the rows; FP64 is DFMA-bound on GB300, so
+// spreading the n_iw matrices over twice as many SMs halves the time):
+// Im[(i w + mu) S - F - Sigma(i w)] = w S - Im Sigma(i w) is
 // definite for a causal self-energy, so every leading principal minor is
 // non-singular and no pivoting is needed.
 #include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
+
+#include <cooperative_groups.h>
 
 #include "dfma_tile.cuh"
 #include "thc_internal.cuh"
@@ -43,6 +47,7 @@ struct thc_dyson {
   double *tr = nullptr;                                 // n_iw x 2 partial traces
   double *scal = nullptr;                               // small scalar scratch
   int evals = 0;                                        // N(mu) evaluations of the last solve
+  double slope = 0.0;                                   // last secant estimate of dN/dmu (0: none)
   std::vector<void*> owned;
   std::string err;
 };
@@ -110,38 +115,47 @@ __global__ void build_kernel(int n, int n_iw, const double* __restrict__ iw, dou
   }
 }
 
-// In-place Gauss-Jordan inverse of the n x n complex matrix of this CTA (no pivoting).
-// Row k and column k of the current step are staged in shared memory.
-__global__ void __launch_bounds__(1024) gj_invert_kernel(int n, double2* __restrict__ A0) {
+// In-place Gauss-Jordan inverse of one n x n complex matrix per cluster of two
+// CTAs (no pivoting).  CTA rank c owns rows [c h, min(n, (c + 1) h)), h = ceil(n / 2).
+// Step k: every CTA reads the current pivot row k from global memory (L2) and
+// scales it into shared memory, and stages column k of its own rows; a cluster
+// barrier; each CTA updates its rows (the owner of row k stores the scaled
+// row); a second cluster barrier makes the step visible before step k + 1.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024) gj_invert_kernel(int n, double2* __restrict__ A0) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ double2 sh[];
   double2* rowk = sh;      // n
-  double2* colk = sh + n;  // n
-  double2* A = A0 + (long long)blockIdx.x * n * n;
-  const long long nn = (long long)n * n;
+  double2* colk = sh + n;  // rows of this CTA
+  const int rank = (int)cluster.block_rank();
+  const int h = (n + 1) / 2, r0 = rank * h, r1 = min(n, r0 + h), nr = r1 - r0;
+  double2* A = A0 + (long long)(blockIdx.x / 2) * n * n;
+  const long long cnt = (long long)nr * n;
   for (int k = 0; k < n; ++k) {
-    // pivot reciprocal and the scaled pivot row (the pivot entry becomes 1/p)
     const double2 p = A[(long long)k * n + k];
     const double den = p.x * p.x + p.y * p.y;
     const double2 ip = make_double2(p.x / den, -p.y / den);
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       const double2 a = (j == k) ? make_double2(1.0, 0.0) : A[(long long)k * n + j];
       rowk[j] = make_double2(a.x * ip.x - a.y * ip.y, a.x * ip.y + a.y * ip.x);
-      colk[j] = A[(long long)j * n + k];
     }
-    __syncthreads();
-    for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
-      const int i = (int)(e / n), j = (int)(e - (long long)i * n);
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) colk[i] = A[(long long)(r0 + i) * n + k];
+    cluster.sync();  // both CTAs have read row k before its owner overwrites it
+    for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int li = (int)(e / n), j = (int)(e - (long long)li * n), i = r0 + li;
+      const long long o = (long long)i * n + j;
       if (i == k) {
-        A[e] = rowk[j];
+        A[o] = rowk[j];
       } else {
-        const double2 f = colk[i], r = rowk[j];
-        double2 a = (j == k) ? make_double2(0.0, 0.0) : A[e];
+        const double2 f = colk[li], r = rowk[j];
+        double2 a = (j == k) ? make_double2(0.0, 0.0) : A[o];
         a.x -= f.x * r.x - f.y * r.y;
         a.y -= f.x * r.y + f.y * r.x;
-        A[e] = a;
+        A[o] = a;
       }
     }
-    __syncthreads();
+    __threadfence();
+    cluster.sync();  // step k is complete in global memory for both CTAs
   }
 }
 
@@ -237,7 +251,7 @@ int dyson_at(thc_dyson* d, double mu, double* n_out) {
   build_kernel<<<blocks_for(nn * nw), 256, 0, d->stream>>>((int)n, (int)nw, iw_d, mu, d->S, d->F, d->Siw, d->Giw);
   THC_TRY(dcheck(d, cudaGetLastError(), "Dyson matrices"));
   const size_t shm = 2 * sizeof(double2) * n;
-  gj_invert_kernel<<<(unsigned)nw, 1024, shm, d->stream>>>((int)n, reinterpret_cast<double2*>(d->Giw));
+  gj_invert_kernel<<<(unsigned)(2 * nw), 1024, shm, d->stream>>>((int)n, reinterpret_cast<double2*>(d->Giw));
   THC_TRY(dcheck(d, cudaGetLastError(), "Gauss-Jordan"));
   trace_gs_kernel<<<(unsigned)nw, 256, 0, d->stream>>>((int)n, reinterpret_cast<const double2*>(d->Giw), d->S, d->tr);
   THC_TRY(dcheck(d, cudaGetLastError(), "Tr[G S]"));
@@ -357,6 +371,10 @@ int thc_dyson_solve(thc_dyson* d, const double* Sigma_tau, double n_elec, double
   note(m, nm);
   double mp = m, np_ = nm;
   double step = (nm < n_elec ? 1.0 : -1.0) * 1e-3;
+  if (d->slope > 0.0 && std::isfinite(d->slope)) {  // Newton-like first step from the last slope
+    const double st = (n_elec - nm) / d->slope;
+    if (std::fabs(st) < 0.5) step = st;
+  }
   for (int it = 0; it < 200 && std::fabs(nm - n_elec) > tol; ++it) {
     double x;
     if (it == 0) {
@@ -375,6 +393,10 @@ int thc_dyson_solve(thc_dyson* d, const double* Sigma_tau, double n_elec, double
     m = x;
     THC_TRY(dyson_at(d, m, &nm));
     note(m, nm);
+    if (m != mp && nm != np_) {
+      const double sl = (nm - np_) / (m - mp);
+      if (sl > 0.0 && std::isfinite(sl)) d->slope = sl;
+    }
   }
   if (std::fabs(nm - n_elec) > 1e3 * tol)
     return dfail(d, THC_EINVAL, "thc_dyson_solve: chemical potential search did not converge");
