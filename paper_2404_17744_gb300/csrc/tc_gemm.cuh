@@ -183,6 +183,19 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// 32 TMEM lanes x 16 consecutive 32-bit columns into r[0..15] (no wait):
+// thread t reads lane (base + t).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // 32 TMEM lanes x 16 consecutive 32-bit columns, added into acc[0..15]:
 // thread t reads lane (base + t).
 __device__ __forceinline__ void tmem_ld16_add(uint32_t taddr, float* acc) {
@@ -389,8 +402,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         tc_fence_after();
+        {  // all loads of the stage in flight, one wait
+          uint32_t r[C::HALF];
 #pragma unroll
-        for (int c = 0; c < C::HALF; c += 16) tmem_ld16_add(lane_base + buf * BN + c, acc + c);
+          for (int c = 0; c < C::HALF; c += 16) tmem_ld16(lane_base + buf * BN + c, r + c);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < C::HALF; ++i) acc[i] += __uint_as_float(r[i]);
+        }
         tc_fence_before();
         mbar_arrive(&acc_free[buf]);
       }
