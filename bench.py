@@ -61,6 +61,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Maximum of `value` over the ranks of the default process group (the slowest rank
+    defines the job's time); the identity for a single process."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, flops_per_step: float, steps: int, max_seconds: float) -> float:
+    """Whole-job TFLOP/s: every rank runs a replica of the workload (weak scaling)."""
+    return world * flops_per_step * steps / max_seconds / 1e12
+
+
 def algorithmic_flops(n, N, n_tau):
     """Flops of one Sigma evaluation (both terms), 2 per multiply-add."""
     return n_tau * (2 * N * n ** 3 + 4 * N ** 2 * n ** 2 + 4 * N ** 3 + 8 * N ** 2 * n + 6 * N * n ** 2)
@@ -241,11 +258,7 @@ def measure(args, case, precision, world, dev, stream, X, V, G, S, flush, sample
     thc.thc_sync(ctx)
     kernels = read_profile(thc, ctx)
     thc.thc_profile(ctx, False)
-    total_ms = float(sum(e0.elapsed_time(e1) for e0, e1 in evs))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(e0.elapsed_time(e1) for e0, e1 in evs)), world, dev)
     return ctx, dict(total_ms=total_ms, kernels=kernels, launches=launches, clocks=clocks,
                      energy=energies[-1] if energies else None)
 
@@ -340,7 +353,7 @@ def run_ours(args):
         ctx, r64 = measure(args, case, thc.THC_FP64, world, dev, stream, X, V, G, S, flush, rank == 0)
         lib_flops, u_flops = thc.thc_sigma_flops(ctx)
         assert abs(lib_flops - flops_step) < 1e-6 * flops_step
-        value = world * flops_step * args.steps / (r64["total_ms"] * 1e-3) / 1e12
+        value = job_throughput(world, flops_step, args.steps, r64["total_ms"] * 1e-3)
 
         # end to end through the host-buffer entry point (H2D of G, D2H of Sigma inside)
         Gh = torch.from_numpy(case.G_tau).pin_memory()
@@ -352,12 +365,8 @@ def run_ours(args):
         e2e_steps = max(1, min(args.steps, 2))
         for _ in range(e2e_steps):
             thc.thc_sigma_eval_host(ctx, Gh, None, Sh)
-        e2e_dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_dt = float(t.item())
-        e2e_value = world * flops_step * e2e_steps / e2e_dt / 1e12
+        e2e_dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e_value = job_throughput(world, flops_step, e2e_steps, e2e_dt)
         thc.thc_destroy(ctx)
 
         # ---- mixed precision (3 x BF16 on tcgen05), same input; error against the FP64 result
@@ -367,7 +376,7 @@ def run_ours(args):
             thc.thc_destroy(ctx)
             stream.synchronize()
             split = rsp
-            split["value"] = world * flops_step * args.steps / (rsp["total_ms"] * 1e-3) / 1e12
+            split["value"] = job_throughput(world, flops_step, args.steps, rsp["total_ms"] * 1e-3)
             split["max_abs_dsigma_vs_fp64"] = float((S_split - S).abs().max().item())
             split["abs_dE_vs_fp64"] = abs(rsp["energy"] - r64["energy"])
 
