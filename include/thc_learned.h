@@ -58,8 +58,9 @@ void thc_mlp_destroy(thc_mlp *m);
  *   inputs x_e = [c_k[:, e] / s_c, (c_k - c_{k-1})[:, e] / s_d]  (d_in = 2 n_l),
  *   proposal c = c_k + s_d MLP(x_e)  (d_out = n_l), returned as Sigma(tau) = U_tau c,
  * with s_c, s_d the root-mean-square of c_k and of c_k - c_{k-1}.  Training
- * pairs: (x built from c_j and c_{j-1}) -> (c_latest - c_j) / s_d for the
- * observed iterates j inside the history window max_hist (>= 3).
+ * pairs: (x built from c_j and c_{j-1}) -> (c_latest - c_j) / s_d(j) for the
+ * observed iterates j inside the history window max_hist (>= 3), each scaled by
+ * the RMS s_d(j) of its own change c_j - c_{j-1} and s_c of the latest iterate.
  *   U_tau host n_tau x n_l, fit_tau host n_l x n_tau (the IR sampling matrices);
  *   W1 (hidden x 2 n_l), b1, W2 (n_l x hidden), b2: initial weights, host FP32.
  */
@@ -73,12 +74,17 @@ int thc_proposer_observe(thc_proposer *p, const double *Sigma_tau);
 /* thc_proposer_count -- number of iterates observed. */
 int thc_proposer_count(const thc_proposer *p);
 
+/* thc_proposer_reset -- forget the observed trajectory, keep the trained
+ * network: a network fitted on one run's trajectory can then propose for
+ * another run of the same sizes (transfer between related systems). */
+int thc_proposer_reset(thc_proposer *p);
+
 /* thc_proposer_train -- build the training pairs from the window and run
  * `steps` Adam steps (mini-batch `batch`); needs >= 3 observed iterates. */
 int thc_proposer_train(thc_proposer *p, int steps, int batch, double lr, double *final_loss);
 
-/* thc_proposer_propose -- write the proposed Sigma(tau) (dev, n_tau x n_ao x n_ao).
- * Synchronises. */
+/* thc_proposer_propose -- write the proposed Sigma(tau) (dev, n_tau x n_ao x n_ao)
+ * from the last two observed iterates (s_c, s_d taken from them).  Synchronises. */
 int thc_proposer_propose(thc_proposer *p, double *Sigma_tau);
 
 const char *thc_proposer_last_error(const thc_proposer *p);

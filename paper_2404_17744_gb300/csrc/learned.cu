@@ -8,8 +8,9 @@
 //     x_e = [ c_k[:, e] / s_c ,  (c_k - c_{k-1})[:, e] / s_d ]        (2 L inputs)
 // through a ReLU layer of H units to a correction of its coefficients,
 //     c_prop[:, e] = c_k[:, e] + s_d * MLP(x_e)                        (L outputs).
-// It is trained online on the loop's own trajectory: samples (j, e) with
-// input x built from c_j, c_{j-1} and target (c_latest - c_j) / s_d.
+// It is trained on a loop's own trajectory: samples (j, e) with input x built
+// from c_j, c_{j-1} and target (c_latest - c_j) / s_d(j), where s_c is the
+// RMS of the latest iterate and s_d(j) the RMS of the change c_j - c_{j-1}.
 // Weights are FP16 in the forward and backward passes with FP32 master
 // copies, FP32 accumulation and Adam; every contraction runs in the FP32
 // SIMT tile below.
@@ -502,7 +503,7 @@ int thc_proposer_init(thc_proposer** out, int n_ao, int n_tau, int n_l, const do
   A((void**)&p->prop, 8 * L * n2, "proposal");
   A((void**)&p->X, 4 * ns * 2 * L, "samples X");
   A((void**)&p->T, 4 * ns * L, "samples T");
-  A((void**)&p->red, 8 * 4, "scratch");
+  A((void**)&p->red, 8 * (size_t)(max_hist + 4), "scratch");
   if (rc == THC_OK) rc = pcheck(p, cudaMemcpyAsync(p->U_tau, U_tau, 8 * n_tau * L, cudaMemcpyDefault, p->stream), "U_tau");
   if (rc == THC_OK) rc = pcheck(p, cudaMemcpyAsync(p->fit_tau, fit_tau, 8 * L * n_tau, cudaMemcpyDefault, p->stream), "fit");
   if (rc == THC_OK) rc = thc_mlp_init(&p->mlp, 2 * n_l, hidden, n_l, (int)ns, W1, b1, W2, b2, stream);
@@ -531,6 +532,12 @@ int thc_proposer_observe(thc_proposer* p, const double* Sigma_tau) {
 
 int thc_proposer_count(const thc_proposer* p) { return p ? p->count : 0; }
 
+int thc_proposer_reset(thc_proposer* p) {
+  if (!p) return thc::fail(nullptr, THC_EINVAL, "thc_proposer_reset: NULL proposer");
+  p->count = 0;  // trajectory forgotten, network weights and scales kept
+  return THC_OK;
+}
+
 int thc_proposer_train(thc_proposer* p, int steps, int batch, double lr, double* final_loss) {
   if (!p || steps < 1) return pfail(p, THC_EINVAL, "thc_proposer_train: bad argument");
   const int k = p->count;  // iterates 0..k-1 observed; latest k-1
@@ -538,21 +545,26 @@ int thc_proposer_train(thc_proposer* p, int steps, int batch, double lr, double*
   if (k < 3) return pfail(p, THC_EINVAL, "thc_proposer_train: needs at least three observed iterates");
   const long long L = p->L, n2 = p->n2, len = L * n2;
   double* latest = slot(p, k - 1);
-  // scales from the latest iterate and its last change
+  // s_c from the latest iterate; every pair (j) is scaled by its own change c_j - c_{j-1}, as a
+  // proposal made at that point would be
   rms_kernel<<<1, 1024, 0, p->stream>>>(len, latest, nullptr, p->red);
-  rms_kernel<<<1, 1024, 0, p->stream>>>(len, latest, slot(p, k - 2), p->red + 1);
-  double h[2];
-  THC_TRY(pcheck(p, cudaMemcpyAsync(h, p->red, 16, cudaMemcpyDeviceToHost, p->stream), "scales"));
+  for (int j = first; j <= k - 2; ++j)
+    rms_kernel<<<1, 1024, 0, p->stream>>>(len, slot(p, j), slot(p, j - 1), p->red + 1 + (j - first));
+  std::vector<double> h(1 + std::max(0, k - 1 - first));
+  THC_TRY(pcheck(p, cudaMemcpyAsync(h.data(), p->red, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, p->stream),
+                 "scales"));
   THC_TRY(pcheck(p, cudaStreamSynchronize(p->stream), "scales sync"));
   p->s_c = h[0] > 0 ? h[0] : 1.0;
-  p->s_d = h[1] > 0 ? h[1] : 1.0;
   long long ns = 0;
   for (int j = first; j <= k - 2; ++j) {  // pairs (c_j, c_{j-1}) -> c_latest - c_j
+    const double sd = h[1 + (j - first)];
+    if (!(sd > 0)) continue;
     samples_kernel<<<pblocks(len), 256, 0, p->stream>>>((int)L, n2, slot(p, j), slot(p, j - 1), latest, 1.0 / p->s_c,
-                                                        1.0 / p->s_d, p->X, p->T, ns);
+                                                        1.0 / sd, p->X, p->T, ns);
     THC_TRY(pcheck(p, cudaGetLastError(), "samples"));
     ns += n2;
   }
+  if (ns == 0) return pfail(p, THC_EINVAL, "thc_proposer_train: the observed iterates do not change");
   return thc_mlp_train(p->mlp, (int)ns, p->X, p->T, steps, batch, lr, final_loss);
 }
 
@@ -562,6 +574,14 @@ int thc_proposer_propose(thc_proposer* p, double* Sigma_tau) {
   if (k < 2) return pfail(p, THC_EINVAL, "thc_proposer_propose: needs at least two observed iterates");
   const long long L = p->L, n2 = p->n2, len = L * n2, nt = p->n_tau;
   double* c = slot(p, k - 1);
+  // inputs and outputs are scaled by the current iterate and its last change
+  rms_kernel<<<1, 1024, 0, p->stream>>>(len, c, nullptr, p->red);
+  rms_kernel<<<1, 1024, 0, p->stream>>>(len, c, slot(p, k - 2), p->red + 1);
+  double h[2];
+  THC_TRY(pcheck(p, cudaMemcpyAsync(h, p->red, 16, cudaMemcpyDeviceToHost, p->stream), "scales"));
+  THC_TRY(pcheck(p, cudaStreamSynchronize(p->stream), "scales sync"));
+  p->s_c = h[0] > 0 ? h[0] : 1.0;
+  p->s_d = h[1] > 0 ? h[1] : 1.0;
   samples_kernel<<<pblocks(len), 256, 0, p->stream>>>((int)L, n2, c, slot(p, k - 2), nullptr, 1.0 / p->s_c,
                                                       1.0 / p->s_d, p->X, nullptr, 0);
   THC_TRY(pcheck(p, cudaGetLastError(), "features"));

@@ -168,17 +168,29 @@ class GF2Loop:
 class LearnedProposer:
     """Learned Sigma proposals for GF2Loop.run (include/thc_learned.h).
 
-    Every iteration the exact Sigma_out is observed.  From the third iterate
-    on, while the residual is above `active_above`, the network is retrained
-    on the trajectory and its proposal replaces the DIIS input.  A proposal is
-    judged by the next iteration's exact residual: if that is not below the
-    residual the proposal was made at, the proposal counts as rejected, the
-    loop continues from DIIS (which keeps the evaluated pair in its history)
-    and proposals pause for `cooldown` iterations.
+    Two ways of use:
+
+    * online (default): every iteration the exact Sigma_out is observed; from
+      the third iterate on, while the residual is above `active_above`, the
+      network is retrained on the trajectory and its proposal replaces the DIIS
+      input;
+    * transfer: `record=True` only observes a first run; `fit()` trains the
+      network on that trajectory (pairs from every iterate to the converged
+      one); `start_transfer()` forgets the trajectory and makes the network,
+      unchanged, propose from the second iterate of the next run (same sizes,
+      a related system).
+
+    A proposal replaces the input of one iteration; at most `max_proposals`
+    are made per run (default one: a jump-start in place of a damping step,
+    after which DIIS, which extrapolates better once it has a few pairs, is left
+    alone).  A proposal is judged by the next iteration's exact residual: if that
+    is not below the residual the proposal was made at, it counts as rejected;
+    either way the loop continues from DIIS, which keeps the evaluated pair in
+    its history.
     """
 
-    def __init__(self, loop, hidden=512, max_hist=6, steps=150, batch=8192, lr=2e-3, seed=17744,
-                 active_above=1e-5, cooldown=2):
+    def __init__(self, loop, hidden=512, max_hist=8, steps=150, batch=8192, lr=2e-3, seed=17744,
+                 active_above=1e-5, cooldown=2, record=False, max_proposals=1):
         g = loop.grid
         L = g.basis.L
         rng = np.random.default_rng(seed)
@@ -191,8 +203,12 @@ class LearnedProposer:
                                        self.W2, self.b2, loop.stream.cuda_stream)
         self.steps, self.batch, self.lr = steps, batch, lr
         self.active_above, self.cooldown = active_above, cooldown
-        self.pending = None          # residual at which the last proposal was made
+        self.record = record           # observe only
+        self.transfer = False          # propose with the fitted network, no retraining
+        self.pending = None            # residual at which the last proposal was made
         self.pause = 0
+        self.max_proposals = max_proposals
+        self.proposed = 0
         self.accepted = self.rejected = 0
         self.losses = []
 
@@ -207,8 +223,20 @@ class LearnedProposer:
         except Exception:
             pass
 
+    def fit(self, steps=None, lr=None):
+        """Train on the recorded trajectory: inputs from each iterate, targets towards the last."""
+        self.losses.append(thc.thc_proposer_train(self.p, steps or self.steps, self.batch, lr or self.lr))
+        return self.losses[-1]
+
+    def start_transfer(self):
+        thc.thc_proposer_reset(self.p)
+        self.record, self.transfer = False, True
+        self.pending, self.pause, self.proposed = None, 0, 0
+
     def __call__(self, loop, it, residual):
         thc.thc_proposer_observe(self.p, loop.Sig_out)
+        if self.record:
+            return "recorded"
         label = ""
         if self.pending is not None:
             if residual < self.pending:
@@ -222,9 +250,12 @@ class LearnedProposer:
         if self.pause > 0:
             self.pause -= 1
             return label + "paused"
-        if thc.thc_proposer_count(self.p) < 3 or residual < self.active_above:
+        count = thc.thc_proposer_count(self.p)
+        if residual < self.active_above or count < (2 if self.transfer else 3) or self.proposed >= self.max_proposals:
             return label.rstrip("; ")
-        self.losses.append(thc.thc_proposer_train(self.p, self.steps, self.batch, self.lr))
+        if not self.transfer:
+            self.losses.append(thc.thc_proposer_train(self.p, self.steps, self.batch, self.lr))
         thc.thc_proposer_propose(self.p, loop.Sig_in)
         self.pending = residual
+        self.proposed += 1
         return label + "proposed"

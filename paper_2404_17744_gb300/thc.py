@@ -110,6 +110,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_proposer_observe.restype = i
     lib.thc_proposer_count.argtypes = [vp]
     lib.thc_proposer_count.restype = i
+    lib.thc_proposer_reset.argtypes = [vp]
+    lib.thc_proposer_reset.restype = i
     lib.thc_proposer_train.argtypes = [vp, i, i, d, ctypes.POINTER(d)]
     lib.thc_proposer_train.restype = i
     lib.thc_proposer_propose.argtypes = [vp, dp]
@@ -386,6 +388,11 @@ def thc_proposer_observe(p, Sigma_tau):
 
 def thc_proposer_count(p) -> int:
     return int(load_library().thc_proposer_count(p))
+
+
+def thc_proposer_reset(p):
+    lib = load_library()
+    _lcheck(lib.thc_proposer_reset(p), lib.thc_proposer_last_error, p)
 
 
 def thc_proposer_train(p, steps, batch, lr) -> float:

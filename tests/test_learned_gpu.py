@@ -92,3 +92,36 @@ def test_loop_with_learned_proposals_reaches_the_same_energy(precision, tol, bar
           f"E {r1[-1].E:.10f}, proposals accepted/rejected {ar}; labels {[r.proposal for r in r1]}")
     assert c0 and c1
     assert abs(r0[-1].E - r1[-1].E) < bar
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(0, 1e-10, 1e-9), (1, 1e-6, 1e-5)])
+def test_transfer_between_related_systems(precision, tol, bar):
+    """Fit on the trajectory of one system, propose for a related one (same sizes,
+    another seed); the converged energy is unchanged and the iteration counts with
+    and without the transferred network are printed."""
+    from paper_2404_17744_gb300 import scf
+    g = ir.make_loop_grid(100.0, 10.0)
+    a = synth.make_sigma_case(20, 60, 4, 100.0, 17745, identity_S=False, n_occ=8)
+    b = synth.make_sigma_case(20, 60, 4, 100.0, 17746, identity_S=False, n_occ=8)
+    LA = scf.GF2Loop(a.X, a.V, a.F, a.S, g, 8.0, precision=precision)
+    P = scf.LearnedProposer(LA, record=True, steps=400)
+    try:
+        assert LA.run(tol=tol, max_iter=80, proposer=P)
+        loss = P.fit()
+        P.start_transfer()
+        runs = {}
+        for learned in (False, True):
+            LB = scf.GF2Loop(b.X, b.V, b.F, b.S, g, 8.0, precision=precision)
+            try:
+                conv = LB.run(tol=tol, max_iter=80, proposer=P if learned else None)
+                runs[learned] = (conv, LB.records)
+            finally:
+                LB.close()
+    finally:
+        P.close()
+        LA.close()
+    (c0, r0), (c1, r1) = runs[False], runs[True]
+    print(f"transfer precision {precision}: fit loss {loss:.3e}; plain {len(r0)} iterations, learned {len(r1)} "
+          f"(accepted {P.accepted}, rejected {P.rejected}); labels {[r.proposal for r in r1]}")
+    assert c0 and c1
+    assert abs(r0[-1].E - r1[-1].E) < bar
