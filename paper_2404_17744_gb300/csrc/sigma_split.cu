@@ -91,8 +91,11 @@ using Tile = tc::TileRef;
 // Functors without global reads in their epilogue prefetch and stage nothing.
 #define THC_NO_PREFETCH                                                      \
   static constexpr bool kStagesRows = false;                                 \
+  static constexpr bool kRowWise = false;                                    \
   __device__ void prefetch(int, int, int, int, int, int) const {}            \
-  __device__ void stage_rows(int, int, int, int, int, int, float*) const {}
+  __device__ void stage_rows(int, int, int, int, int, int, float*) const {}  \
+  __device__ float row_chunk(int, int, int, const uint32_t*, const float*, int, int, float p) const { return p; } \
+  __device__ void row_done(int, int, float, int) const {}
 
 __device__ __forceinline__ void split_store(bf16* hi, bf16* lo, long long o, float v) {
   const bf16 h = __float2bfloat16_rn(v);
@@ -183,6 +186,27 @@ struct EpiHad {
   double* D;
   int n, N, P0, Pc;
   static constexpr bool kStagesRows = true;
+  static constexpr bool kRowWise = true;
+  // single-chunk mode: thread = row P; sum_v C[P][v] B[R][P][v] over 32 columns at a time
+  __device__ float row_chunk(int b, int row, int col0, const uint32_t* c, const float* brow, int M, int Ncols,
+                             float part) const {
+    if (row >= M) return part;
+    const int cnt = min(32, Ncols - col0);
+    if (!(n & 3)) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < cnt) part = fmaf(__uint_as_float(c[j]), brow[j], part);
+    } else {
+      const float* g = Bf + ((long long)b * Pc + row) * n + col0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < cnt) part = fmaf(__uint_as_float(c[j]), __ldg(g + j), part);
+    }
+    return part;
+  }
+  __device__ void row_done(int b, int row, float part, int M) const {
+    if (row < M) atomicAdd(&D[((long long)P0 + row) * N + b], (double)part);
+  }
   __device__ void prefetch(int, int, int, int, int, int) const {}
   __device__ void stage_rows(int b, int row, int col0, int ncols, int M, int Ncols, float* dst) const {
     if (row >= M || col0 >= Ncols || (n & 3)) return;
@@ -346,7 +370,7 @@ int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, 
   THC_TRY(make_map(ctx, &bh, B.hi, K, B, BN));
   THC_TRY(make_map(ctx, &bl, B.lo, K, B, BN));
   auto kern = tc::split_gemm_kernel<BN, MULTI, Epi>;
-  using CfgE = Cfg<BN, Epi::kStagesRows ? BN / 2 : 0>;
+  using CfgE = typename tc::CfgFor<BN, MULTI, Epi>::type;
   static bool attr_set = false;  // one per instantiation
   if (!attr_set) {
     THC_TRY(check_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgE::SMEM),
@@ -397,9 +421,11 @@ constexpr long long kSingleChunkK = 256;
 template <class Epi>
 int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool bb, long long M, long long N,
          long long K, long long batch, const Epi& epi, const char* what) {
-  // Functors that stage an input row per output row (the fused C/D contraction) run
-  // promoted at BN = 128: their rows are copied in while the stages drain.
+  // Functors that stage an input row per output row (the fused C/D contraction) run at
+  // BN = 128: row-wise in the single-chunk mode for K <= 256, promoted otherwise.
   if constexpr (Epi::kStagesRows) {
+    if (K <= kSingleChunkK && Epi::kRowWise)
+      return launch_split_gemm<128, false>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
     return launch_split_gemm<128, true>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
   } else {
   if (K > kSingleChunkK) return launch_split_gemm<128, true>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);

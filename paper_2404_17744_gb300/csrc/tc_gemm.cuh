@@ -58,22 +58,32 @@ constexpr int NTHREADS = 320;  // 10 warps: TMA, MMA, 8 epilogue
 constexpr int NEPI = 256;      // epilogue threads
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s per wait
 
-template <int BN, int ROWS = 0>
+template <int BN, int ROWS = 0, bool ROWWISE = false>
 struct Cfg {
-  // ROWS: FP32 values per output row the epilogue functor stages (0 or BN / 2)
+  // ROWS: FP32 values (padding included) per epilogue thread staged for the functor;
+  // ROWWISE: the functor works on each thread's own row, without the 32 x 32 staging tile
   static constexpr int A_BYTES = BM * BKE * 2;
   static constexpr int B_BYTES = BN * BKE * 2;
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int TMEM_COLS = 2 * BN;   // two accumulators; BN in {128, 256}
   static constexpr int HALF = BN / 2;         // columns per epilogue thread
-  static constexpr int STAGING = 8 * 32 * 32 * 4;      // one swizzled 32 x 32 FP32 tile per epilogue warp
-  static constexpr int ROW_STAGING = 8 * 32 * ROWS * 4;  // staged functor inputs, 32 rows per epilogue warp
+  static constexpr int STAGING = ROWWISE ? 0 : 8 * 32 * 32 * 4;  // one swizzled 32 x 32 FP32 tile per warp
+  static constexpr int ROW_STAGING = 8 * 32 * ROWS * 4;           // staged functor inputs, 32 rows per warp
   static constexpr int FIXED = STAGING + ROW_STAGING + 1024 /*align*/ + 256 /*barriers*/;
   static constexpr int STAGES = ((232448 - FIXED) / STAGE) >= 3 ? 3 : 2;
   static constexpr int SMEM = STAGES * STAGE + FIXED;
   static_assert(SMEM <= 232448, "shared memory per CTA");
   static_assert(BN == 128 || BN == 256, "tile width");
-  static_assert(ROWS == 0 || ROWS == BN / 2, "staged row width");
+};
+
+// Staged-row geometry of a functor in a given mode: promoted functors that stage rows
+// use HALF values per thread; row-wise functors in the single-chunk mode use HALF + 4
+// (16-byte aligned rows, fewer bank conflicts when lanes walk their own rows).
+template <int BN, bool MULTI, class Epi>
+struct CfgFor {
+  static constexpr bool ROWWISE = !MULTI && Epi::kRowWise;
+  static constexpr int ROWS = ROWWISE ? BN / 2 + 4 : ((MULTI && Epi::kStagesRows) ? BN / 2 : 0);
+  using type = Cfg<BN, ROWS, ROWWISE>;
 };
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -230,7 +240,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                       const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int M,
                       int N, int K, int batch, Operands ops, Epi epi, int* err) {
-  using C = Cfg<BN, Epi::kStagesRows ? BN / 2 : 0>;
+  using C = typename CfgFor<BN, MULTI, Epi>::type;
+  constexpr bool ROWWISE = CfgFor<BN, MULTI, Epi>::ROWWISE;
+  constexpr int RSTRIDE = CfgFor<BN, MULTI, Epi>::ROWS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* staging = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE);
@@ -332,6 +344,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (MULTI || kb == nkb - 1) mma_commit(&acc_full[buf]);  // accumulator ready
         }
       }
+    }
+  } else if (ROWWISE) {
+    // single-chunk, row-wise functor: every thread reduces its own row against the
+    // input row it copied into shared memory at the start of the tile
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    float* myrow = row_staging + ((warp - 2) * 32 + lane) * RSTRIDE;
+    long long local = 0;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
+      const int mt = (int)(t % tm), nt = (int)((t / tm) % tn), b = (int)(t / ((long long)tm * tn));
+      const int m0 = mt * BM, n0 = nt * BN, buf = (int)(local & 1);
+      const int row = m0 + quarter * 32 + lane, colb = n0 + half * C::HALF;
+      epi.stage_rows(b, row, colb, C::HALF, M, N, myrow);  // the previous tile is done with the buffer
+      cp_async_commit();
+      if (!mbar_wait(&acc_full[buf], (uint32_t)(local >> 1) & 1)) {
+        if (lane == 0) atomicExch(err, 3);
+        break;
+      }
+      tc_fence_after();
+      cp_async_wait_all();
+      const uint32_t src = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + buf * BN + half * C::HALF;
+      float part = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < C::HALF; c += 32) {
+        uint32_t r[32];
+        tmem_ld16(src + c, r);
+        tmem_ld16(src + c + 16, r + 16);
+        tmem_wait_ld();
+        part = epi.row_chunk(b, row, colb + c, r, myrow + c, M, N, part);
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_free[buf]);
+      epi.row_done(b, row, part, M);
     }
   } else if (!MULTI) {
     const int quarter = warp & 3, half = (warp - 2) >> 2;
