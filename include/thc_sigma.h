@@ -186,7 +186,9 @@ int thc_profile(thc_ctx *ctx, int enable);
  * its name, number of launches, summed device time in ms and summed
  * algorithmic flops of those launches.  Any out-pointer may be NULL.
  * Synchronises the stream.  Class names: u_build, project, sox_A, sox_B,
- * sox_CD, polarisation, direct_VPi, direct_W, back_transform, energy, split.
+ * sox_CD, polarisation, direct_VPi, direct_W, back_transform, energy, split,
+ * sox_BCD (sox_B and sox_CD are the FP64 path's; the split path runs both
+ * contractions as the one fused sox_BCD kernel).
  */
 int thc_profile_get(thc_ctx *ctx, int kclass, const char **name, long long *launches,
                     double *ms, double *flops);

@@ -24,6 +24,7 @@
 #include <mutex>
 #include <string>
 
+#include "tc_bcd.cuh"
 #include "tc_gemm.cuh"
 #include "thc_internal.cuh"
 
@@ -83,19 +84,26 @@ int make_map(thc_ctx* ctx, CUtensorMap* m, const bf16* base, long long K, const 
   return THC_OK;
 }
 
+// 3-D map with explicit extents (elements), byte strides of dims 1 and 2, and box; 128-byte swizzle.
+int make_map_3d(thc_ctx* ctx, CUtensorMap* m, const bf16* base, const long long dims_in[3], const long long strides_in[2],
+                const int box_in[3]) {
+  cuuint64_t dims[3] = {(cuuint64_t)dims_in[0], (cuuint64_t)dims_in[1], (cuuint64_t)dims_in[2]};
+  cuuint64_t strides[2] = {(cuuint64_t)strides_in[0], (cuuint64_t)strides_in[1]};
+  cuuint32_t box[3] = {(cuuint32_t)box_in[0], (cuuint32_t)box_in[1], (cuuint32_t)box_in[2]};
+  cuuint32_t es[3] = {1, 1, 1};
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || strides[0] % 16 || strides[1] % 16)
+    return fail(ctx, THC_EINVAL, "tensor map operand not 16-byte aligned");
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, THC_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return THC_OK;
+}
+
 // ------------------------------------------------------------ epilogues
 // Each functor is run by one warp on a 32 x 32 chunk of the output tile:
 // t(r, j) = C[row0 + r][col0 + j]; rows >= M and columns >= N are skipped.
 using Tile = tc::TileRef;
-
-// Functors without global reads in their epilogue prefetch and stage nothing.
-#define THC_NO_PREFETCH                                                      \
-  static constexpr bool kStagesRows = false;                                 \
-  static constexpr bool kRowWise = false;                                    \
-  __device__ void prefetch(int, int, int, int, int, int) const {}            \
-  __device__ void stage_rows(int, int, int, int, int, int, float*) const {}  \
-  __device__ float row_chunk(int, int, int, const uint32_t*, const float*, int, int, float p) const { return p; } \
-  __device__ void row_done(int, int, float, int) const {}
 
 __device__ __forceinline__ void split_store(bf16* hi, bf16* lo, long long o, float v) {
   const bf16 h = __float2bfloat16_rn(v);
@@ -106,11 +114,10 @@ __device__ __forceinline__ void split_store(bf16* hi, bf16* lo, long long o, flo
 // dst(b, row, col) = scale * C, split; row-major, or transposed dst(b, col, row).
 template <bool TRANSPOSED>
 struct EpiSplit {
-  THC_NO_PREFETCH
   bf16 *hi, *lo;
   long long ld, bs;
   float scale;
-  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N, const float*, int) const {
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N) const {
     if (TRANSPOSED) {  // lanes along rows: dst(b, col, row) is contiguous in row
       const int row = row0 + lane;
       if (row >= M) return;
@@ -129,11 +136,10 @@ struct EpiSplit {
 
 // A^T blocks: row = P n + q (P local to the block), col = v  ->  At[P][v][q], split (lanes along q).
 struct EpiAt {
-  THC_NO_PREFETCH
   bf16 *hi, *lo;
   int n;
   long long ld;
-  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int N, const float*, int) const {
+  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int N) const {
     const int row = row0 + lane;
     if (row >= M) return;
     const int P = row / n, q = row - P * n;
@@ -146,10 +152,9 @@ struct EpiAt {
 
 // FP32 store: dst[b * bs + row * ld + col] (lanes along columns).
 struct EpiF32 {
-  THC_NO_PREFETCH
   float* dst;
   long long ld, bs;
-  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N, const float*, int) const {
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N) const {
     const int col = col0 + lane;
     if (col >= N) return;
     float* d = dst + (long long)b * bs + col;
@@ -161,10 +166,9 @@ struct EpiF32 {
 
 // FP64 store: dst[b * bs + row * ld + col] (lanes along columns).
 struct EpiF64 {
-  THC_NO_PREFETCH
   double* dst;
   long long ld, bs;
-  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N, const float*, int) const {
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N) const {
     const int col = col0 + lane;
     if (col >= N) return;
     double* d = dst + (long long)b * bs + col;
@@ -174,85 +178,14 @@ struct EpiF64 {
   }
 };
 
-// Hadamard-reduce of the fused C/D step: b = R, row = P (local), col = v.
-//   D[(P0 + P) N + R] += sum_v C[P][v] B[R][P][v]
-// B is stored R-major ([R][P][v], P local to the block).  While a tile
-// accumulates, every epilogue thread copies its row of B into shared memory
-// with 16-byte cp.async (rows of n % 4 != 0 floats are read from global memory
-// in the functor instead); the chunk is then multiplied in place and lane r
-// sums row r into one FP64 atomic.
-struct EpiHad {
-  const float* Bf;  // N x Pc x n
-  double* D;
-  int n, N, P0, Pc;
-  static constexpr bool kStagesRows = true;
-  static constexpr bool kRowWise = true;
-  // single-chunk mode: thread = row P; sum_v C[P][v] B[R][P][v] over 32 columns at a time
-  __device__ float row_chunk(int b, int row, int col0, const uint32_t* c, const float* brow, int M, int Ncols,
-                             float part) const {
-    if (row >= M) return part;
-    const int cnt = min(32, Ncols - col0);
-    if (!(n & 3)) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < cnt) part = fmaf(__uint_as_float(c[j]), brow[j], part);
-    } else {
-      const float* g = Bf + ((long long)b * Pc + row) * n + col0;
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < cnt) part = fmaf(__uint_as_float(c[j]), __ldg(g + j), part);
-    }
-    return part;
-  }
-  __device__ void row_done(int b, int row, float part, int M) const {
-    if (row < M) atomicAdd(&D[((long long)P0 + row) * N + b], (double)part);
-  }
-  __device__ void prefetch(int, int, int, int, int, int) const {}
-  __device__ void stage_rows(int b, int row, int col0, int ncols, int M, int Ncols, float* dst) const {
-    if (row >= M || col0 >= Ncols || (n & 3)) return;
-    const float* src = Bf + ((long long)b * Pc + row) * n + col0;
-    const int cnt = min(ncols, Ncols - col0);  // a multiple of 4 when n is
-    for (int c = 0; c < cnt; c += 4) tc::cp_async16(dst + c, src + c);
-  }
-  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols, const float* rows,
-                             int rstride) const {
-    const int col = col0 + lane;
-    if (!(n & 3)) {
-#pragma unroll 8
-      for (int r = 0; r < 32; ++r) {
-        const int P = row0 + r;
-        t(r, lane) = (P < M && col < Ncols) ? t(r, lane) * rows[r * rstride + lane] : 0.f;
-      }
-    } else {
-#pragma unroll
-      for (int r0 = 0; r0 < 32; r0 += 16) {  // two passes of 16 loads in flight
-        float bv[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int P = row0 + r0 + r;
-          bv[r] = (P < M && col < Ncols) ? __ldg(Bf + ((long long)b * Pc + P) * n + col) : 0.f;
-        }
-#pragma unroll
-        for (int r = 0; r < 16; ++r) t(r0 + r, lane) *= bv[r];
-      }
-    }
-    __syncwarp();
-    float sum = 0.f;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) sum += t(lane, j);
-    if (row0 + lane < M) atomicAdd(&D[((long long)P0 + row0 + lane) * N + b], (double)sum);
-  }
-};
-
 // Merge epilogue of W = T V: M[b][R][P] = c_x D[b][P][R] + c_d G^X[b][R][P] W, split (lanes along P).
 struct EpiMerge {
-  THC_NO_PREFETCH
   bf16 *hi, *lo;
   long long ld;
   const double* D;  // may be null
   const float* GX;
   int N;
-  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols, const float*, int) const {
+  __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols) const {
     const int P = col0 + lane;
     if (P >= Ncols) return;
     const long long NN = (long long)N * N;
@@ -269,11 +202,10 @@ struct EpiMerge {
 
 // U build: row = P, col = (q - q0) n + s  ->  U[(P n + q) ld + s], split (lanes along s).
 struct EpiU {
-  THC_NO_PREFETCH
   bf16 *hi, *lo;
   int n, q0;
   long long ld;
-  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int Ncols, const float*, int) const {
+  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int Ncols) const {
     const int c = col0 + lane;
     if (c >= Ncols) return;
     const int q = q0 + c / n, s = c - (c / n) * n;
@@ -370,7 +302,7 @@ int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, 
   THC_TRY(make_map(ctx, &bh, B.hi, K, B, BN));
   THC_TRY(make_map(ctx, &bl, B.lo, K, B, BN));
   auto kern = tc::split_gemm_kernel<BN, MULTI, Epi>;
-  using CfgE = typename tc::CfgFor<BN, MULTI, Epi>::type;
+  using CfgE = tc::Cfg<BN>;
   static bool attr_set = false;  // one per instantiation
   if (!attr_set) {
     THC_TRY(check_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgE::SMEM),
@@ -421,13 +353,6 @@ constexpr long long kSingleChunkK = 256;
 template <class Epi>
 int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool bb, long long M, long long N,
          long long K, long long batch, const Epi& epi, const char* what) {
-  // Functors that stage an input row per output row (the fused C/D contraction) run at
-  // BN = 128: row-wise in the single-chunk mode for K <= 256, promoted otherwise.
-  if constexpr (Epi::kStagesRows) {
-    if (K <= kSingleChunkK && Epi::kRowWise)
-      return launch_split_gemm<128, false>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
-    return launch_split_gemm<128, true>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
-  } else {
   if (K > kSingleChunkK) return launch_split_gemm<128, true>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
   const ShapeKey key{kclass, M, N, K, batch};
   int bn = 0;
@@ -460,11 +385,60 @@ int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool
   }
   if (bn == 256) return launch_split_gemm<256, false>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
   return launch_split_gemm<128, false>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
-  }
 }
 
 Split split_of(bf16* hi, bf16* lo, long long rows, long long ld, long long batch = 1) {
   return Split{hi, lo, rows, ld, batch, rows * ld};
+}
+
+// Fused B and C/D of one tau point and P block (tc::sox_bcd_kernel):
+//   D[P0 + P][R] += sum_v (sum_w Y[P0 + P][w] U[R][v][w]) (sum_q A^T[P][v][q] Y[R][q]).
+// Y: N x ldn rows of the tau point; U: [R][v][w]; At: [P][v][q] with Pc blocks of P.
+int launch_bcd(thc_ctx* ctx, const Split& Y, const Split& U, const Split& At, long long P0, long long Pc,
+               double* D) {
+  const long long n = ctx->n, N = ctx->N, ldn = ctx->ldn;
+  if (Pc <= 0) return THC_OK;
+  CUtensorMap yh, yl, uh, ul, ah, al;
+  THC_TRY(make_map(ctx, &yh, Y.hi, n, Y, tc::BM));
+  THC_TRY(make_map(ctx, &yl, Y.lo, n, Y, tc::BM));
+  const long long udims[3] = {n, n, N}, adims[3] = {n, n, Pc};
+  const long long strides[2] = {ldn * 2, n * ldn * 2};
+  const int box[3] = {tc::BKE, 1, tc::BM};
+  THC_TRY(make_map_3d(ctx, &uh, U.hi, udims, strides, box));
+  THC_TRY(make_map_3d(ctx, &ul, U.lo, udims, strides, box));
+  THC_TRY(make_map_3d(ctx, &ah, At.hi, adims, strides, box));
+  THC_TRY(make_map_3d(ctx, &al, At.lo, adims, strides, box));
+  static bool attr_set = false;
+  if (!attr_set) {
+    THC_TRY(check_cuda(ctx,
+                       cudaFuncSetAttribute(tc::sox_bcd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tc::BcdCfg::SMEM),
+                       "fused B C/D smem attribute"));
+    attr_set = true;
+  }
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    THC_TRY(check_cuda(ctx, cudaGetDevice(&dev), "device"));
+    THC_TRY(check_cuda(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count"));
+  }
+  // v chunks per (P, R) tile: fewest v steps on the busiest SM, counting one more per unit for its flush
+  const long long tiles = ((Pc + tc::BM - 1) / tc::BM) * ((N + tc::BM - 1) / tc::BM);
+  int nvc = 1;
+  long long best = -1;
+  for (long long c = 1; c <= std::min<long long>(n, 64); ++c) {
+    const long long waves = (tiles * c + sms - 1) / sms, cost = waves * ((n + c - 1) / c + 1);
+    if (best < 0 || cost < best) {
+      best = cost;
+      nvc = (int)c;
+    }
+  }
+  const dim3 grid((unsigned)std::min<long long>(tiles * nvc, sms), 1, 1);
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, K_SOX_BCD, 2.0 * 2.0 * Pc * N * n * n, &rec));
+  tc::sox_bcd_kernel<<<grid, tc::NTHREADS, tc::BcdCfg::SMEM, ctx->stream>>>(
+      yh, yl, uh, ul, ah, al, tc::BcdArgs{(int)Pc, (int)P0, (int)N, (int)n, nvc, D}, ctx->d_err);
+  return prof_end(ctx, &rec, cudaGetLastError(), "B C/D");
 }
 
 }  // namespace
@@ -488,7 +462,7 @@ int split_init(thc_ctx* ctx, size_t budget) {
   THC_TRY(pair(&ctx->Vs_h, &ctx->Vs_l, N * ldN, "Vs"));
   // blocking: per tau point and per P of the SOX block
   const size_t per_t = h * 2 * (2 * n * ldn + 2 * N * ldn + 3 * N * ldN + n * ldN) + 4 * 2 * N * N + 8 * N * N;
-  const size_t per_p = h * 2 * n * ldn + 4 * N * n;
+  const size_t per_p = h * 2 * n * ldn;
   const bool sox = ctx->terms & THC_SOX;
   if (sox) THC_TRY(pair(&ctx->Us_h, &ctx->Us_l, (size_t)N * n * ldn, "U"));
   size_t pb = std::max<size_t>(1, (budget / 2) / per_p);
@@ -511,7 +485,6 @@ int split_init(thc_ctx* ctx, size_t budget) {
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->Dd, 8 * tc * N * N, "D"));
   if (sox) {
     THC_TRY(pair(&ctx->Ats_h, &ctx->Ats_l, pb * n * ldn, "A^T blocks"));
-    THC_TRY(ctx_alloc(ctx, (void**)&ctx->Bf, 4 * pb * N * n, "B blocks"));
   }
   // constant operands
   THC_TRY(launch_split_f64(ctx, ctx->X, 0, 1, N, 1.0, split_of(ctx->Xt_h, ctx->Xt_l, N, ldn), n, "split X^T"));
@@ -601,7 +574,6 @@ int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* S
     if (sox) {
       THC_TRY(check_cuda(ctx, cudaMemsetAsync(ctx->Dd, 0, 8 * tc * NN, ctx->stream), "clear D"));
       const Split U = split_of(ctx->Us_h, ctx->Us_l, N * n, ldn);
-      const Split Ub = Split{ctx->Us_h, ctx->Us_l, n, ldn, N, n * ldn};  // [R][v][w]
       for (long long k = 0; k < tc; ++k) {
         const Split Gmk = Gms.at_batch(k, 1);
         const Split Yk = Ys.at_batch(k, 1);
@@ -612,11 +584,8 @@ int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* S
           // A^T_P[v][q] = sum_s U[P q][s] G(-tau)[v][s]  (G(-tau) carries its sign in Gms)
           THC_TRY(gemm(ctx, K_SOX_A, U.at_row(P0 * n, Pc * n), false, Gmk, false, Pc * n, n, n, 1,
                        EpiAt{At.hi, At.lo, (int)n, ldn}, "A"));
-          // B_P[R][v] = sum_q Y[R][q] A^T_P[v][q], stored R-major: Bf[R][P][v]
-          THC_TRY(gemm(ctx, K_SOX_B, Yk, false, At, true, N, n, n, Pc, EpiF32{ctx->Bf, Pc * n, n}, "B"));
-          // D[P][R] += sum_v (sum_w Y[P][w] U_R[v][w]) B_P[R][v]
-          THC_TRY(gemm(ctx, K_SOX_CD, Yk.at_row(P0, Pc), false, Ub, true, Pc, n, n, N,
-                       EpiHad{ctx->Bf, Dk, (int)n, (int)N, (int)P0, (int)Pc}, "C/D"));
+          // D[P][R] += sum_v (sum_w Y[P][w] U[R][v][w]) (sum_q Y[R][q] A^T_P[v][q])  (B and C never stored)
+          THC_TRY(launch_bcd(ctx, Yk, U, At, P0, Pc, Dk));
         }
       }
     }

@@ -21,15 +21,15 @@
 //   warp 1    allocates TMEM; one lane issues the 3 x 4 tcgen05.mma
 //             (kind::f16, M = 128, N = BN, K = 16) of a stage into one of two
 //             TMEM accumulators (stages alternate between them) and commits
-//             the stage back to the producer and to the epilogue;
+//             the stage back to the producer and to the epilogue (ragged
+//             edges: the last K stage issues only the steps that reach below
+//             K, and the last column tile uses N = round-up-16 of its width);
 //   warps 2-9 drain each finished stage accumulator with tcgen05.ld into FP32
 //             registers (warp w owns TMEM lanes 32 (w % 4) .. and one half of
 //             the columns), free it for the stage after next, and finally hand
 //             32 x 32 chunks, staged in a private XOR-swizzled shared-memory
 //             tile, to the epilogue functor, which the whole warp runs with
-//             coalesced global accesses.  A functor that reads one input value
-//             per output element (kStagesRows) has those rows copied into
-//             shared memory with cp.async while its tile accumulates.
+//             coalesced global accesses.
 // Draining every stage ("promotion") keeps the tensor core's internal
 // accumulation to one 64-deep stage: measured on GB300, accumulating a
 // 1000-deep K inside the tensor core loses several times more precision than
@@ -58,41 +58,20 @@ constexpr int NTHREADS = 320;  // 10 warps: TMA, MMA, 8 epilogue
 constexpr int NEPI = 256;      // epilogue threads
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s per wait
 
-template <int BN, int ROWS = 0, bool ROWWISE = false>
+template <int BN>
 struct Cfg {
-  // ROWS: FP32 values (padding included) per epilogue thread staged for the functor;
-  // ROWWISE: the functor works on each thread's own row, without the 32 x 32 staging tile
   static constexpr int A_BYTES = BM * BKE * 2;
   static constexpr int B_BYTES = BN * BKE * 2;
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int TMEM_COLS = 2 * BN;   // two accumulators; BN in {128, 256}
   static constexpr int HALF = BN / 2;         // columns per epilogue thread
-  static constexpr int STAGING = ROWWISE ? 0 : 8 * 32 * 32 * 4;  // one swizzled 32 x 32 FP32 tile per warp
-  static constexpr int ROW_STAGING = 8 * 32 * ROWS * 4;           // staged functor inputs, 32 rows per warp
-  static constexpr int FIXED = STAGING + ROW_STAGING + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int STAGING = 8 * 32 * 32 * 4;  // one swizzled 32 x 32 FP32 tile per warp
+  static constexpr int FIXED = STAGING + 1024 /*align*/ + 256 /*barriers*/;
   static constexpr int STAGES = ((232448 - FIXED) / STAGE) >= 3 ? 3 : 2;
   static constexpr int SMEM = STAGES * STAGE + FIXED;
   static_assert(SMEM <= 232448, "shared memory per CTA");
   static_assert(BN == 128 || BN == 256, "tile width");
 };
-
-// Staged-row geometry of a functor in a given mode: promoted functors that stage rows
-// use HALF values per thread; row-wise functors in the single-chunk mode use HALF + 4
-// (16-byte aligned rows, fewer bank conflicts when lanes walk their own rows).
-template <int BN, bool MULTI, class Epi>
-struct CfgFor {
-  static constexpr bool ROWWISE = !MULTI && Epi::kRowWise;
-  static constexpr int ROWS = ROWWISE ? BN / 2 + 4 : ((MULTI && Epi::kStagesRows) ? BN / 2 : 0);
-  using type = Cfg<BN, ROWS, ROWWISE>;
-};
-
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
-               "l"(gsrc)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -240,14 +219,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                       const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int M,
                       int N, int K, int batch, Operands ops, Epi epi, int* err) {
-  using C = typename CfgFor<BN, MULTI, Epi>::type;
-  constexpr bool ROWWISE = CfgFor<BN, MULTI, Epi>::ROWWISE;
-  constexpr int RSTRIDE = CfgFor<BN, MULTI, Epi>::ROWS;
+  using C = Cfg<BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* staging = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE);
-  float* row_staging = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + C::STAGING);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STAGING + C::ROW_STAGING);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE + C::STAGING);
   uint64_t* empty = full + C::STAGES;
   uint64_t* acc_full = empty + C::STAGES;  // [2] stage accumulator ready for the epilogue
   uint64_t* acc_free = acc_full + 2;       // [2] stage accumulator drained
@@ -308,10 +284,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
       long long g = 0, local = 0;  // K stages and tiles handled by this CTA
       bool ok = true;
       for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++local) {
+        // a ragged last column tile multiplies only its round-up-to-16 width (columns beyond
+        // it stay unwritten in TMEM; every epilogue skips columns >= N)
+        const int nt = (int)((t / tm) % tn);
+        const int n_eff = min(BN, (N - nt * BN + 15) & ~15);
+        const uint32_t idesc = idesc_bf16(BM, n_eff);
         if (!MULTI) {  // one accumulator per tile, alternating between the two buffers
           const int buf = (int)(local & 1);
           if (!mbar_wait(&acc_free[buf], ((uint32_t)(local >> 1) & 1) ^ 1)) {
@@ -333,65 +313,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint32_t base = smem_u32(smem + s * C::STAGE);
           const uint64_t ah = sw128_desc(base), al = sw128_desc(base + C::A_BYTES);
           const uint64_t bh = sw128_desc(base + 2 * C::A_BYTES), bl = sw128_desc(base + 2 * C::A_BYTES + C::B_BYTES);
+          // the last stage of a ragged K issues only the 16-deep steps that reach below K
+          const int ksteps = min(BKE / 16, (K - kb * BKE + 15) >> 4);
 #pragma unroll
           for (int k = 0; k < BKE / 16; ++k) {
-            const uint64_t off = static_cast<uint64_t>((k * 32) >> 4);  // 16 BF16 = 32 bytes along K
-            mma_bf16(d, ah + off, bh + off, idesc, (MULTI ? k : (kb | k)) != 0);
-            mma_bf16(d, ah + off, bl + off, idesc, 1u);
-            mma_bf16(d, al + off, bh + off, idesc, 1u);
+            if (k < ksteps) {
+              const uint64_t off = static_cast<uint64_t>((k * 32) >> 4);  // 16 BF16 = 32 bytes along K
+              mma_bf16(d, ah + off, bh + off, idesc, (MULTI ? k : (kb | k)) != 0);
+              mma_bf16(d, ah + off, bl + off, idesc, 1u);
+              mma_bf16(d, al + off, bh + off, idesc, 1u);
+            }
           }
           mma_commit(&empty[s]);  // frees the smem stage once these MMAs have read it
           if (MULTI || kb == nkb - 1) mma_commit(&acc_full[buf]);  // accumulator ready
         }
       }
     }
-  } else if (ROWWISE) {
-    // single-chunk, row-wise functor: every thread reduces its own row against the
-    // input row it copied into shared memory at the start of the tile
-    const int quarter = warp & 3, half = (warp - 2) >> 2;
-    float* myrow = row_staging + ((warp - 2) * 32 + lane) * RSTRIDE;
-    long long local = 0;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
-      const int mt = (int)(t % tm), nt = (int)((t / tm) % tn), b = (int)(t / ((long long)tm * tn));
-      const int m0 = mt * BM, n0 = nt * BN, buf = (int)(local & 1);
-      const int row = m0 + quarter * 32 + lane, colb = n0 + half * C::HALF;
-      epi.stage_rows(b, row, colb, C::HALF, M, N, myrow);  // the previous tile is done with the buffer
-      cp_async_commit();
-      if (!mbar_wait(&acc_full[buf], (uint32_t)(local >> 1) & 1)) {
-        if (lane == 0) atomicExch(err, 3);
-        break;
-      }
-      tc_fence_after();
-      cp_async_wait_all();
-      const uint32_t src = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + buf * BN + half * C::HALF;
-      float part = 0.f;
-#pragma unroll 1
-      for (int c = 0; c < C::HALF; c += 32) {
-        uint32_t r[32];
-        tmem_ld16(src + c, r);
-        tmem_ld16(src + c + 16, r + 16);
-        tmem_wait_ld();
-        part = epi.row_chunk(b, row, colb + c, r, myrow + c, M, N, part);
-      }
-      tc_fence_before();
-      mbar_arrive(&acc_free[buf]);
-      epi.row_done(b, row, part, M);
-    }
   } else if (!MULTI) {
     const int quarter = warp & 3, half = (warp - 2) >> 2;
     const TileRef tile{staging + (warp - 2) * 32 * 32};
     long long local = 0;
-    auto prefetch_tile = [&](long long tt) {  // L2 warm-up of what the epilogue of tile tt reads
-      if (tt >= tiles) return;
-      const int pm = (int)(tt % tm), pn = (int)((tt / tm) % tn), pb = (int)(tt / ((long long)tm * tn));
-      epi.prefetch(pb, pm * BM + quarter * 32 + lane, pn * BN + half * C::HALF, C::HALF, M, N);
-    };
-    prefetch_tile(blockIdx.x);
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
       const int mt = (int)(t % tm), nt = (int)((t / tm) % tn), b = (int)(t / ((long long)tm * tn));
       const int m0 = mt * BM, n0 = nt * BN, buf = (int)(local & 1);
-      // one tile ahead: by the time this CTA stores tile t + gridDim.x its inputs are in L2
-      prefetch_tile(t + gridDim.x);
       if (!mbar_wait(&acc_full[buf], (uint32_t)(local >> 1) & 1)) {
         if (lane == 0) atomicExch(err, 3);
         break;
@@ -410,7 +354,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int j = 0; j < 32; ++j) tile(lane, j) = v[j];
         __syncwarp();
         const int col0 = n0 + half * C::HALF + c;
-        if (col0 < N) epi(b, row0, col0, tile, lane, M, N, nullptr, 0);
+        if (col0 < N) epi(b, row0, col0, tile, lane, M, N);
         __syncwarp();
       }
       tc_fence_before();
@@ -425,15 +369,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
       const int mt = (int)(t % tm), nt = (int)((t / tm) % tn), b = (int)(t / ((long long)tm * tn));
       const int m0 = mt * BM, n0 = nt * BN;
-      float* rows = row_staging + (warp - 2) * 32 * C::HALF;
-      if constexpr (Epi::kStagesRows) {
-        // copy this thread's functor inputs into shared memory while the tile accumulates
-        epi.stage_rows(b, m0 + quarter * 32 + lane, n0 + half * C::HALF, C::HALF, M, N, rows + lane * C::HALF);
-        cp_async_commit();
-      } else {
-        // warm L2 with whatever the epilogue will read while the tile accumulates
-        epi.prefetch(b, m0 + quarter * 32 + lane, n0 + half * C::HALF, C::HALF, M, N);
-      }
       float acc[C::HALF];
 #pragma unroll
       for (int i = 0; i < C::HALF; ++i) acc[i] = 0.f;
@@ -458,7 +393,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_arrive(&acc_free[buf]);
       }
       if (!ok) break;
-      if constexpr (Epi::kStagesRows) cp_async_wait_all();
       __syncwarp();
       const int row0 = m0 + quarter * 32;
 #pragma unroll
@@ -467,7 +401,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) tile(lane, j) = acc[c + j];
         __syncwarp();
-        if (col0 < N) epi(b, row0, col0, tile, lane, M, N, rows + c, C::HALF);
+        if (col0 < N) epi(b, row0, col0, tile, lane, M, N);
         __syncwarp();
       }
     }

@@ -24,6 +24,7 @@ enum KernelClass {
   K_BACK,         // M X^T and X (M X^T)
   K_ENERGY,       // trace and weighted sum
   K_SPLIT,        // FP64 <-> BF16 hi/lo conversions
+  K_SOX_BCD,      // fused B_PRv and C/D (split precision)
   K_COUNT
 };
 const char* kernel_class_name(int k);
@@ -83,7 +84,6 @@ struct thc_ctx {
   __nv_bfloat16 *Ms_h = nullptr, *Ms_l = nullptr;   // merged M, tc x N x ldN
   __nv_bfloat16 *T2s_h = nullptr, *T2s_l = nullptr; // (M X^T)^T, tc x n x ldN
   __nv_bfloat16 *Ats_h = nullptr, *Ats_l = nullptr; // A^T blocks, Pb x n x ldn
-  float *Bf = nullptr;                              // B block, R-major: N x Pc x n
   double *Dd = nullptr;                             // D, tc x N x N
   int *d_err = nullptr;                             // device error flag of the tensor-core kernels
 
