@@ -19,7 +19,13 @@
 // its FP32 partial tile of D into the FP64 D with one atomic per element.  Units
 // are numbered with the v chunk slowest, so the CTAs of a wave walk the same few
 // values of v together and the U_v and A^T_v slices they read are served from
-// L2.  A persistent CTA takes units blockIdx.x, blockIdx.x + gridDim.x, ...
+// L2.  A persistent cluster takes units c, c + clusters, ...
+//
+// CTAs run in clusters of CP x CR (1 x 2 in use): the CTAs of a cluster share
+// their P tile (or R tile) and so the operands of that side.  Each loads one
+// slice of a shared operand block and multicasts it (TMA .multicast::cluster)
+// to the CTAs that need it, which cuts the operand traffic from L2 by a quarter
+// for a pair along R.
 //
 // Warp roles (as in split_gemm_kernel):
 //   warp 0    one lane issues the TMA loads of every 64-deep K stage: for the C
@@ -58,17 +64,57 @@ struct BcdArgs {
   int P0;     // first P of the block: row offset into Y and D
   int N;      // THC rank: range of R, rows of Y, row length of D
   int n;      // AO count: range of v, depth (w, q) of both products
-  int nvc;    // v chunks per (P, R) tile
+  int nvc;    // v chunks per cluster tile
   double* D;  // N x N FP64, D[P][R] at P * N + R
 };
 
-// Maps: Y (k, row, 1), box 64 x 128 x 1; U (w, v, R) and A^T (q, v, P), box 64 x 1 x 128.
+// Tensor maps of one operand half (hi or lo): Y rows for the P side (box 64 x 128/CR)
+// and the R side (box 64 x 128/CP), U (w, v, R) with box 64 x 1 x 128/CP, and
+// A^T (q, v, P) with box 64 x 1 x 128/CR.
+struct BcdMaps {
+  CUtensorMap yp, yr, u, at;
+};
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n barrier.cluster.wait.acquire;" ::: "memory");
+}
+// TMA load of a box into the same shared-memory offset of every CTA in mask, each
+// of whose mbarrier at offset bar receives the completed bytes.
+__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                               int c2, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster [%0], "
+      "[%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+// tcgen05.commit arriving on the mbarrier at offset bar of every CTA in mask.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+// CP x CR cluster (rank = pi CR + rj) over a (CP 128) x (CR 128) block of D:
+// CTA (pi, rj) owns P tile CP t_P + pi and R tile CR t_R + rj.  The P-side operands
+// (Y rows of the P tile, A^T_v) are common to the CR CTAs of a row pi: each loads
+// one 128/CR-row slice and multicasts it to them; the R-side operands (U_v, Y rows
+// of the R tile) likewise across the CP CTAs of a column rj.  Every CTA's MMA
+// releases a stage on all CTAs of the cluster, so a producer refills a stage only
+// when every CTA it writes into has consumed it.  CP = CR = 1 is the plain kernel.
+template <int CP, int CR>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    sox_bcd_kernel(const __grid_constant__ CUtensorMap mYhi, const __grid_constant__ CUtensorMap mYlo,
-                   const __grid_constant__ CUtensorMap mUhi, const __grid_constant__ CUtensorMap mUlo,
-                   const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo, BcdArgs a,
-                   int* err) {
+    sox_bcd_kernel(const __grid_constant__ BcdMaps hi, const __grid_constant__ BcdMaps lo, BcdArgs a, int* err) {
   using C = BcdCfg;
+  constexpr int CS = CP * CR;
+  constexpr int PROWS = BM / CR, RROWS = BM / CP;  // rows of the slices this CTA loads
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* staging = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE);
@@ -79,14 +125,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_free + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = CS > 1 ? cluster_ctarank() : 0u;
+  const int pi = (int)rank / CR, rj = (int)rank % CR;
   const int nkb = (a.n + BKE - 1) / BKE;
   const int tm = (a.Pc + BM - 1) / BM, tn = (a.N + BM - 1) / BM;
-  const long long tiles = (long long)tm * tn, units = tiles * a.nvc;
-  // unit u: v chunk u / tiles (slowest), then P tile fastest
+  const int tm2 = (tm + CP - 1) / CP, tn2 = (tn + CR - 1) / CR;
+  const long long ctiles = (long long)tm2 * tn2, units = ctiles * a.nvc;
+  const long long cl = blockIdx.x / CS, ncl = gridDim.x / CS;
+  // unit u of a cluster: v chunk u / ctiles (slowest), then P fastest
   auto decode = [&](long long u, int& pt, int& rt, int& v0, int& v1) {
-    const long long vc = u / tiles, t = u - vc * tiles;
-    pt = (int)(t % tm);
-    rt = (int)(t / tm);
+    const long long vc = u / ctiles, t = u - vc * ctiles;
+    pt = (int)(t % tm2) * CP + pi;
+    rt = (int)(t / tm2) * CR + rj;
     v0 = (int)(vc * a.n / a.nvc);
     v1 = (int)((vc + 1) * a.n / a.nvc);
   };
@@ -94,19 +144,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CS);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_free[i], NEPI);
     }
     fence_mbar_init();
-    prefetch_map(&mYhi);
-    prefetch_map(&mYlo);
-    prefetch_map(&mUhi);
-    prefetch_map(&mUlo);
-    prefetch_map(&mAhi);
-    prefetch_map(&mAlo);
+    prefetch_map(&hi.yp);
+    prefetch_map(&lo.yp);
+    prefetch_map(&hi.yr);
+    prefetch_map(&lo.yr);
+    prefetch_map(&hi.u);
+    prefetch_map(&lo.u);
+    prefetch_map(&hi.at);
+    prefetch_map(&lo.at);
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -114,16 +166,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CS > 1) cluster_sync_all();  // every CTA's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
     if (lane == 0) {
+      uint16_t pmask = 0, rmask = 0;  // CTAs sharing this CTA's P tile / R tile
+      for (int r = 0; r < CR; ++r) pmask |= (uint16_t)(1u << (pi * CR + r));
+      for (int p = 0; p < CP; ++p) rmask |= (uint16_t)(1u << (p * CR + rj));
+      // one slice of an operand block: multicast when shared, a plain load otherwise
+      auto load = [&](uint8_t* blk, int slice, int rows, const CUtensorMap* m, uint64_t* bar, int c0, int c1, int c2,
+                      uint16_t mask, bool shared) {
+        uint8_t* dst = blk + slice * rows * 128;
+        if (shared)
+          tma_load_3d_mc(dst, m, bar, c0, c1, c2, mask);
+        else
+          tma_load_3d(dst, m, bar, c0, c1, c2);
+      };
       long long g = 0;  // running K-stage counter
       bool ok = true;
-      for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
+      for (long long u = cl; u < units && ok; u += ncl) {
         int pt, rt, v0, v1;
         decode(u, pt, rt, v0, v1);
+        const int prow = pt * BM + rj * PROWS, rrow = rt * BM + pi * RROWS;  // first rows of this CTA's slices
         for (int v = v0; v < v1 && ok; ++v) {
           for (int prod = 0; prod < 2 && ok; ++prod) {
             for (int kb = 0; kb < nkb; ++kb, ++g) {
@@ -138,30 +204,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const int k0 = kb * BKE;
               mbar_arrive_expect_tx(&full[s], C::STAGE);
               if (prod == 0) {  // C_v: A = Y (P tile), B = U_v (R tile)
-                tma_load_3d(st, &mYhi, &full[s], k0, a.P0 + pt * BM, 0);
-                tma_load_3d(st + C::OP, &mYlo, &full[s], k0, a.P0 + pt * BM, 0);
-                tma_load_3d(st + 2 * C::OP, &mUhi, &full[s], k0, v, rt * BM);
-                tma_load_3d(st + 3 * C::OP, &mUlo, &full[s], k0, v, rt * BM);
+                load(st, rj, PROWS, &hi.yp, &full[s], k0, a.P0 + prow, 0, pmask, CR > 1);
+                load(st + C::OP, rj, PROWS, &lo.yp, &full[s], k0, a.P0 + prow, 0, pmask, CR > 1);
+                load(st + 2 * C::OP, pi, RROWS, &hi.u, &full[s], k0, v, rrow, rmask, CP > 1);
+                load(st + 3 * C::OP, pi, RROWS, &lo.u, &full[s], k0, v, rrow, rmask, CP > 1);
               } else {          // B_v: A = A^T_v (P tile), B = Y (R tile)
-                tma_load_3d(st, &mAhi, &full[s], k0, v, pt * BM);
-                tma_load_3d(st + C::OP, &mAlo, &full[s], k0, v, pt * BM);
-                tma_load_3d(st + 2 * C::OP, &mYhi, &full[s], k0, rt * BM, 0);
-                tma_load_3d(st + 3 * C::OP, &mYlo, &full[s], k0, rt * BM, 0);
+                load(st, rj, PROWS, &hi.at, &full[s], k0, v, prow, pmask, CR > 1);
+                load(st + C::OP, rj, PROWS, &lo.at, &full[s], k0, v, prow, pmask, CR > 1);
+                load(st + 2 * C::OP, pi, RROWS, &hi.yr, &full[s], k0, rrow, 0, rmask, CP > 1);
+                load(st + 3 * C::OP, pi, RROWS, &lo.yr, &full[s], k0, rrow, 0, rmask, CP > 1);
               }
             }
+          }
+        }
+      }
+      if constexpr (CS > 1) {
+        // every CTA's release of the last stages has arrived here before the CTA can exit
+        for (int i = 0; i < C::STAGES && ok; ++i, ++g) {
+          if (!mbar_wait(&empty[g % C::STAGES], ((uint32_t)(g / C::STAGES) & 1) ^ 1)) {
+            atomicExch(err, 14);
+            ok = false;
           }
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      const uint16_t all = (uint16_t)((1u << CS) - 1);
       long long g = 0, j = 0;  // K stages and v steps handled by this CTA
       bool ok = true;
-      for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
+      for (long long u = cl; u < units && ok; u += ncl) {
         int pt, rt, v0, v1;
         decode(u, pt, rt, v0, v1);
-        // a ragged last R tile multiplies only its round-up-to-16 width
-        const uint32_t idesc = idesc_bf16(BM, min(BM, (a.N - rt * BM + 15) & ~15));
+        // a ragged last R tile multiplies only its round-up-to-16 width (at least 16)
+        const uint32_t idesc = idesc_bf16(BM, max(16, min(BM, (a.N - rt * BM + 15) & ~15)));
         for (int v = v0; v < v1 && ok; ++v, ++j) {
           const int buf = (int)(j & 1);
           if (!mbar_wait(&acc_free[buf], ((uint32_t)(j >> 1) & 1) ^ 1)) {
@@ -193,7 +269,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   mma_bf16(d, al + off, bh + off, idesc, 1u);
                 }
               }
-              mma_commit(&empty[s]);
+              if constexpr (CS > 1)
+                mma_commit_mc(&empty[s], all);  // the stage is free here and in every CTA loading into it
+              else
+                mma_commit(&empty[s]);
             }
           }
           if (ok) mma_commit(&acc_full[buf]);  // C_v and B_v of this v complete
@@ -206,7 +285,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const TileRef tile{staging + (warp - 2) * 32 * 32};
     long long j = 0;
     bool ok = true;
-    for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
+    for (long long u = cl; u < units && ok; u += ncl) {
       int pt, rt, v0, v1;
       decode(u, pt, rt, v0, v1);
       float acc[64];
@@ -254,6 +333,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CS > 1) cluster_sync_all();  // no CTA leaves while another may still signal it
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, C::TMEM_COLS);
