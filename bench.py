@@ -38,6 +38,9 @@ L2_BYTES = 129 * 1024 * 1024
 NCU_TRAFFIC = {
     ("sox_CD", "thc200"): (1.927304e9 + 0.011961e9, "profiles/sox_cd_kernel_thc200s.md (same per-launch shape)"),
     ("sox_CD", "thc200s"): (1.927304e9 + 0.011961e9, "profiles/sox_cd_kernel_thc200s.md"),
+    ("sox_BCD", "thc200:bf16x3"): (0.397607e9 + 0.019301e9,
+                                   "profiles/sox_bcd_kernel_thc200s.md (same per-launch shape)"),
+    ("sox_BCD", "thc200s:bf16x3"): (0.397607e9 + 0.019301e9, "profiles/sox_bcd_kernel_thc200s.md"),
 }
 
 
