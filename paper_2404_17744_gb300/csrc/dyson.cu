@@ -9,14 +9,18 @@
 //
 // The tau <-> i w transforms are the sparse-sampling matrices of an IR basis
 // (supplied by the caller); they run in the DFMA contraction tile.  The
-// inversions are an in-place Gauss-Jordan elimination, a cluster of two CTAs
-// per frequency (each owns half of the rows; FP64 is DFMA-bound on GB300, so
-// spreading the n_iw matrices over twice as many SMs halves the time):
+// inversions are an in-place Gauss-Jordan elimination, a cluster of several
+// CTAs per frequency (each owns a block of rows; FP64 is DFMA-bound on GB300,
+// so the matrices are spread over as many SMs as the device holds clusters):
 // Im[(i w + mu) S - F - Sigma(i w)] = w S - Im Sigma(i w) is
 // definite for a causal self-energy, so every leading principal minor is
-// non-singular and no pivoting is needed.
+// non-singular and no pivoting is needed.  When the sampled frequencies come
+// in pairs w, -w (the Matsubara sampling of an IR basis does), only the
+// positive half is inverted: for real S, F and Sigma(tau), G(-i w) is the
+// complex conjugate of G(i w).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -45,6 +49,10 @@ struct thc_dyson {
   double *Giw = nullptr;                                // n_iw x n^2 x 2
   double *g_l = nullptr;                                // L x n^2 (real part)
   double *tr = nullptr;                                 // n_iw x 2 partial traces
+  double *part = nullptr;                               // per-block partial sums of the energy contraction
+  bool half = false;                                    // frequencies in pairs (w_m = -w_{n_iw-1-m}): invert m >= n_iw/2
+  int gj_cs = 1;                                        // CTAs per cluster of the Gauss-Jordan kernel
+  bool gj_resident = false;                             // its rows kept in shared memory
   double *scal = nullptr;                               // small scalar scratch
   int evals = 0;                                        // N(mu) evaluations of the last solve
   double slope = 0.0;                                   // last secant estimate of dN/dmu (0: none)
@@ -115,47 +123,97 @@ __global__ void build_kernel(int n, int n_iw, const double* __restrict__ iw, dou
   }
 }
 
-// In-place Gauss-Jordan inverse of one n x n complex matrix per cluster of two
-// CTAs (no pivoting).  CTA rank c owns rows [c h, min(n, (c + 1) h)), h = ceil(n / 2).
-// Step k: every CTA reads the current pivot row k from global memory (L2) and
-// scales it into shared memory, and stages column k of its own rows; a cluster
-// barrier; each CTA updates its rows (the owner of row k stores the scaled
-// row); a second cluster barrier makes the step visible before step k + 1.
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024) gj_invert_kernel(int n, double2* __restrict__ A0) {
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// In-place Gauss-Jordan inverse of matrix m0 + blockIdx.x / CS (n x n complex, no
+// pivoting), one cluster of CS CTAs per matrix; CTA rank c owns rows
+// [c h, min(n, (c + 1) h)), h = ceil(n / CS).  With resident != 0 a CTA keeps its
+// rows in shared memory from the first step to the last (when h n complex values
+// fit); otherwise they stay in global memory (L2).  Step k: the owner of row k
+// publishes the scaled row r_j = a_kj / a_kk (r_k = 1 / a_kk, computed once by
+// one thread: FP64 division is costly on this GPU) in one of two shared-memory
+// buffers; one cluster barrier; every CTA copies it from the owner's shared
+// memory (distributed shared memory), reads and clears column k of its own rows,
+// and updates them:
+//   a_ij -= a_ik r_j (i != k; column k becomes -a_ik / a_kk),  a_kj = r_j.
+// A CTA barrier orders its own writes before the next step reads them.
+__global__ void __launch_bounds__(1024) gj_cluster_kernel(int n, int m0, int resident, double2* __restrict__ A0) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int h = (n + CS - 1) / CS, r0 = rank * h, nr = max(0, min(n, r0 + h) - r0);
   extern __shared__ double2 sh[];
-  double2* rowk = sh;      // n
-  double2* colk = sh + n;  // rows of this CTA
-  const int rank = (int)cluster.block_rank();
-  const int h = (n + 1) / 2, r0 = rank * h, r1 = min(n, r0 + h), nr = r1 - r0;
-  double2* A = A0 + (long long)(blockIdx.x / 2) * n * n;
+  double2* pub = sh;           // [2][n] scaled pivot rows published by their owner
+  double2* rowk = sh + 2 * n;  // [n] this CTA's copy of the current one
+  double2* colk = rowk + n;    // [h] column k of this CTA's rows
+  double2* A = A0 + (long long)(m0 + blockIdx.x / CS) * n * n;
+  double2* blk = A + (long long)r0 * n;  // this CTA's rows, row stride n
   const long long cnt = (long long)nr * n;
+  if (resident) {
+    double2* s_rows = colk + h;
+    for (long long e = threadIdx.x; e < cnt; e += blockDim.x) s_rows[e] = blk[e];
+    blk = s_rows;
+    __syncthreads();
+  }
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
   for (int k = 0; k < n; ++k) {
-    const double2 p = A[(long long)k * n + k];
-    const double den = p.x * p.x + p.y * p.y;
-    const double2 ip = make_double2(p.x / den, -p.y / den);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const double2 a = (j == k) ? make_double2(1.0, 0.0) : A[(long long)k * n + j];
-      rowk[j] = make_double2(a.x * ip.x - a.y * ip.y, a.x * ip.y + a.y * ip.x);
+    const int owner = k / h;
+    double2* buf = pub + (k & 1) * n;
+    if (rank == owner) {  // uniform over the CTA
+      const double2* ak = blk + (long long)(k - r0) * n;
+      if (threadIdx.x == 0) {
+        const double2 p = ak[k];
+        const double inv = 1.0 / (p.x * p.x + p.y * p.y);
+        buf[k] = make_double2(p.x * inv, -p.y * inv);
+      }
+      __syncthreads();
+      const double2 ip = buf[k];
+      for (int j = threadIdx.x; j < n; j += blockDim.x)
+        if (j != k) buf[j] = cmul(ak[j], ip);
     }
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) colk[i] = A[(long long)(r0 + i) * n + k];
-    cluster.sync();  // both CTAs have read row k before its owner overwrites it
-    for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int li = (int)(e / n), j = (int)(e - (long long)li * n), i = r0 + li;
-      const long long o = (long long)i * n + j;
-      if (i == k) {
-        A[o] = rowk[j];
-      } else {
-        const double2 f = colk[li], r = rowk[j];
-        double2 a = (j == k) ? make_double2(0.0, 0.0) : A[o];
-        a.x -= f.x * r.x - f.y * r.y;
-        a.y -= f.x * r.y + f.y * r.x;
-        A[o] = a;
+    // column k of the other rows: staged, then cleared (its update leaves -a_ik r_k)
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+      colk[i] = blk[(long long)i * n + k];
+      if (r0 + i != k) blk[(long long)i * n + k] = make_double2(0.0, 0.0);
+    }
+    cluster.sync();  // row k is published; every CTA is past step k - 1
+    const double2* src = cluster.map_shared_rank(buf, owner);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) rowk[j] = src[j];
+    __syncthreads();
+    for (int j = tx; j < n; j += 32) {
+      const double2 r = rowk[j];
+      for (int li = ty; li < nr; li += nty) {
+        double2* a = blk + (long long)li * n + j;
+        if (r0 + li == k) {
+          *a = r;
+        } else {
+          const double2 f = colk[li];
+          double2 v = *a;
+          v.x -= f.x * r.x - f.y * r.y;
+          v.y -= f.x * r.y + f.y * r.x;
+          *a = v;
+        }
       }
     }
-    __threadfence();
-    cluster.sync();  // step k is complete in global memory for both CTAs
+    __syncthreads();
+  }
+  if (resident) {
+    double2* out = A + (long long)r0 * n;
+    for (long long e = threadIdx.x; e < cnt; e += blockDim.x) out[e] = blk[e];
+  }
+  cluster.sync();  // no CTA leaves while another may still read its published row
+}
+
+// G[m] = conj(G[n_iw - 1 - m]) for m < n_iw / 2.
+__global__ void mirror_conj_kernel(long long nn, int nw, double2* __restrict__ G) {
+  const long long total = nn * (nw / 2);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long m = i / nn, e = i - m * nn;
+    const double2 v = G[(long long)(nw - 1 - m) * nn + e];
+    G[m * nn + e] = make_double2(v.x, -v.y);
   }
 }
 
@@ -195,41 +253,69 @@ __global__ void trace_gs_kernel(int n, const double2* __restrict__ G, const doub
   }
 }
 
-// out[0] = sum_l p_l sum_ij a_l[i][j] b_l[j][i]; out[1] = sum_l ub_l sum_ij a_l[i][j] M[j][i]; one CTA.
+// part[2 b], part[2 b + 1]: block b's share of
+//   sum_l p_l sum_ij a_l[i][j] b_l[j][i]   and   sum_l ub_l sum_ij a_l[i][j] M[j][i]
+// over the rows (l, i) it owns (one warp per row, lanes along j).
 __global__ void coef_contract_kernel(int n, int L, const double* __restrict__ a, const double* __restrict__ b,
                                      const double* __restrict__ p, const double* __restrict__ ub,
-                                     const double* __restrict__ M, double* __restrict__ out) {
-  const long long nn = (long long)n * n;
+                                     const double* __restrict__ M, double* __restrict__ part) {
+  const long long nn = (long long)n * n, rows = (long long)L * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   double s1 = 0.0, s2 = 0.0;
-  for (long long e = threadIdx.x; e < nn * L; e += blockDim.x) {
-    const long long l = e / nn, r = e - l * nn, i = r / n, j = r - i * n;
-    const double av = a[e];
-    s1 = fma(p[l] * av, b[l * nn + j * n + i], s1);
-    if (M) s2 = fma(ub[l] * av, M[j * n + i], s2);
+  for (long long row = (long long)blockIdx.x * nwarp + warp; row < rows; row += (long long)gridDim.x * nwarp) {
+    const long long l = row / n, i = row - l * n;
+    const double* ar = a + row * n;
+    const double* bl = b + l * nn;
+    double t1 = 0.0, t2 = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const double av = ar[j];
+      t1 = fma(av, bl[(long long)j * n + i], t1);
+      if (M) t2 = fma(av, M[(long long)j * n + i], t2);
+    }
+    s1 = fma(p[l], t1, s1);
+    s2 = fma(ub[l], t2, s2);
   }
   __shared__ double r1[32], r2[32];
   for (int o = 16; o > 0; o >>= 1) {
     s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   }
-  if ((threadIdx.x & 31) == 0) {
-    r1[threadIdx.x >> 5] = s1;
-    r2[threadIdx.x >> 5] = s2;
+  if (lane == 0) {
+    r1[warp] = s1;
+    r2[warp] = s2;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
-    s1 = threadIdx.x < (blockDim.x >> 5) ? r1[threadIdx.x] : 0.0;
-    s2 = threadIdx.x < (blockDim.x >> 5) ? r2[threadIdx.x] : 0.0;
+    s1 = threadIdx.x < nwarp ? r1[threadIdx.x] : 0.0;
+    s2 = threadIdx.x < nwarp ? r2[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) {
       s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
     if (threadIdx.x == 0) {
-      out[0] = s1;
-      out[1] = s2;
+      part[2 * blockIdx.x] = s1;
+      part[2 * blockIdx.x + 1] = s2;
     }
   }
 }
+
+// out[0..1] = column sums of part[cnt][2], in a fixed order (one warp).
+__global__ void pair_sum_kernel(int cnt, const double* __restrict__ part, double* __restrict__ out) {
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = threadIdx.x; i < cnt; i += 32) {
+    s1 += part[2 * i];
+    s2 += part[2 * i + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s1;
+    out[1] = s2;
+  }
+}
+constexpr int kEnergyBlocks = 296;  // 2 per SM
 
 int blocks_for(long long total) { return (int)std::min<long long>((total + 255) / 256, 152LL * 32); }
 
@@ -244,24 +330,114 @@ int sigma_to_iw(thc_dyson* d, const double* Sig_tau) {
                            AccEpi{d->Siw + 1, 0, 2 * n2, 2, 1.0, false}, "Sigma(iw) im");
 }
 
-// G(i w_m) for all m at chemical potential mu; returns the electron count per spin.
+// Dynamic shared memory of gj_cluster_kernel: pivot-row buffers and column, plus the
+// CTA's rows when they are resident.
+size_t gj_smem(int n, int cs, bool resident) {
+  const size_t h = (size_t)((n + cs - 1) / cs);
+  return sizeof(double2) * (3 * (size_t)n + h + (resident ? h * (size_t)n : 0));
+}
+constexpr size_t kGjSmemMax = 232448;  // 227 KB per CTA
+
+// Cluster size of the Gauss-Jordan kernel and whether a CTA's rows stay in shared
+// memory: the fewest steps' worth of work on the busiest CTA, i.e. rows per CTA times
+// waves of resident clusters, with rows kept in global memory (L2) counted twice
+// (ties: smaller clusters).
+int choose_gj_cluster(thc_dyson* d) {
+  static std::mutex mu;
+  static bool attr_set = false;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!attr_set) {
+      THC_TRY(dcheck(d, cudaFuncSetAttribute(gj_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kGjSmemMax),
+                     "Gauss-Jordan shared memory"));
+      attr_set = true;
+    }
+  }
+  const long long count = d->half ? d->n_iw / 2 : d->n_iw;
+  int best_cs = 1;
+  bool best_res = false;
+  long long best = -1;
+  for (int cs = 1; cs <= 8 && cs <= d->n; ++cs) {
+    for (int res = 0; res < 2; ++res) {
+      const size_t smem = gj_smem(d->n, cs, res != 0);
+      if (smem > kGjSmemMax) continue;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)cs;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)(cs * std::max<long long>(1, count)), 1, 1);
+      cfg.blockDim = dim3(1024, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int q = 0;
+      if (cudaOccupancyMaxActiveClusters(&q, gj_cluster_kernel, &cfg) != cudaSuccess || q < 1) {
+        cudaGetLastError();
+        continue;
+      }
+      const long long cost = ((count + q - 1) / q) * ((d->n + cs - 1) / cs) * (res ? 1 : 2);
+      if (best < 0 || cost < best) {
+        best = cost;
+        best_cs = cs;
+        best_res = res != 0;
+      }
+    }
+  }
+  d->gj_cs = best_cs;
+  d->gj_resident = best_res;
+  return THC_OK;
+}
+
+// Gauss-Jordan inversion of matrices m0 .. m0 + count - 1 of d->Giw, one cluster of d->gj_cs CTAs each.
+int invert(thc_dyson* d, long long m0, long long count) {
+  if (count <= 0) return THC_OK;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)d->gj_cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(count * d->gj_cs), 1, 1);
+  cfg.blockDim = dim3(1024, 1, 1);
+  cfg.dynamicSmemBytes = gj_smem(d->n, d->gj_cs, d->gj_resident);
+  cfg.stream = d->stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, gj_cluster_kernel, d->n, (int)m0, d->gj_resident ? 1 : 0,
+                                           reinterpret_cast<double2*>(d->Giw));
+  return dcheck(d, e == cudaSuccess ? cudaGetLastError() : e, "Gauss-Jordan");
+}
+
+// G(i w_m) at chemical potential mu for every m (the positive half only when the
+// frequencies come in pairs); returns the electron count per spin.
 int dyson_at(thc_dyson* d, double mu, double* n_out) {
   const long long n = d->n, nn = n * n, nw = d->n_iw;
-  double* iw_d = d->scal + 8;  // frequencies live after 8 scalar slots
-  build_kernel<<<blocks_for(nn * nw), 256, 0, d->stream>>>((int)n, (int)nw, iw_d, mu, d->S, d->F, d->Siw, d->Giw);
+  const long long m0 = d->half ? nw / 2 : 0, cnt = nw - m0;
+  const double* iw_d = d->scal + 8 + m0;  // frequencies live after 8 scalar slots
+  build_kernel<<<blocks_for(nn * cnt), 256, 0, d->stream>>>((int)n, (int)cnt, iw_d, mu, d->S, d->F,
+                                                            d->Siw + 2 * m0 * nn, d->Giw + 2 * m0 * nn);
   THC_TRY(dcheck(d, cudaGetLastError(), "Dyson matrices"));
-  const size_t shm = 2 * sizeof(double2) * n;
-  gj_invert_kernel<<<(unsigned)(2 * nw), 1024, shm, d->stream>>>((int)n, reinterpret_cast<double2*>(d->Giw));
-  THC_TRY(dcheck(d, cudaGetLastError(), "Gauss-Jordan"));
-  trace_gs_kernel<<<(unsigned)nw, 256, 0, d->stream>>>((int)n, reinterpret_cast<const double2*>(d->Giw), d->S, d->tr);
+  THC_TRY(invert(d, m0, cnt));
+  trace_gs_kernel<<<(unsigned)cnt, 256, 0, d->stream>>>((int)n, reinterpret_cast<const double2*>(d->Giw) + m0 * nn,
+                                                        d->S, d->tr + 2 * m0);
   THC_TRY(dcheck(d, cudaGetLastError(), "Tr[G S]"));
   std::vector<double> t(2 * nw);
-  THC_TRY(dcheck(d, cudaMemcpyAsync(t.data(), d->tr, sizeof(double) * 2 * nw, cudaMemcpyDeviceToHost, d->stream),
+  THC_TRY(dcheck(d, cudaMemcpyAsync(t.data() + 2 * m0, d->tr + 2 * m0, sizeof(double) * 2 * cnt,
+                                    cudaMemcpyDeviceToHost, d->stream),
                  "copy traces"));
   THC_TRY(dcheck(d, cudaStreamSynchronize(d->stream), "Dyson sync"));
-  // Tr[gamma S] = -Re sum_m c_m t_m
+  // Tr[gamma S] = -Re sum_m c_m t_m, with t_{n_iw - 1 - m} = conj(t_m) for the mirrored half
   double acc = 0.0;
-  for (long long m = 0; m < nw; ++m) acc += d->cre[m] * t[2 * m] - d->cim[m] * t[2 * m + 1];
+  for (long long m = m0; m < nw; ++m) {
+    acc += d->cre[m] * t[2 * m] - d->cim[m] * t[2 * m + 1];
+    if (d->half) {
+      const long long mm = nw - 1 - m;
+      acc += d->cre[mm] * t[2 * m] + d->cim[mm] * t[2 * m + 1];
+    }
+  }
   *n_out = -acc;
   d->evals += 1;
   return THC_OK;
@@ -336,9 +512,15 @@ int thc_dyson_init(thc_dyson** out, int n_ao, int n_tau, int n_iw, int n_l, doub
   if (rc == THC_OK) rc = dalloc(d, &d->Giw, 2 * n2 * n_iw, "G(iw)");
   if (rc == THC_OK) rc = dalloc(d, &d->tr, 2 * (size_t)n_iw, "traces");
   if (rc == THC_OK) rc = dalloc(d, &d->scal, 8 + (size_t)n_iw, "scalars");
+  if (rc == THC_OK) rc = dalloc(d, &d->part, 2 * (size_t)kEnergyBlocks, "energy partial sums");
   if (rc == THC_OK)
     rc = dcheck(d, cudaMemcpyAsync(d->scal + 8, iw, sizeof(double) * n_iw, cudaMemcpyDefault, d->stream), "iw");
   if (rc == THC_OK) rc = dcheck(d, cudaStreamSynchronize(d->stream), "dyson init sync");
+  // frequencies in pairs (w_m = -w_{n_iw-1-m}, positive in the upper half): invert that half only
+  d->half = n_iw % 2 == 0;
+  for (int m = n_iw / 2; m < n_iw && d->half; ++m)
+    if (!(iw[m] > 0.0) || !(std::fabs(iw[m] + iw[n_iw - 1 - m]) <= 1e-12 * iw[m])) d->half = false;
+  if (rc == THC_OK) rc = choose_gj_cluster(d);
   if (rc != THC_OK) return bail(rc);
   *out = d;
   return THC_OK;
@@ -401,6 +583,11 @@ int thc_dyson_solve(thc_dyson* d, const double* Sigma_tau, double n_elec, double
   if (std::fabs(nm - n_elec) > 1e3 * tol)
     return dfail(d, THC_EINVAL, "thc_dyson_solve: chemical potential search did not converge");
   *mu = m;
+  if (d->half) {
+    mirror_conj_kernel<<<blocks_for(n2 * (nw / 2)), 256, 0, d->stream>>>(n2, (int)nw,
+                                                                        reinterpret_cast<double2*>(d->Giw));
+    THC_TRY(dcheck(d, cudaGetLastError(), "G(-i w)"));
+  }
   // g_l = Re[fit_iw G(iw)] ;  G(tau) = U_tau g
   THC_TRY(gemm<true, false>(d, L, n2, nw, View{d->fit_re, 0, nw, 1}, View{d->Giw, 0, 2 * n2, 2},
                             AccEpi{d->g_l, 0, n2, 1, 1.0, false}, "g_l re"));
@@ -423,11 +610,13 @@ int thc_dyson_energy(thc_dyson* d, const double* G_tau, const double* Sigma_tau,
                             AccEpi{d->sig_l, 0, n2, 1, 1.0, false}, "sigma_l"));
   // E_dyn = -int Tr[G(beta - tau) Sigma(tau)] = -sum_l p_l Tr[g_l sigma_l];  Tr[G(beta^-) F], Tr[G(beta^-) S]
   double h[4];
-  coef_contract_kernel<<<1, 1024, 0, d->stream>>>((int)d->n, (int)L, d->g_l, d->sig_l, d->parity_d, d->ubeta_d, d->F,
-                                                  d->scal);
+  coef_contract_kernel<<<kEnergyBlocks, 512, 0, d->stream>>>((int)d->n, (int)L, d->g_l, d->sig_l, d->parity_d,
+                                                            d->ubeta_d, d->F, d->part);
+  pair_sum_kernel<<<1, 32, 0, d->stream>>>(kEnergyBlocks, d->part, d->scal);
   THC_TRY(dcheck(d, cudaGetLastError(), "energy contraction"));
-  coef_contract_kernel<<<1, 1024, 0, d->stream>>>((int)d->n, (int)L, d->g_l, d->sig_l, d->parity_d, d->ubeta_d, d->S,
-                                                  d->scal + 2);
+  coef_contract_kernel<<<kEnergyBlocks, 512, 0, d->stream>>>((int)d->n, (int)L, d->g_l, d->sig_l, d->parity_d,
+                                                            d->ubeta_d, d->S, d->part);
+  pair_sum_kernel<<<1, 32, 0, d->stream>>>(kEnergyBlocks, d->part, d->scal + 2);
   THC_TRY(dcheck(d, cudaGetLastError(), "count contraction"));
   THC_TRY(dcheck(d, cudaMemcpyAsync(h, d->scal, sizeof(double) * 4, cudaMemcpyDeviceToHost, d->stream), "copy"));
   THC_TRY(dcheck(d, cudaStreamSynchronize(d->stream), "energy sync"));

@@ -3,7 +3,7 @@ against the FP64 oracle loop, through the C ABI (include/thc_dyson.h).
 
 Bars: G(tau) and mu of one Dyson step within 1e-9; energies of the same
 (G, Sigma) within 1e-12; converged loop energy within 1e-9 (FP64) and within
-1e-5 Ha (3 x BF16 self-energy) of the oracle loop.
+1e-5 Ha (3 x BF16 self-energy, loop stopped at |dE| < 1e-7) of the oracle loop.
 """
 import functools
 
@@ -67,6 +67,36 @@ def test_dyson_step_matches_oracle():
         thc.thc_dyson_destroy(d)
 
 
+@pytest.mark.parametrize("mirrored", [True, False])
+def test_dyson_inversions_with_and_without_mirrored_frequencies(mirrored):
+    """A 37-orbital Dyson step at the oracle's mu, on the IR grid (frequencies in pairs
+    w, -w: the GPU inverts half of them and conjugates) and on the same grid without
+    its first Matsubara point (no pairs: every frequency inverted)."""
+    import dataclasses
+    from paper_2404_17744_gb300 import thc
+    case = synth.make_sigma_case(37, 80, 4, 50.0, 43, identity_S=False, n_occ=11)
+    g = grid_for(50.0, 10.0)
+    if not mirrored:
+        U_iw = g.U_iw[1:]
+        g = dataclasses.replace(g, n=g.n[1:], iw=g.iw[1:], U_iw=U_iw, fit_iw=np.linalg.pinv(U_iw))
+    G0, mu0 = so.solve_dyson(g, case.S, case.F, None, 11.0, 0.0)
+    rng = np.random.default_rng(5)
+    nt = len(g.tau)
+    Sig = 0.05 * synth.random_symmetric(nt, case.n, rng) * np.exp(-np.linspace(0, 3, nt))[:, None, None]
+    G_ref, mu_ref = so.solve_dyson(g, case.S, case.F, Sig, 11.0, mu0)
+    d = _dyson(case, g)
+    try:
+        dev = torch.device("cuda:0")
+        Gd = torch.empty((nt, case.n, case.n), dtype=torch.float64, device=dev)
+        Sd = torch.from_numpy(Sig).to(dev)
+        assert thc.thc_dyson_solve(d, Sd, 11.0, mu_ref, 10.0, Gd) == mu_ref
+        err = np.abs(Gd.cpu().numpy() - G_ref).max()
+        print(f"mirrored={mirrored}: {len(g.iw)} frequencies, max|dG| = {err:.1e}")
+        assert err < 1e-10
+    finally:
+        thc.thc_dyson_destroy(d)
+
+
 def test_vector_utilities():
     from paper_2404_17744_gb300 import thc
     dev = torch.device("cuda:0")
@@ -116,7 +146,10 @@ def test_split_loop_reaches_fp64_energy():
     case = synth.make_sigma_case(20, 60, 4, 100.0, 17745, identity_S=False, n_occ=8)
     g = grid_for(100.0, 10.0)
     c1, r64 = _loop(case, g, 8.0, thc.THC_FP64, tol=1e-9)
-    c2, rsp = _loop(case, g, 8.0, thc.THC_BF16X3, tol=1e-9)
+    # the BF16 rounding of G makes the split Sigma map step-like at ~2^-17 relative, so its
+    # last iterates can cycle near 1e-8 Ha: the split loop stops at |dE| < 1e-7
+    c2, rsp = _loop(case, g, 8.0, thc.THC_BF16X3, tol=1e-7)
+    dE = [f"{abs(b.E - a.E):.1e}" for a, b in zip(rsp[:-1], rsp[1:])]
+    print(f"FP64 E {r64[-1].E:.10f} ({len(r64)} it), split E {rsp[-1].E:.10f} ({len(rsp)} it), |dE| {dE[-6:]}")
     assert c1 and c2
-    print(f"FP64 E {r64[-1].E:.10f} ({len(r64)} it), split E {rsp[-1].E:.10f} ({len(rsp)} it)")
     assert abs(r64[-1].E - rsp[-1].E) < 1e-5
