@@ -124,86 +124,99 @@ __global__ void build_kernel(int n, int n_iw, const double* __restrict__ iw, dou
 }
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// v - f r as four chained FMAs (the FP64 pipe is the bound of the elimination)
+__device__ __forceinline__ double2 cfms(double2 f, double2 r, double2 v) {
+  return make_double2(fma(f.y, r.y, fma(-f.x, r.x, v.x)), fma(-f.y, r.x, fma(-f.x, r.y, v.y)));
 }
 
 // In-place Gauss-Jordan inverse of matrix m0 + blockIdx.x / CS (n x n complex, no
 // pivoting), one cluster of CS CTAs per matrix; CTA rank c owns rows
 // [c h, min(n, (c + 1) h)), h = ceil(n / CS).  With resident != 0 a CTA keeps its
 // rows in shared memory from the first step to the last (when h n complex values
-// fit); otherwise they stay in global memory (L2).  Step k: the owner of row k
-// publishes the scaled row r_j = a_kj / a_kk (r_k = 1 / a_kk, computed once by
-// one thread: FP64 division is costly on this GPU) in one of two shared-memory
-// buffers; one cluster barrier; every CTA copies it from the owner's shared
-// memory (distributed shared memory), reads and clears column k of its own rows,
-// and updates them:
-//   a_ij -= a_ik r_j (i != k; column k becomes -a_ik / a_kk),  a_kj = r_j.
-// A CTA barrier orders its own writes before the next step reads them.
+// fit); otherwise they stay in global memory (L2).
+//
+// Step k uses the scaled pivot row r_j = a_kj / a_kk (r_k = 1 / a_kk), which every
+// CTA holds in one of two shared-memory row buffers: each CTA reads and clears
+// column k of its rows, then updates them,
+//   a_ij -= a_ik r_j (i != k; column k becomes -a_ik / a_kk),  a_kj = r_j,
+// and one cluster barrier ends the step.  Look-ahead: during step k the last warp
+// of the CTA that owns row k + 1 updates that row first, forms 1 / a_{k+1,k+1}
+// (one lane: FP64 division is costly on this GPU), and writes the scaled row into
+// the other row buffer of every CTA of the cluster (distributed shared memory),
+// while the other warps update the remaining rows.  The buffers alternate, so a
+// buffer is written only after every CTA has finished the step that read it.
 __global__ void __launch_bounds__(1024) gj_cluster_kernel(int n, int m0, int resident, double2* __restrict__ A0) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
   const int h = (n + CS - 1) / CS, r0 = rank * h, nr = max(0, min(n, r0 + h) - r0);
   extern __shared__ double2 sh[];
-  double2* pub = sh;           // [2][n] scaled pivot rows published by their owner
-  double2* rowk = sh + 2 * n;  // [n] this CTA's copy of the current one
-  double2* colk = rowk + n;    // [h] column k of this CTA's rows
+  double2* rowbuf = sh;          // [2][n] scaled pivot rows, written by their owner
+  double2* colk = sh + 2 * n;    // [h] column k of this CTA's rows
   double2* A = A0 + (long long)(m0 + blockIdx.x / CS) * n * n;
   double2* blk = A + (long long)r0 * n;  // this CTA's rows, row stride n
   const long long cnt = (long long)nr * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int la_warp = nwarp - 1;
   if (resident) {
     double2* s_rows = colk + h;
     for (long long e = threadIdx.x; e < cnt; e += blockDim.x) s_rows[e] = blk[e];
     blk = s_rows;
-    __syncthreads();
   }
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
-  for (int k = 0; k < n; ++k) {
-    const int owner = k / h;
-    double2* buf = pub + (k & 1) * n;
-    if (rank == owner) {  // uniform over the CTA
-      const double2* ak = blk + (long long)(k - r0) * n;
-      if (threadIdx.x == 0) {
-        const double2 p = ak[k];
-        const double inv = 1.0 / (p.x * p.x + p.y * p.y);
-        buf[k] = make_double2(p.x * inv, -p.y * inv);
-      }
-      __syncthreads();
-      const double2 ip = buf[k];
-      for (int j = threadIdx.x; j < n; j += blockDim.x)
-        if (j != k) buf[j] = cmul(ak[j], ip);
+  // one warp: scale row kk (held in src) by 1 / src[kk] into row buffer kk & 1 of every CTA
+  auto publish = [&](int kk, const double2* src) {
+    double px = 0.0, py = 0.0;
+    if (lane == 0) {
+      const double2 p = src[kk];
+      const double inv = 1.0 / (p.x * p.x + p.y * p.y);
+      px = p.x * inv;
+      py = -p.y * inv;
     }
-    // column k of the other rows: staged, then cleared (its update leaves -a_ik r_k)
+    const double2 ip = make_double2(__shfl_sync(0xffffffffu, px, 0), __shfl_sync(0xffffffffu, py, 0));
+    for (int j = lane; j < n; j += 32) {
+      const double2 v = (j == kk) ? ip : cmul(src[j], ip);
+      for (int c = 0; c < CS; ++c) cluster.map_shared_rank(rowbuf + (kk & 1) * n, c)[j] = v;
+    }
+  };
+  cluster.sync();  // every CTA of the cluster runs (and holds its rows) before remote writes
+  if (rank == 0 && warp == la_warp) publish(0, blk);
+  cluster.sync();
+  for (int k = 0; k < n; ++k) {
+    const double2* rowk = rowbuf + (k & 1) * n;
     for (int i = threadIdx.x; i < nr; i += blockDim.x) {
       colk[i] = blk[(long long)i * n + k];
       if (r0 + i != k) blk[(long long)i * n + k] = make_double2(0.0, 0.0);
     }
-    cluster.sync();  // row k is published; every CTA is past step k - 1
-    const double2* src = cluster.map_shared_rank(buf, owner);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) rowk[j] = src[j];
     __syncthreads();
-    for (int j = tx; j < n; j += 32) {
+    const int kn = k + 1, lin = kn - r0;
+    const bool la = kn < n && kn / h == rank;  // this CTA owns the next pivot row
+    if (la && warp == la_warp) {
+      double2* Ar = blk + (long long)lin * n;
+      const double2 f = colk[lin];
+      for (int j = lane; j < n; j += 32) Ar[j] = cfms(f, rowk[j], Ar[j]);
+      __syncwarp();
+      publish(kn, Ar);
+    }
+    for (int j = lane; j < n; j += 32) {
       const double2 r = rowk[j];
-      for (int li = ty; li < nr; li += nty) {
+      for (int li = warp; li < nr; li += nwarp) {
+        if (la && li == lin) continue;
         double2* a = blk + (long long)li * n + j;
         if (r0 + li == k) {
           *a = r;
         } else {
-          const double2 f = colk[li];
-          double2 v = *a;
-          v.x -= f.x * r.x - f.y * r.y;
-          v.y -= f.x * r.y + f.y * r.x;
-          *a = v;
+          *a = cfms(colk[li], r, *a);
         }
       }
     }
-    __syncthreads();
+    cluster.sync();  // step k done everywhere; row k + 1 published
   }
   if (resident) {
     double2* out = A + (long long)r0 * n;
     for (long long e = threadIdx.x; e < cnt; e += blockDim.x) out[e] = blk[e];
   }
-  cluster.sync();  // no CTA leaves while another may still read its published row
 }
 
 // G[m] = conj(G[n_iw - 1 - m]) for m < n_iw / 2.
@@ -330,11 +343,11 @@ int sigma_to_iw(thc_dyson* d, const double* Sig_tau) {
                            AccEpi{d->Siw + 1, 0, 2 * n2, 2, 1.0, false}, "Sigma(iw) im");
 }
 
-// Dynamic shared memory of gj_cluster_kernel: pivot-row buffers and column, plus the
+// Dynamic shared memory of gj_cluster_kernel: two pivot-row buffers and a column, plus the
 // CTA's rows when they are resident.
 size_t gj_smem(int n, int cs, bool resident) {
   const size_t h = (size_t)((n + cs - 1) / cs);
-  return sizeof(double2) * (3 * (size_t)n + h + (resident ? h * (size_t)n : 0));
+  return sizeof(double2) * (2 * (size_t)n + h + (resident ? h * (size_t)n : 0));
 }
 constexpr size_t kGjSmemMax = 232448;  // 227 KB per CTA
 
