@@ -12,6 +12,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace thc {
 namespace f64 {
 
@@ -160,13 +162,36 @@ struct StoreEpi {
   }
 };
 
+// Store epilogue of a contraction whose batch b needs only the columns c >= c0 + b
+// (the rest lies below the diagonal of a symmetric result): tiles wholly left of
+// that bound are not computed.
+struct TriStoreEpi {
+  double* p;
+  long long sb, sr, sc;
+  double alpha;
+  long long c0;
+  __device__ __forceinline__ void operator()(long long b, long long m, long long c, double v) const {
+    p[b * sb + m * sr + c * sc] = alpha * v;
+  }
+  __device__ __forceinline__ bool skip_tile(long long b, long long c_end) const { return c_end <= c0 + b; }
+};
+
+template <class E, class = void>
+struct HasSkipTile : std::false_type {};
+template <class E>
+struct HasSkipTile<E, std::void_t<decltype(&E::skip_tile)>> : std::true_type {};
+
 // Generic batched contraction: C(b) = epi(A(b) B(b)); grid (ceil(M/BM), ceil(Nn/BN), batch).
+// An epilogue with skip_tile(b, c_end) drops whole CTA tiles it does not need.
 template <bool AK, bool BK_, class LA, class LB, class Epi>
 __global__ void __launch_bounds__(NT) gemm_kernel(long long M, long long Nn, long long K, LA la, LB lb,
                                                   Epi epi) {
   __shared__ __align__(16) Tiles T;
   const long long b = blockIdx.z;
   const long long m0 = (long long)blockIdx.x * BM, n0 = (long long)blockIdx.y * BN;
+  if constexpr (HasSkipTile<Epi>::value) {
+    if (epi.skip_tile(b, n0 + BN)) return;
+  }
   const Lane L;
   double acc[4][4];
 #pragma unroll

@@ -41,7 +41,9 @@ int launch_gemm(thc_ctx* ctx, int kclass, long long M, long long Nn, long long K
 //   D_PR  = sum_v C_RvP B_PRv
 // CTA (x, y) owns R = y and 64 consecutive P of the block; it walks all v
 // tiles, multiplies each C tile by the matching B entries and reduces over v
-// in registers, so C is never stored.  Deterministic: no atomics.
+// in registers, so C is never stored.  Deterministic: no atomics.  D_PR is
+// symmetric for symmetric G(+-tau), so only P <= R is computed (CTAs whose P
+// all exceed R return at once) and the rest is mirrored afterwards.
 __global__ void __launch_bounds__(NT) sox_cd_kernel(int n, int N, int P0, int Pcnt, const double* __restrict__ U,
                                                      const double* __restrict__ Y, const double* __restrict__ Bblk,
                                                      double* __restrict__ D) {
@@ -49,6 +51,7 @@ __global__ void __launch_bounds__(NT) sox_cd_kernel(int n, int N, int P0, int Pc
   __shared__ double red[4][BN];
   const long long R = blockIdx.y;
   const long long p0 = (long long)blockIdx.x * BN;  // local P offset in the block
+  if (P0 + p0 > R) return;                          // every P of this CTA lies below the diagonal
   const f64::Lane L;
   // A(m = v, k = w) = U[R, v, w];  B(k = w, c = p) = Y[P0 + p, w]
   const View a{U + R * n * (long long)n, 0, n, 1};
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(NT) sox_cd_kernel(int n, int N, int P0, int Pc
   __syncthreads();
   if (threadIdx.x < BN) {
     const long long p = p0 + threadIdx.x;
-    if (p < Pcnt) {
+    if (p < Pcnt && P0 + p <= R) {
       const double s = (red[0][threadIdx.x] + red[1][threadIdx.x]) + (red[2][threadIdx.x] + red[3][threadIdx.x]);
       D[((long long)P0 + p) * N + R] = s;
     }
@@ -102,6 +105,25 @@ __global__ void polarisation_kernel(long long N, long long batch, const double* 
     const long long b = idx / NN, r = idx - b * NN;
     const long long i = r / N, j = r - i * N;
     Pi[idx] = GXp[idx] * GXm[b * NN + j * N + i];
+  }
+}
+
+// D[b][P][R] = D[b][R][P] for P > R: CTA (x, y, b) writes the lower 32 x 32 tile
+// (P tile y, R tile x <= y) from the upper one through shared memory.
+__global__ void mirror_upper_kernel(long long N, double* __restrict__ D) {
+  const long long tr = blockIdx.y, tcl = blockIdx.x;
+  if (tcl > tr) return;
+  __shared__ double t[32][33];
+  double* Db = D + (long long)blockIdx.z * N * N;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int i = ty; i < 32; i += blockDim.y) {  // t[i][x] = D[R = 32 tcl + i][P = 32 tr + x]
+    const long long R = tcl * 32 + i, P = tr * 32 + tx;
+    if (R < N && P < N) t[i][tx] = Db[R * N + P];
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += blockDim.y) {  // D[P = 32 tr + i][R = 32 tcl + x] = t[x][i]
+    const long long P = tr * 32 + i, R = tcl * 32 + tx;
+    if (P < N && R < N && P > R) Db[P * N + R] = t[tx][i];
   }
 }
 
@@ -219,17 +241,28 @@ int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Si
           THC_TRY(launch_gemm<false, true>(ctx, K_SOX_A, n, Pc * n, n, 1, View{Gb, 0, 1, n},
                                            View{ctx->U + P0 * nn, 0, 1, n},
                                            f64::StoreEpi{ctx->Ablk, 0, 1, n, -1.0}, "A"));
-          // B_PRv = sum_q A_Pqv G_Rq (batched over P): (m = v, c = R), A(v, q) = A[P, q, v], B(q, R) = Y[R, q]
-          THC_TRY(launch_gemm<false, true>(ctx, K_SOX_B, n, N, n, Pc, View{ctx->Ablk, nn, 1, n}, View{Yk, 0, 1, n},
-                                           f64::StoreEpi{ctx->Bblk, Nn, 1, n, 1.0}, "B"));
-          // C and D fused
+          // B_PRv = sum_q A_Pqv G_Rq (batched over P): (m = v, c = R), A(v, q) = A[P, q, v], B(q, R) = Y[R, q];
+          // only R >= P is used (D is symmetric): column tiles wholly left of P are skipped
+          double bflops = 0.0, cdflops = 0.0;  // multiply-adds the kernels carry out, x 2
+          for (long long b = 0; b < Pc; ++b) bflops += 2.0 * n * n * (N - (P0 + b) / BN * BN);
+          for (long long p0 = 0; p0 < Pc; p0 += BN)
+            if (P0 + p0 < N) cdflops += (2.0 * nn + 2.0 * n) * std::min<long long>(BN, Pc - p0) * (N - (P0 + p0));
+          {
+            ProfRec rec;
+            THC_TRY(prof_begin(ctx, K_SOX_B, bflops, &rec));
+            f64::gemm_kernel<false, true><<<grid_for(n, N, Pc), NT, 0, ctx->stream>>>(
+                n, N, n, View{ctx->Ablk, nn, 1, n}, View{Yk, 0, 1, n}, f64::TriStoreEpi{ctx->Bblk, Nn, 1, n, 1.0, P0});
+            THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "B"));
+          }
+          // C and D fused, P <= R
           ProfRec rec;
-          THC_TRY(prof_begin(ctx, K_SOX_CD, 2.0 * Pc * N * nn + 2.0 * Pc * N * n, &rec));
+          THC_TRY(prof_begin(ctx, K_SOX_CD, cdflops, &rec));
           sox_cd_kernel<<<dim3((unsigned)((Pc + BN - 1) / BN), (unsigned)N), NT, 0, ctx->stream>>>(
               (int)n, (int)N, (int)P0, (int)Pc, ctx->U, Yk, ctx->Bblk, Dk);
           THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "C/D"));
         }
       }
+      THC_TRY(launch_mirror_upper(ctx, ctx->D, N, tc));
     }
     // M = C_SOX D^T + C_DIRECT G^X o (V Pi V)
     const double* Mbuf;
@@ -277,6 +310,13 @@ int energy_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const do
   THC_TRY(check_cuda(ctx, cudaMemcpyAsync(E, ctx->e_out, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
                      "copy energy"));
   return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "energy sync");
+}
+
+int launch_mirror_upper(thc_ctx* ctx, double* D, long long N, long long batch) {
+  if (N <= 1 || batch <= 0) return THC_OK;
+  const unsigned t = (unsigned)((N + 31) / 32);
+  mirror_upper_kernel<<<dim3(t, t, (unsigned)batch), dim3(32, 8, 1), 0, ctx->stream>>>(N, D);
+  return check_cuda(ctx, cudaGetLastError(), "mirror D");
 }
 
 }  // namespace thc

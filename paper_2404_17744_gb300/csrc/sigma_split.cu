@@ -420,7 +420,8 @@ Split split_of(bf16* hi, bf16* lo, long long rows, long long ld, long long batch
 }
 
 // Fused B and C/D of one tau point and P block (tc::sox_bcd_kernel):
-//   D[P0 + P][R] += sum_v (sum_w Y[P0 + P][w] U[R][v][w]) (sum_q A^T[P][v][q] Y[R][q]).
+//   D[P0 + P][R] += sum_v (sum_w Y[P0 + P][w] U[R][v][w]) (sum_q A^T[P][v][q] Y[R][q])
+// for P0 + P <= R only (D is symmetric; the caller mirrors it).
 // Y: N x ldn rows of the tau point; U: [R][v][w]; At: [P][v][q] with Pc blocks of P.
 // CP x CR is the cluster shape (operand slices multicast within it).
 template <int CP, int CR>
@@ -469,8 +470,17 @@ int launch_bcd_shape(thc_ctx* ctx, const Split& Y, const Split& U, const Split& 
     max_clusters = mc;
   }
   // v chunks per cluster tile: fewest v steps on the busiest SM, one more per unit for its flush
+  // cluster tiles that reach R >= P (the kernel's enumeration) and the (P, R) pairs they cover
   const long long tm = (Pc + tc::BM - 1) / tc::BM, tn = (N + tc::BM - 1) / tc::BM;
-  const long long ctiles = ((tm + CP - 1) / CP) * ((tn + CR - 1) / CR);
+  const long long tm2 = (tm + CP - 1) / CP, tn2 = (tn + CR - 1) / CR, hp = CP * tc::BM, wr = CR * tc::BM;
+  long long ctiles = 0;
+  double pairs = 0.0;
+  for (long long i = 0; i < tm2; ++i) {
+    const long long c0 = (P0 + i * hp) / wr, rows = std::min(Pc, (i + 1) * hp) - i * hp;
+    if (c0 >= tn2) continue;
+    ctiles += tn2 - c0;
+    pairs += (double)rows * (double)(N - c0 * wr);
+  }
   int nvc = 1;
   long long best = -1;
   for (long long c = 1; c <= std::min<long long>(n, 64); ++c) {
@@ -494,7 +504,7 @@ int launch_bcd_shape(thc_ctx* ctx, const Split& Y, const Split& U, const Split& 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   ProfRec rec;
-  THC_TRY(prof_begin(ctx, K_SOX_BCD, 2.0 * 2.0 * Pc * N * n * n, &rec));
+  THC_TRY(prof_begin(ctx, K_SOX_BCD, 2.0 * 2.0 * pairs * n * n, &rec));  // the tiles computed
   const cudaError_t e =
       cudaLaunchKernelEx(&cfg, kern, mh, ml, tc::BcdArgs{(int)Pc, (int)P0, (int)N, (int)n, nvc, D}, ctx->d_err);
   return prof_end(ctx, &rec, e == cudaSuccess ? cudaGetLastError() : e, "B C/D");
@@ -655,6 +665,7 @@ int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* S
           THC_TRY(launch_bcd(ctx, Yk, U, At, P0, Pc, Dk));
         }
       }
+      THC_TRY(launch_mirror_upper(ctx, ctx->Dd, N, tc));  // D_PR = D_RP: fill P > R
     }
     // merged M, back-transform
     if (dir) {

@@ -16,7 +16,10 @@
 //
 // Work units are (P tile, R tile, v chunk); the v range of a (P, R) tile is cut
 // into chunks so that the units fill the SMs in whole waves, and every unit adds
-// its FP32 partial tile of D into the FP64 D with one atomic per element.  Units
+// its FP32 partial tile of D into the FP64 D with one atomic per element.  D_PR is
+// symmetric for symmetric G(+-tau) (rename w <-> q, v <-> s and use U_Pqs = U_Psq),
+// so only tiles that reach R >= P are computed, only P <= R is added, and the
+// caller mirrors the rest.  Units
 // are numbered with the v chunk slowest, so the CTAs of a wave walk the same few
 // values of v together and the U_v and A^T_v slices they read are served from
 // L2.  A persistent cluster takes units c, c + clusters, ...
@@ -130,13 +133,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int nkb = (a.n + BKE - 1) / BKE;
   const int tm = (a.Pc + BM - 1) / BM, tn = (a.N + BM - 1) / BM;
   const int tm2 = (tm + CP - 1) / CP, tn2 = (tn + CR - 1) / CR;
-  const long long ctiles = (long long)tm2 * tn2, units = ctiles * a.nvc;
+  // D is symmetric: only cluster tiles that reach R >= P are computed.  Cluster row i
+  // (P from P0 + i CP 128) starts at cluster column first_col(i); ctiles counts them.
+  auto first_col = [&](int i) { return (int)((a.P0 + (long long)i * CP * BM) / ((long long)CR * BM)); };
+  long long ctiles = 0;
+  for (int i = 0; i < tm2; ++i) ctiles += max(0, tn2 - first_col(i));
+  const long long units = ctiles * a.nvc;
   const long long cl = blockIdx.x / CS, ncl = gridDim.x / CS;
-  // unit u of a cluster: v chunk u / ctiles (slowest), then P fastest
+  // unit u of a cluster: v chunk u / ctiles (slowest), then the upper cluster tiles row by row
   auto decode = [&](long long u, int& pt, int& rt, int& v0, int& v1) {
-    const long long vc = u / ctiles, t = u - vc * ctiles;
-    pt = (int)(t % tm2) * CP + pi;
-    rt = (int)(t / tm2) * CR + rj;
+    const long long vc = u / ctiles;
+    long long t = u - vc * ctiles;
+    int i = 0;
+    for (; i < tm2; ++i) {
+      const int c = max(0, tn2 - first_col(i));
+      if (t < c) break;
+      t -= c;
+    }
+    pt = i * CP + pi;
+    rt = (first_col(i) + (int)t) * CR + rj;
     v0 = (int)(vc * a.n / a.nvc);
     v1 = (int)((vc + 1) * a.n / a.nvc);
   };
@@ -323,8 +338,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int i = 0; i < 32; ++i) tile(lane, i) = acc[c + i];
         __syncwarp();
         const int R = rt * BM + half * 64 + c + lane;
-        if (R < a.N) {
-          for (int r = 0; r < 32 && prow + r < a.Pc; ++r)
+        if (R < a.N) {  // the upper triangle only: P0 + P <= R
+          for (int r = 0; r < 32 && prow + r < a.Pc && a.P0 + prow + r <= R; ++r)
             atomicAdd(&a.D[(long long)(a.P0 + prow + r) * a.N + R], (double)tile(r, lane));
         }
         __syncwarp();

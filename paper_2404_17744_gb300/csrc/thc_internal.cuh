@@ -117,6 +117,8 @@ void prof_release(thc_ctx* ctx);
 size_t fp64_workspace_bytes(int n, int N, int tc, int Pb);
 int fp64_build_U(thc_ctx* ctx);
 int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma);
+// D[b][P][R] = D[b][R][P] for P > R, b < batch (D_PR is symmetric; both paths compute P <= R)
+int launch_mirror_upper(thc_ctx* ctx, double* D, long long N, long long batch);
 int energy_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const double* Sigma,
                 const double* w_host, double* E);
 

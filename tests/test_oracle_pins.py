@@ -137,6 +137,24 @@ def test_symmetry_and_V_scaling():
     np.testing.assert_allclose(S2, 1.7 ** 2 * S1, rtol=1e-12, atol=1e-15)
 
 
+@pytest.mark.parametrize("seed", [3, 4])
+def test_sox_intermediate_D_is_symmetric(seed):
+    """D_PR = sum_{v w q s} G_Pw U_Rvw G_Rq U_Pqs G_vs(-tau) is symmetric in (P, R) when
+    G(tau) and G(-tau) are (rename w <-> q, v <-> s and use U_Pqs = U_Psq); the GPU paths
+    compute D on and above the diagonal only and mirror it.  A non-symmetric G breaks it."""
+    case = synth.make_sigma_case(11, 37, 4, 30.0, seed, identity_S=False, n_occ=4)
+    U = o.thc_U(case.X, case.V)
+    for k in range(case.n_tau):
+        G, Gm = case.G_tau[k], o.g_minus_tau(case.G_bmt[k])
+        _, it = o.sigma_sox_thc(case.X, U, G, Gm, return_intermediates=True)
+        D = it["D"]
+        assert np.abs(D - D.T).max() <= 1e-12 * np.abs(D).max()
+    rng = np.random.default_rng(seed)
+    Gn = G + 0.1 * np.abs(G).max() * rng.standard_normal(G.shape)
+    _, it = o.sigma_sox_thc(case.X, U, Gn, Gm, return_intermediates=True)
+    assert np.abs(it["D"] - it["D"].T).max() > 1e-6 * np.abs(it["D"]).max()
+
+
 def test_fragment_separability():
     """Two non-interacting fragments (appendix): block-diagonal Sigma, additive E_dyn."""
     beta = 15.0
