@@ -36,11 +36,11 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes (read + write) per launch from an ncu capture of the kernel as it
 # stands, keyed by (kernel class, workload); profiles/ holds the capture summary.
 NCU_TRAFFIC = {
-    ("sox_CD", "thc200"): (1.927304e9 + 0.011961e9, "profiles/sox_cd_kernel_thc200s.md (same per-launch shape)"),
-    ("sox_CD", "thc200s"): (1.927304e9 + 0.011961e9, "profiles/sox_cd_kernel_thc200s.md"),
-    ("sox_BCD", "thc200:bf16x3"): (0.397607e9 + 0.019301e9,
+    ("sox_B", "thc200"): (0.324722e9 + 0.820432e9, "profiles/sox_b_gemm_kernel_thc200s.md (same per-launch shape)"),
+    ("sox_B", "thc200s"): (0.324722e9 + 0.820432e9, "profiles/sox_b_gemm_kernel_thc200s.md"),
+    ("sox_BCD", "thc200:bf16x3"): (0.344487e9 + 0.007276e9,
                                    "profiles/sox_bcd_kernel_thc200s.md (same per-launch shape)"),
-    ("sox_BCD", "thc200s:bf16x3"): (0.397607e9 + 0.019301e9, "profiles/sox_bcd_kernel_thc200s.md"),
+    ("sox_BCD", "thc200s:bf16x3"): (0.344487e9 + 0.007276e9, "profiles/sox_bcd_kernel_thc200s.md"),
 }
 
 
