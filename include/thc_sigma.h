@@ -169,6 +169,10 @@ int thc_set_stream(thc_ctx *ctx, void *stream);
  * thc_sigma_eval on ctx (contractions of the scheme only, 2 per multiply-add):
  *   n_tau (2 N n^3 + 4 N^2 n^2 + 4 N^3 + 8 N^2 n + 6 N n^2)  for both terms;
  * and of the one-off U build, 2 N^2 n^2 (returned through u_flops if non-NULL).
+ * This is the scheme's count, the unit of work of one evaluation.  The library
+ * forms the symmetric SOX intermediate D_PR on one side of its diagonal only, so
+ * its kernels carry out fewer flops (about 2 N^2 n^2 fewer per tau point); the
+ * profiler below reports those.
  */
 double thc_sigma_flops(const thc_ctx *ctx, double *u_flops);
 
@@ -184,7 +188,9 @@ int thc_profile(thc_ctx *ctx, int enable);
  * thc_profile_get -- totals of kernel class kclass (0 <= kclass < number of
  * classes; THC_EINVAL past the last) since the last thc_profile(ctx, 1):
  * its name, number of launches, summed device time in ms and summed
- * algorithmic flops of those launches.  Any out-pointer may be NULL.
+ * flops those launches carried out (2 per multiply-add; for sox_B, sox_CD and
+ * sox_BCD only the part of the (P, R) square they compute).  Any out-pointer
+ * may be NULL.
  * Synchronises the stream.  Class names: u_build, project, sox_A, sox_B,
  * sox_CD, polarisation, direct_VPi, direct_W, back_transform, energy, split,
  * sox_BCD (sox_B and sox_CD are the FP64 path's; the split path runs both
