@@ -166,13 +166,13 @@ int thc_set_stream(thc_ctx *ctx, void *stream);
 
 /*
  * thc_sigma_flops -- algorithmic FP64-equivalent flop count of one
- * thc_sigma_eval on ctx (contractions of the scheme only, 2 per multiply-add):
- *   n_tau (2 N n^3 + 4 N^2 n^2 + 4 N^3 + 8 N^2 n + 6 N n^2)  for both terms;
+ * thc_sigma_eval on ctx (contractions only, 2 per multiply-add), for both terms:
+ *   n_tau (2 N n^3 + 2 N (N + 1) n^2 + 4 N^3 + 6 N^2 n + N (N + 1) n + 6 N n^2),
  * and of the one-off U build, 2 N^2 n^2 (returned through u_flops if non-NULL).
- * This is the scheme's count, the unit of work of one evaluation.  The library
- * forms the symmetric SOX intermediate D_PR on one side of its diagonal only, so
- * its kernels carry out fewer flops (about 2 N^2 n^2 fewer per tau point); the
- * profiler below reports those.
+ * The SOX intermediate D_PR is symmetric, so B, C and D are counted over the
+ * N (N + 1) / 2 pairs P <= R that the library forms (the paper's scheme over all
+ * (P, R) pairs would be 2 N^2 n^2 + N^2 n more per tau point).  The profiler below
+ * reports what the kernels carry out, whole tiles included.
  */
 double thc_sigma_flops(const thc_ctx *ctx, double *u_flops);
 

@@ -265,7 +265,8 @@ double thc_sigma_flops(const thc_ctx* ctx, double* u_flops) {
   if (!ctx) return 0.0;
   const double n = ctx->n, N = ctx->N, nt = ctx->n_tau;
   double f = 4.0 * N * n * n + 2.0 * N * N * n;  // Y, M X^T, X T2
-  if (ctx->terms & THC_SOX) f += 2.0 * N * n * n * n + 4.0 * N * N * n * n + 2.0 * N * N * n;
+  // SOX: A for all P, then B and C/D for the N (N + 1) / 2 pairs P <= R (D_PR is symmetric)
+  if (ctx->terms & THC_SOX) f += 2.0 * N * n * n * n + 2.0 * N * (N + 1) * n * n + N * (N + 1) * n;
   if (ctx->terms & THC_DIRECT) f += 2.0 * N * n * n + 4.0 * N * N * n + 4.0 * N * N * N;
   if (u_flops) *u_flops = (ctx->terms & THC_SOX) ? 2.0 * N * N * n * n : 0.0;
   return nt * f;
