@@ -91,8 +91,11 @@ def test_split_single_terms(terms, name):
     _check(synth.make_sigma_case(21, 75, 4, 40.0, 9, n_occ=8), terms, name)
 
 
-def test_split_small_workspace(monkeypatch):
-    monkeypatch.setenv("THC_WORKSPACE_BYTES", str(2_000_000))
+@pytest.mark.parametrize("budget", [2_000_000, 300_000])
+def test_split_small_workspace(monkeypatch, budget):
+    # 300 kB gives P blocks of 23 THC points: the fused B C/D kernel then starts its blocks
+    # at P0 that are not multiples of its 128-row tiles, and D's upper triangle crosses them
+    monkeypatch.setenv("THC_WORKSPACE_BYTES", str(budget))
     _check(synth.make_sigma_case(40, 150, 5, 30.0, 17))
 
 
