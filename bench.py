@@ -9,10 +9,11 @@ once in thc_sigma_init, outside the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank runs an independent replica of the
-workload (the path has no exchange step), the timed region is bracketed by
-barriers, and the MAX time over ranks is used.  --impl reference times the
-FP64 CPU oracle on a bounded sample of the same workload on the host cores.
+The method runs on one GPU.  Under torchrun with WORLD_SIZE > 1 the GPU arm
+launches nothing: rank 0 prints one line with "unavailable" and every rank
+exits 0 (the fused B C/D kernel multicasts TMA loads inside a CTA pair, which
+only single-GPU runs may use).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload on the host cores (rank 0 only).
 """
 from __future__ import annotations
 
@@ -64,21 +65,9 @@ def dist_env():
     return rank, world, local
 
 
-def max_over_ranks(value: float, world: int, device=None) -> float:
-    """Maximum of `value` over the ranks of the default process group (the slowest rank
-    defines the job's time); the identity for a single process."""
-    if world <= 1:
-        return float(value)
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def job_throughput(world: int, flops_per_step: float, steps: int, max_seconds: float) -> float:
-    """Whole-job TFLOP/s: every rank runs a replica of the workload (weak scaling)."""
-    return world * flops_per_step * steps / max_seconds / 1e12
+def job_throughput(flops_per_step: float, steps: int, seconds: float) -> float:
+    """TFLOP/s of `steps` steps of `flops_per_step` each in `seconds`."""
+    return flops_per_step * steps / seconds / 1e12
 
 
 def algorithmic_flops(n, N, n_tau):
@@ -233,7 +222,7 @@ def read_profile(thc, ctx):
     return kernels
 
 
-def measure(args, case, precision, world, dev, stream, X, V, G, S, flush, sampler_on):
+def measure(args, case, precision, dev, stream, X, V, G, S, flush, sampler_on):
     """Times args.steps Sigma evaluations (+ energy) of one precision mode on `stream`."""
     import torch
     from paper_2404_17744_gb300 import thc
@@ -248,8 +237,6 @@ def measure(args, case, precision, world, dev, stream, X, V, G, S, flush, sample
     for _ in range(args.warmup):
         step()
     stream.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device()) if sampler_on else None
     thc.thc_profile(ctx, True)
@@ -262,14 +249,12 @@ def measure(args, case, precision, world, dev, stream, X, V, G, S, flush, sample
         e1.record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
     launches = thc.thc_launch_count(ctx) - launches0
     clocks = sampler.stop() if sampler else None
     thc.thc_sync(ctx)
     kernels = read_profile(thc, ctx)
     thc.thc_profile(ctx, False)
-    total_ms = max_over_ranks(float(sum(e0.elapsed_time(e1) for e0, e1 in evs)), world, dev)
+    total_ms = float(sum(e0.elapsed_time(e1) for e0, e1 in evs))
     return ctx, dict(total_ms=total_ms, kernels=kernels, launches=launches, clocks=clocks,
                      energy=energies[-1] if energies else None)
 
@@ -362,11 +347,10 @@ def run_ours(args):
     from workloads import synth
 
     rank, world, local = dist_env()
+    if world > 1:
+        return single_gpu_only(args, rank, world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     case = synth.make_workload(args.workload)
     stream = torch.cuda.Stream(device=dev)
     flops_step = algorithmic_flops(case.n, case.N, case.n_tau)
@@ -381,33 +365,31 @@ def run_ours(args):
         stream.synchronize()
 
         # ---- plain FP64 path (the headline workload)
-        ctx, r64 = measure(args, case, thc.THC_FP64, world, dev, stream, X, V, G, S, flush, rank == 0)
+        ctx, r64 = measure(args, case, thc.THC_FP64, dev, stream, X, V, G, S, flush, rank == 0)
         lib_flops, u_flops = thc.thc_sigma_flops(ctx)
         assert abs(lib_flops - flops_step) < 1e-6 * flops_step
-        value = job_throughput(world, flops_step, args.steps, r64["total_ms"] * 1e-3)
+        value = job_throughput(flops_step, args.steps, r64["total_ms"] * 1e-3)
 
         # end to end through the host-buffer entry point (H2D of G, D2H of Sigma inside)
         Gh = torch.from_numpy(case.G_tau).pin_memory()
         Sh = torch.empty_like(Gh).pin_memory()
         thc.thc_sigma_eval_host(ctx, Gh, None, Sh)
-        if world > 1:
-            torch.distributed.barrier()
         t0 = time.perf_counter()
         e2e_steps = max(1, min(args.steps, 2))
         for _ in range(e2e_steps):
             thc.thc_sigma_eval_host(ctx, Gh, None, Sh)
-        e2e_dt = max_over_ranks(time.perf_counter() - t0, world, dev)
-        e2e_value = job_throughput(world, flops_step, e2e_steps, e2e_dt)
+        e2e_dt = time.perf_counter() - t0
+        e2e_value = job_throughput(flops_step, e2e_steps, e2e_dt)
         thc.thc_destroy(ctx)
 
         # ---- mixed precision (3 x BF16 on tcgen05), same input; error against the FP64 result
         split = None
         if not args.no_split:
-            ctx, rsp = measure(args, case, thc.THC_BF16X3, world, dev, stream, X, V, G, S_split, flush, False)
+            ctx, rsp = measure(args, case, thc.THC_BF16X3, dev, stream, X, V, G, S_split, flush, False)
             thc.thc_destroy(ctx)
             stream.synchronize()
             split = rsp
-            split["value"] = job_throughput(world, flops_step, args.steps, rsp["total_ms"] * 1e-3)
+            split["value"] = job_throughput(flops_step, args.steps, rsp["total_ms"] * 1e-3)
             split["max_abs_dsigma_vs_fp64"] = float((S_split - S).abs().max().item())
             split["abs_dE_vs_fp64"] = abs(rsp["energy"] - r64["energy"])
 
@@ -470,9 +452,9 @@ def run_ours(args):
                             "and C/D over the N(N+1)/2 pairs P <= R (D_PR is symmetric and is mirrored); "
                             "executed_tflops counts what the kernels carry out, whole tiles included",
                    "executed_tflops": executed_flops(r64["kernels"]) / (r64["total_ms"] * 1e-3) / 1e12,
-                   "fp64_frac_of_peak": value / world / FP64_PEAK_TFLOPS,
+                   "fp64_frac_of_peak": value / FP64_PEAK_TFLOPS,
                    "l2": "flushed between timed steps (258 MiB write); U_Pqs exceeds L2",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "E_dyn": r64["energy"]},
+                   "parallelism": "single GPU", "E_dyn": r64["energy"]},
         "roofline": roofline,
         "gpu_launches": int(r64["launches"]),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Gh.numel() * 8),
@@ -500,7 +482,7 @@ def run_ours(args):
         line["scgf2_loop"] = loop
         line["config"]["s_per_scgf2_iteration_fp64"] = loop["fp64"]["s_per_iteration"]
         line["config"]["s_per_scgf2_iteration_bf16x3"] = loop["bf16x3"]["s_per_iteration"]
-    if world == 1 and not args.no_cpu_baseline:
+    if not args.no_cpu_baseline:
         v, pts, secs = oracle_sample(case)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                                 "sample": f"{pts} tau points of the workload (full Sigma(tau_k) each), "
@@ -515,19 +497,32 @@ def run_batch64(args):
     from paper_2404_17744_gb300 import thc
     from workloads import batch as wb
     rank, world, local = dist_env()
+    if world > 1:
+        return single_gpu_only(args, rank, world)
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     cases = wb.make_batch(64, 50, 400, 100, 100.0, seed=17747)
     r = batch_measure(cases, thc.THC_BF16X3, args.steps, args.warmup, stream)
-    line = {"metric": METRIC, "value": r["value"] * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["s_per_batch_eval"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
             "config": {"workload": "batch64: 64 molecules, n_ao uniform in [50, 400], n_thc = 5 n_ao, 100 "
                                    "Gauss-Legendre tau points, beta = 100; 3xBF16 tensor cores; one CUDA-graph "
                                    "launch per evaluation over 4 worker streams; tile widths from the autotuner"},
             "gpu_launches": r["graph_kernels"] * args.steps, "batched": r}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def single_gpu_only(args, rank, world):
+    """Multi-process launch of the GPU arm: nothing runs on any GPU; rank 0 reports why."""
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps({"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                          "unavailable": "single-GPU method: one GPU evaluates every tau point, and the fused "
+                                         "B C/D kernel's CTA pairs multicast TMA loads, which only a 1-GPU "
+                                         "run may use; no multi-GPU path is built (replicas only, not run)"}),
+              flush=True)
     return 0
 
 

@@ -46,7 +46,8 @@ extern "C" {
 
 /* return codes */
 #define THC_OK        0
-#define THC_EINVAL   -1   /* bad sizes, NULL pointers, non-mirrored grid without G_bmt */
+#define THC_EINVAL   -1   /* bad sizes, NULL pointers, non-mirrored grid without G_bmt,
+                             a NaN or infinite input value */
 #define THC_ENOMEM   -2   /* device allocation failed */
 #define THC_ECUDA    -3   /* a CUDA runtime call or kernel launch failed */
 #define THC_ETIMEOUT -4   /* a bounded device-side wait ran out */
@@ -57,6 +58,10 @@ extern "C" {
 #define THC_BF16X3   1    /* projections and V contractions as 3 BF16 products
                              (hi*hi + hi*lo + lo*hi) on tcgen05 tensor cores with
                              FP32 accumulation; inputs and outputs stay FP64 */
+#define THC_TF32     2    /* not built: thc_sigma_init returns THC_ENOTSUP.  One TF32
+                             product keeps 11 significant bits, too few for the 1e-6 Ha
+                             bound on Sigma; three TF32 products meet it at half the
+                             BF16 tensor rate, so THC_BF16X3 is the reduced-precision mode */
 
 /* terms (bit mask) */
 #define THC_DIRECT   1
@@ -78,9 +83,10 @@ typedef struct thc_ctx thc_ctx;   /* opaque, library-owned */
  *   tau       host, n_tau ascending points in (0, beta) (copied); if the grid
  *             is mirror-symmetric (|tau_k + tau_{n_tau-1-k} - beta| <= 1e-10 beta
  *             for all k) G(beta - tau_k) is read from G_tau itself
- *   precision THC_FP64 or THC_BF16X3
+ *   precision THC_FP64 or THC_BF16X3 (THC_TF32: THC_ENOTSUP)
  *   terms     THC_DIRECT | THC_SOX (non-zero)
  *   stream    cudaStream_t the context launches on (NULL: legacy default stream)
+ * X and V are scanned on the device: a NaN or infinite value gives THC_EINVAL.
  * Device memory held: U (N n^2 doubles) plus a workspace sized at init from
  * the free device memory (at most a quarter of it, or THC_WORKSPACE_BYTES
  * from the environment when set).
@@ -96,7 +102,10 @@ int thc_sigma_init(thc_ctx **ctx, int n_ao, int n_thc, int n_tau, double beta,
  *              mirror-symmetric (then G(beta - tau_k) = G_tau[n_tau-1-k])
  *   Sigma_tau  dev, n_tau x n x n, overwritten with Sigma(tau_k); must not
  *              alias G_tau or G_bmt
- * THC_EINVAL if G_bmt is NULL and the grid is not mirror-symmetric.
+ * THC_EINVAL if G_bmt is NULL and the grid is not mirror-symmetric.  The call
+ * stays asynchronous, so G is scanned for NaN and infinite values on the
+ * stream and a hit is reported as THC_EINVAL by the next call that
+ * synchronises (thc_sync, thc_energy, thc_sigma_eval_host, thc_sigma_tune).
  */
 int thc_sigma_eval(thc_ctx *ctx, const double *G_tau, const double *G_bmt, double *Sigma_tau);
 
@@ -124,8 +133,9 @@ int thc_energy(thc_ctx *ctx, const double *G_tau, const double *G_bmt,
                const double *Sigma_tau, const double *tau_weights, double *E_dyn);
 
 /*
- * thc_sync -- wait for the work queued on ctx's stream and report a
- * tensor-core pipeline wait that ran out (THC_ETIMEOUT) during it.
+ * thc_sync -- wait for the work queued on ctx's stream and report what it met:
+ * a tensor-core pipeline wait that ran out (THC_ETIMEOUT) or a NaN or infinite
+ * value in an evaluation's G (THC_EINVAL).  Both reports are cleared.
  */
 int thc_sync(thc_ctx *ctx);
 
@@ -193,8 +203,8 @@ int thc_profile(thc_ctx *ctx, int enable);
  * may be NULL.
  * Synchronises the stream.  Class names: u_build, project, sox_A, sox_B,
  * sox_CD, polarisation, direct_VPi, direct_W, back_transform, energy, split,
- * sox_BCD (sox_B and sox_CD are the FP64 path's; the split path runs both
- * contractions as the one fused sox_BCD kernel).
+ * sox_BCD, check (sox_B and sox_CD are the FP64 path's; the split path runs both
+ * contractions as the one fused sox_BCD kernel; check is the non-finite input scan).
  */
 int thc_profile_get(thc_ctx *ctx, int kclass, const char **name, long long *launches,
                     double *ms, double *flops);
@@ -227,6 +237,22 @@ long long thc_launch_count(const thc_ctx *ctx);
 int thc_energy_static(int n_ao, int n_tau, const double *G_tau, const double *G_bmt,
                       const double *Sigma_tau, const double *tau_weights, double *E_dyn,
                       void *stream);
+
+/*
+ * thc_wait_selftest -- exercises the failure path of the bounded device-side
+ * waits (the paper has no counterpart: this checks the library's own error
+ * handling).  One CTA holds TMEM and a bulk copy in flight, waits limit_ns on
+ * an mbarrier that nothing ever completes, then unwinds as the tensor-core
+ * kernels do after a timeout: it waits (bounded) for its copy and its
+ * tensor-core operations, frees TMEM and returns.
+ *   limit_ns  the wait's limit, 1e3 .. 1e9 ns (THC_EINVAL otherwise)
+ *   stream    cudaStream_t (NULL: legacy default stream); synchronised
+ * Returns THC_ETIMEOUT when the wait ran out and the unwind completed (the
+ * expected result), THC_ECUDA if the unwind itself did not complete in time.
+ * Allocates and frees 2 KB of device memory.  Failures are described by
+ * thc_last_error(NULL).
+ */
+int thc_wait_selftest(long long limit_ns, void *stream);
 
 /* thc_destroy -- free everything ctx owns (NULL is a no-op).  Synchronises. */
 void thc_destroy(thc_ctx *ctx);

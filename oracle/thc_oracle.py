@@ -114,6 +114,28 @@ def sigma_sox_thc(X: np.ndarray, U: np.ndarray, G: np.ndarray, Gm: np.ndarray,
     return sigma
 
 
+def sigma_sox_thc_rows(X: np.ndarray, U: np.ndarray, G: np.ndarray, Gm: np.ndarray,
+                       rows: int = 64) -> np.ndarray:
+    """SOX at one tau by the same steps as ``sigma_sox_thc``, with D_PR formed
+    `rows` values of P at a time so that the three-index intermediates B and C
+    never exist for all P at once (they are N x N x n each: 25 GB at 500 AOs and
+    2500 THC points).  Every step is the formula of the scheme evaluated on a slice
+    of P; nothing is reordered or fused.  Pinned to ``sigma_sox_thc`` on small inputs.
+    """
+    G_Rq = X.T @ G
+    G_wP = G @ X
+    N = U.shape[0]
+    D = np.empty((N, N))
+    for p0 in range(0, N, rows):
+        sl = slice(p0, min(N, p0 + rows))
+        A = np.matmul(U[sl], Gm)                                    # A_Pqv, P in the slice
+        B = np.einsum("Pqv,Rq->PRv", A, G_Rq, optimize=True)        # B_PRv
+        C = np.einsum("Rvw,wP->RvP", U, G_wP[:, sl], optimize=True)  # C_RvP
+        D[sl] = np.einsum("RvP,PRv->PR", C, B, optimize=True)       # D_PR
+    S_RP = C_SOX * D.T
+    return X @ S_RP @ X.T
+
+
 def sigma_direct_thc(X: np.ndarray, V: np.ndarray, G: np.ndarray, Gm: np.ndarray) -> np.ndarray:
     """Direct term at one tau in THC form.
 

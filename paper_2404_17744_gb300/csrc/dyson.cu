@@ -356,17 +356,11 @@ constexpr size_t kGjSmemMax = 232448;  // 227 KB per CTA
 // waves of resident clusters, with rows kept in global memory (L2) counted twice
 // (ties: smaller clusters).
 int choose_gj_cluster(thc_dyson* d) {
-  static std::mutex mu;
-  static bool attr_set = false;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (!attr_set) {
-      THC_TRY(dcheck(d, cudaFuncSetAttribute(gj_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kGjSmemMax),
-                     "Gauss-Jordan shared memory"));
-      attr_set = true;
-    }
-  }
+  THC_TRY(thc::per_device(reinterpret_cast<const void*>(gj_cluster_kernel), nullptr, [&](int, int*) {
+    return dcheck(d, cudaFuncSetAttribute(gj_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kGjSmemMax),
+                  "Gauss-Jordan shared memory");
+  }));
   const long long count = d->half ? d->n_iw / 2 : d->n_iw;
   int best_cs = 1;
   bool best_res = false;

@@ -331,18 +331,12 @@ int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, 
   THC_TRY(make_map(ctx, &bl, B.lo, K, B, BN));
   auto kern = tc::split_gemm_kernel<BN, MULTI, Epi>;
   using CfgE = tc::Cfg<BN>;
-  static bool attr_set = false;  // one per instantiation
-  if (!attr_set) {
+  int sms = 0;  // the kernel's shared-memory attribute is set once per device with it
+  THC_TRY(per_device(reinterpret_cast<const void*>(kern), &sms, [&](int dev, int* v) {
     THC_TRY(check_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgE::SMEM),
                        "split gemm smem attribute"));
-    attr_set = true;
-  }
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    THC_TRY(check_cuda(ctx, cudaGetDevice(&dev), "device"));
-    THC_TRY(check_cuda(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count"));
-  }
+    return check_cuda(ctx, cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  }));
   const long long tiles = ((M + tc::BM - 1) / tc::BM) * ((N + BN - 1) / BN) * batch;
   const dim3 grid((unsigned)std::min<long long>(tiles, sms), 1, 1);  // persistent: one CTA per SM at most
   ProfRec rec;
@@ -442,12 +436,11 @@ int launch_bcd_shape(thc_ctx* ctx, const Split& Y, const Split& U, const Split& 
     THC_TRY(make_map_3d(ctx, &m.at, h ? At.lo : At.hi, adims, strides, abox));
   }
   auto kern = tc::sox_bcd_kernel<CP, CR>;
-  static int max_clusters = 0;  // resident clusters of this shape on the device
-  if (!max_clusters) {
+  int max_clusters = 0;  // resident clusters of this shape on the current device
+  THC_TRY(per_device(reinterpret_cast<const void*>(kern), &max_clusters, [&](int dev, int* out) {
     THC_TRY(check_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::BcdCfg::SMEM),
                        "fused B C/D smem attribute"));
-    int dev = 0, sms = 0;
-    THC_TRY(check_cuda(ctx, cudaGetDevice(&dev), "device"));
+    int sms = 0;
     THC_TRY(check_cuda(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count"));
     int mc = sms / CS;
     if (CS > 1) {
@@ -467,8 +460,9 @@ int launch_bcd_shape(thc_ctx* ctx, const Split& Y, const Split& U, const Split& 
       mc = std::min(mc, q);
     }
     if (mc < 1) return fail(ctx, THC_ENOTSUP, "fused B C/D: no cluster of this shape fits on the device");
-    max_clusters = mc;
-  }
+    *out = mc;
+    return THC_OK;
+  }));
   // v chunks per cluster tile: fewest v steps on the busiest SM, one more per unit for its flush
   // cluster tiles that reach R >= P (the kernel's enumeration) and the (P, R) pairs they cover
   const long long tm = (Pc + tc::BM - 1) / tc::BM, tn = (N + tc::BM - 1) / tc::BM;
@@ -528,8 +522,6 @@ int split_init(thc_ctx* ctx, size_t budget) {
   ctx->ldn = (int)ldn;
   ctx->ldN = (int)ldN;
   const size_t h = sizeof(bf16);
-  THC_TRY(ctx_alloc(ctx, (void**)&ctx->d_err, sizeof(int), "error flag"));
-  THC_TRY(check_cuda(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream), "clear error flag"));
   auto pair = [&](bf16** hi, bf16** lo, size_t elems, const char* what) -> int {
     THC_TRY(ctx_alloc(ctx, (void**)hi, h * elems, what));
     return ctx_alloc(ctx, (void**)lo, h * elems, what);
@@ -592,20 +584,7 @@ int split_init(thc_ctx* ctx, size_t budget) {
       ++it;
     }
   }
-  return split_check(ctx);
-}
-
-int split_check(thc_ctx* ctx) {
-  if (!ctx->d_err) return THC_OK;
-  int h = 0;
-  THC_TRY(check_cuda(ctx, cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
-                     "read error flag"));
-  THC_TRY(check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "error flag sync"));
-  if (h) {
-    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
-    return fail(ctx, THC_ETIMEOUT, "a tensor-core pipeline wait ran out (code " + std::to_string(h) + ")");
-  }
-  return THC_OK;
+  return status_check(ctx);
 }
 
 // ------------------------------------------------------------------ eval
@@ -731,20 +710,20 @@ int gemm_bf16x3(cudaStream_t stream, int batch, int M, int N, int K, const doubl
   };
   auto alloc = [&](void** p, size_t bytes) { return cudaMallocAsync(p, std::max<size_t>(bytes, 16), stream); };
   if (alloc(&ah, h * ba * M * ldK) || alloc(&al, h * ba * M * ldK) || alloc(&bh, h * bb * N * ldK) ||
-      alloc(&bl, h * bb * N * ldK) || alloc(&err, sizeof(int))) {
+      alloc(&bl, h * bb * N * ldK) || alloc(&err, 2 * sizeof(int))) {
     cudaGetLastError();
     cleanup();
     return fail(nullptr, THC_ENOMEM, "thc_gemm_bf16x3: allocation failed");
   }
   tmp.d_err = (int*)err;
-  int rc = check_cuda(nullptr, cudaMemsetAsync(err, 0, sizeof(int), stream), "thc_gemm_bf16x3: clear flag");
+  int rc = check_cuda(nullptr, cudaMemsetAsync(err, 0, 2 * sizeof(int), stream), "thc_gemm_bf16x3: clear flag");
   const Split As = Split{(bf16*)ah, (bf16*)al, M, ldK, ba, (long long)M * ldK};
   const Split Bs = Split{(bf16*)bh, (bf16*)bl, N, ldK, bb, (long long)N * ldK};
   if (rc == THC_OK) rc = launch_split_f64(&tmp, A, sA, K, 1, 1.0, As, K, "split A");
   if (rc == THC_OK) rc = launch_split_f64(&tmp, B, sB, K, 1, 1.0, Bs, K, "split B");
   if (rc == THC_OK)
     rc = gemm(&tmp, K_BACK, As, ba > 1, Bs, bb > 1, M, N, K, batch, EpiF64{C, N, sC}, "thc_gemm_bf16x3");
-  if (rc == THC_OK) rc = split_check(&tmp);
+  if (rc == THC_OK) rc = status_check(&tmp);
   cleanup();
   cudaStreamSynchronize(stream);
   if (rc != THC_OK) fail(nullptr, rc, tmp.err);

@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* empty = full + C::STAGES;
   uint64_t* acc_full = empty + C::STAGES;  // [2] C_v and B_v of a v ready
   uint64_t* acc_free = acc_full + 2;       // [2] buffer read by the epilogue
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_free + 2);
+  uint64_t* drain = acc_free + 2;          // every MMA of this CTA complete (unwind)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = CS > 1 ? cluster_ctarank() : 0u;
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_free[i], NEPI);
     }
+    mbar_init(drain, 1);
     fence_mbar_init();
     prefetch_map(&hi.yp);
     prefetch_map(&lo.yp);
@@ -233,6 +235,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
       }
+      // every copy this CTA armed has landed before it may leave (immediate unless a wait ran out)
+      if (!drain_stages(full, C::STAGES, g)) atomicExch(err, 15);
       if constexpr (CS > 1) {
         // every CTA's release of the last stages has arrived here before the CTA can exit
         for (int i = 0; i < C::STAGES && ok; ++i, ++g) {
@@ -293,6 +297,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (ok) mma_commit(&acc_full[buf]);  // C_v and B_v of this v complete
         }
       }
+      // every MMA issued (and the barrier arrivals it signals in the cluster) has completed
+      // before TMEM is freed (immediate unless a wait ran out)
+      mma_commit(drain);
+      if (!mbar_wait(drain, 0)) atomicExch(err, 16);
     }
   } else {
     const int quarter = warp & 3, half = (warp - 2) >> 2;

@@ -41,7 +41,10 @@
 // overlaps the MMAs of the next), and the epilogue streams 32-column slices
 // straight from TMEM without a register accumulator.
 // Every mbarrier wait is bounded in time (globaltimer); a wait that runs out
-// sets *err and the CTA unwinds, frees its TMEM and returns.
+// sets *err and the CTA unwinds: the producer waits (bounded) for every TMA
+// stage it issued, the MMA lane commits its outstanding MMAs to a drain
+// barrier and waits for it (bounded), and only then is TMEM freed and the CTA
+// returns, so no copy or MMA lands in shared memory or TMEM that was given up.
 #pragma once
 
 #include <cuda.h>
@@ -99,8 +102,9 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// Waits until the phase of parity `parity` of *bar has completed; false after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits until the phase of parity `parity` of *bar has completed; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
   const uint32_t addr = smem_u32(bar);
   const unsigned long long t0 = globaltimer();
   while (true) {
@@ -111,8 +115,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(addr), "r"(parity)
         : "memory");
     if (done) return true;
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
+}
+
+// Unwind of a producer: waits (bounded) for the last phase armed on each of the
+// `stages` full barriers, i.e. for every TMA copy this thread issued.  `issued` is the
+// number of stage uses armed so far (stage g % stages, phase g / stages).
+__device__ __forceinline__ bool drain_stages(uint64_t* full, int stages, long long issued) {
+  bool ok = true;
+  for (int s = 0; s < stages; ++s) {
+    // last use g of stage s below `issued`: g = s + stages * j with the largest j
+    if (issued <= s) continue;
+    const long long last = s + (long long)stages * ((issued - 1 - s) / stages);
+    ok &= mbar_wait(&full[s], (uint32_t)(last / stages) & 1);
+  }
+  return ok;
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
@@ -227,7 +245,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* empty = full + C::STAGES;
   uint64_t* acc_full = empty + C::STAGES;  // [2] stage accumulator ready for the epilogue
   uint64_t* acc_free = acc_full + 2;       // [2] stage accumulator drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_free + 2);
+  uint64_t* drain = acc_free + 2;          // every MMA of this CTA complete (unwind)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nkb = (K + BKE - 1) / BKE;
@@ -243,6 +262,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_free[i], NEPI);
     }
+    mbar_init(drain, 1);
     fence_mbar_init();
     prefetch_map(&mAhi);
     prefetch_map(&mAlo);
@@ -281,6 +301,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tma_load_3d(st + 2 * C::A_BYTES + C::B_BYTES, &mBlo, &full[s], kb * BKE, nt * BN, bb);
         }
       }
+      // every copy issued has landed before the CTA may leave (immediate unless a wait ran out)
+      if (!drain_stages(full, C::STAGES, g)) atomicExch(err, 4);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -328,6 +350,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (MULTI || kb == nkb - 1) mma_commit(&acc_full[buf]);  // accumulator ready
         }
       }
+      // every MMA issued has completed before TMEM is freed (immediate unless a wait ran out)
+      mma_commit(drain);
+      if (!mbar_wait(drain, 0)) atomicExch(err, 5);
     }
   } else if (!MULTI) {
     const int quarter = warp & 3, half = (warp - 2) >> 2;

@@ -3,8 +3,11 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 
 #include "thc_internal.cuh"
 
@@ -13,6 +16,63 @@ thread_local std::string g_init_error;
 }  // namespace
 
 namespace thc {
+
+int per_device(const void* key, int* value, const std::function<int(int, int*)>& fn) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return THC_ECUDA;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({key, dev});
+  if (it != cache.end()) {
+    if (value) *value = it->second;
+    return THC_OK;
+  }
+  int v = 0;
+  const int rc = fn(dev, &v);
+  if (rc != THC_OK) return rc;
+  cache[{key, dev}] = v;
+  if (value) *value = v;
+  return THC_OK;
+}
+
+namespace {
+// flag <- 1 if any of the len values at p is NaN or infinite (grid-stride, no atomics on the
+// common path: a warp votes and one lane writes).
+__global__ void finite_scan_kernel(const double* __restrict__ p, long long len, int* flag) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(p[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
+}
+}  // namespace
+
+int launch_finite_scan(thc_ctx* ctx, const double* p, long long len, int* flag) {
+  if (len <= 0) return THC_OK;
+  const int blocks = (int)std::min<long long>((len + 255) / 256, 152LL * 8);
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, K_CHECK, 0.0, &rec));
+  finite_scan_kernel<<<blocks, 256, 0, ctx->stream>>>(p, len, flag);
+  return prof_end(ctx, &rec, cudaGetLastError(), "non-finite input scan");
+}
+
+int status_check(thc_ctx* ctx) {
+  if (!ctx->d_err) return THC_OK;
+  int h[2] = {0, 0};
+  THC_TRY(check_cuda(ctx, cudaMemcpyAsync(h, ctx->d_err, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream),
+                     "read status words"));
+  THC_TRY(check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "status sync"));
+  if (h[0] || h[1]) {
+    THC_TRY(check_cuda(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(h), ctx->stream), "clear status words"));
+    if (h[0]) return fail(ctx, THC_ETIMEOUT, "a tensor-core pipeline wait ran out (code " + std::to_string(h[0]) + ")");
+    return fail(ctx, THC_EINVAL, "G_tau or G_bmt held a NaN or infinite value (met by an evaluation since the "
+                                 "last synchronising call); the Sigma it produced is not valid");
+  }
+  return THC_OK;
+}
 
 int fail(thc_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -98,8 +158,19 @@ int init_impl(thc_ctx* ctx, const double* X, const double* V, const double* tau,
 
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->X, sizeof(double) * n * N, "X"));
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->V, sizeof(double) * N * N, "V"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->d_err, 2 * sizeof(int), "status words"));
   THC_TRY(check_cuda(ctx, cudaMemcpyAsync(ctx->X, X, sizeof(double) * n * N, cudaMemcpyDefault, ctx->stream), "copy X"));
   THC_TRY(check_cuda(ctx, cudaMemcpyAsync(ctx->V, V, sizeof(double) * N * N, cudaMemcpyDefault, ctx->stream), "copy V"));
+  {  // X and V must be finite: checked here, synchronously, with the status word of G
+    int* flag = ctx->d_err + 1;
+    int h = 0;
+    THC_TRY(check_cuda(ctx, cudaMemsetAsync(ctx->d_err, 0, 2 * sizeof(int), ctx->stream), "clear status words"));
+    THC_TRY(launch_finite_scan(ctx, ctx->X, (long long)(n * N), flag));
+    THC_TRY(launch_finite_scan(ctx, ctx->V, (long long)(N * N), flag));
+    THC_TRY(check_cuda(ctx, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "read flag"));
+    THC_TRY(check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "input check sync"));
+    if (h) return fail(ctx, THC_EINVAL, "X or V holds a NaN or infinite value");
+  }
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->e_part, sizeof(double) * nt, "energy partials"));
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->e_w, sizeof(double) * nt, "energy weights"));
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->e_out, sizeof(double), "energy"));
@@ -144,6 +215,10 @@ int ctx_create(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, const
     return fail(nullptr, THC_EINVAL, "need n_ao, n_thc, n_tau >= 1 and beta > 0");
   if (n_thc > 65535) return fail(nullptr, THC_EINVAL, "n_thc above 65535 is not supported");
   if (!X || !V || !tau) return fail(nullptr, THC_EINVAL, "X, V and tau must be non-NULL");
+  if (precision == THC_TF32)
+    return fail(nullptr, THC_ENOTSUP,
+                "THC_TF32 is not built: one TF32 product (11 significant bits) misses the 1e-6 Ha bound on "
+                "Sigma, and three TF32 products run at half the BF16 tensor rate for the bound THC_BF16X3 meets");
   if (precision != THC_FP64 && precision != THC_BF16X3) return fail(nullptr, THC_EINVAL, "unknown precision");
   if (terms <= 0 || terms > (THC_DIRECT | THC_SOX))
     return fail(nullptr, THC_EINVAL, "terms must be a non-empty subset of THC_DIRECT|THC_SOX");
@@ -199,6 +274,9 @@ int thc_sigma_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, doubl
   if (!G_tau || !Sigma_tau) return fail(ctx, THC_EINVAL, "G_tau and Sigma_tau must be non-NULL");
   if (!G_bmt && !ctx->mirrored) return fail(ctx, THC_EINVAL, "tau grid is not mirror-symmetric: pass G_bmt");
   if (Sigma_tau == G_tau || (G_bmt && Sigma_tau == G_bmt)) return fail(ctx, THC_EINVAL, "Sigma_tau aliases an input");
+  const long long len = (long long)ctx->n_tau * ctx->n * ctx->n;
+  THC_TRY(launch_finite_scan(ctx, G_tau, len, ctx->d_err + 1));
+  if (G_bmt) THC_TRY(launch_finite_scan(ctx, G_bmt, len, ctx->d_err + 1));
   try {
     if (ctx->precision == THC_FP64) return fp64_eval(ctx, G_tau, G_bmt, Sigma_tau);
     return split_eval(ctx, G_tau, G_bmt, Sigma_tau);
@@ -221,7 +299,7 @@ int thc_sigma_eval_host(thc_ctx* ctx, const double* G_tau, const double* G_bmt, 
   THC_TRY(thc_sigma_eval(ctx, ctx->hG, G_bmt ? ctx->hGb : nullptr, ctx->hS));
   THC_TRY(check_cuda(ctx, cudaMemcpyAsync(Sigma_tau, ctx->hS, bytes, cudaMemcpyDeviceToHost, ctx->stream), "D2H Sigma"));
   THC_TRY(check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "host-entry sync"));
-  return split_check(ctx);
+  return status_check(ctx);
 }
 
 int thc_energy(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const double* Sigma_tau,
@@ -231,13 +309,13 @@ int thc_energy(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const dou
   if (!G_tau || !Sigma_tau || !tau_weights || !E_dyn) return fail(ctx, THC_EINVAL, "NULL argument to thc_energy");
   if (!G_bmt && !ctx->mirrored) return fail(ctx, THC_EINVAL, "tau grid is not mirror-symmetric: pass G_bmt");
   THC_TRY(energy_eval(ctx, G_tau, G_bmt, Sigma_tau, tau_weights, E_dyn));
-  return split_check(ctx);
+  return status_check(ctx);
 }
 
 int thc_sync(thc_ctx* ctx) {
   if (!ctx) return thc::fail(nullptr, THC_EINVAL, "ctx is NULL");
   THC_TRY(thc::check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
-  return thc::split_check(ctx);
+  return thc::status_check(ctx);
 }
 
 int thc_gemm_bf16x3(int batch, int M, int N, int K, const double* A, long long strideA, const double* B,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -25,6 +26,7 @@ enum KernelClass {
   K_ENERGY,       // trace and weighted sum
   K_SPLIT,        // FP64 <-> BF16 hi/lo conversions
   K_SOX_BCD,      // fused B_PRv and C/D (split precision)
+  K_CHECK,        // non-finite input scans
   K_COUNT
 };
 const char* kernel_class_name(int k);
@@ -85,7 +87,9 @@ struct thc_ctx {
   __nv_bfloat16 *T2s_h = nullptr, *T2s_l = nullptr; // (M X^T)^T, tc x n x ldN
   __nv_bfloat16 *Ats_h = nullptr, *Ats_l = nullptr; // A^T blocks, Pb x n x ldn
   double *Dd = nullptr;                             // D, tc x N x N
-  int *d_err = nullptr;                             // device error flag of the tensor-core kernels
+  // device status words: [0] a tensor-core pipeline wait that ran out (its code),
+  // [1] a non-finite value met in G_tau / G_bmt by an evaluation; read and cleared by status_check
+  int *d_err = nullptr;
 
   std::vector<void*> owned;  // every cudaMalloc of this context
   std::string err;
@@ -100,6 +104,12 @@ struct thc_ctx {
 };
 
 namespace thc {
+
+// Set-up that CUDA applies to one device (a kernel's shared-memory attribute, the
+// SM count, the resident clusters of a launch shape): fn(dev, &value) runs once per
+// (key, device) with that device current, under a lock; its value is cached and
+// returned in *value.  A failing fn (non-zero return) caches nothing.
+int per_device(const void* key, int* value, const std::function<int(int, int*)>& fn);
 
 // Records msg on ctx and returns code.
 int fail(thc_ctx* ctx, int code, const std::string& msg);
@@ -136,7 +146,11 @@ int autotune_entries();
 // split-precision path (sigma_split.cu)
 int split_init(thc_ctx* ctx, size_t budget);
 int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma);
-int split_check(thc_ctx* ctx);  // synchronises; THC_ETIMEOUT if a tensor-core wait ran out
+// Synchronises and reads the status words: THC_ETIMEOUT if a tensor-core wait ran out,
+// THC_EINVAL if an evaluation met a non-finite input; both are cleared.
+int status_check(thc_ctx* ctx);
+// Queues a scan of len FP64 values at p that sets d_err[1] if one is not finite.
+int launch_finite_scan(thc_ctx* ctx, const double* p, long long len, int* flag);
 int gemm_bf16x3(cudaStream_t stream, int batch, int M, int N, int K, const double* A, long long sA, const double* B,
                 long long sB, double* C, long long sC);
 

@@ -20,6 +20,7 @@ THC_ENOTSUP = -5
 
 THC_FP64 = 0
 THC_BF16X3 = 1
+THC_TF32 = 2      # not built: thc_sigma_init returns THC_ENOTSUP
 
 THC_DIRECT = 1
 THC_SOX = 2
@@ -68,6 +69,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_energy_static.restype = i
     lib.thc_sync.argtypes = [vp]
     lib.thc_sync.restype = i
+    lib.thc_wait_selftest.argtypes = [ctypes.c_longlong, vp]
+    lib.thc_wait_selftest.restype = i
     ll = ctypes.c_longlong
     lib.thc_gemm_bf16x3.argtypes = [i, i, i, i, dp, ll, dp, ll, dp, ll, vp]
     lib.thc_gemm_bf16x3.restype = i
@@ -246,6 +249,12 @@ def thc_energy_static(n_ao, n_tau, G_tau, G_bmt, Sigma_tau, tau_weights, stream=
 
 def thc_sync(ctx):
     _check(load_library().thc_sync(ctx), ctx)
+
+
+def thc_wait_selftest(limit_ns, stream=None):
+    """Runs the bounded-wait failure path once; raises ThcError (THC_ETIMEOUT expected)."""
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(load_library().thc_wait_selftest(int(limit_ns), s), None)
 
 
 def thc_gemm_bf16x3(batch, M, N, K, A, strideA, B, strideB, C, strideC, stream=None):

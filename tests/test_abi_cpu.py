@@ -66,3 +66,21 @@ def test_null_context_calls_are_rejected(lib):
         thc.thc_sigma_eval(None, None, None, None)
     assert thc.thc_launch_count(None) == 0
     thc.thc_destroy(None)
+
+
+def test_tf32_is_reported_as_not_built(lib):
+    from paper_2404_17744_gb300 import thc
+    X = np.zeros((2, 3))
+    V = np.zeros((3, 3))
+    with pytest.raises(thc.ThcError) as ei:
+        thc.thc_sigma_init(2, 3, 2, 3.0, X, V, np.array([1.0, 2.0]), precision=thc.THC_TF32)
+    assert ei.value.code == thc.THC_ENOTSUP
+    assert "TF32" in thc.thc_last_error(None)
+
+
+def test_wait_selftest_rejects_bad_limits_without_gpu(lib):
+    from paper_2404_17744_gb300 import thc
+    for bad in (0, 999, 10 ** 10):
+        with pytest.raises(thc.ThcError) as ei:
+            thc.thc_wait_selftest(bad)
+        assert ei.value.code == thc.THC_EINVAL

@@ -1,12 +1,25 @@
-"""The paper's largest sizes (Sec. III: up to ~1100 AOs; here N = 5 n).
+"""Parity at the paper's sizes (Sec. III: up to ~1100 AOs; here N = 5 n), in the launch
+configuration bench.py times, against the FP64 oracle's stored values.
 
-* 500 AOs, 2500 THC points, tau = 0.1 and beta - 0.1: the 3 x BF16 path against the FP64
-  GPU path (itself pinned to the oracle in test_sigma_gpu.py), 1e-6 bound,
-  plus Sigma_ij = Sigma_ji;
-* 1100 AOs, 5500 THC points, the same two tau points: the 3 x BF16 path alone (the FP64
-  path needs about two minutes per tau point there): symmetry and a non-trivial
-  result.
+tests/golden/<workload>_oracle.json is written by tests/golden/make_golden_large.py,
+which calls only oracle/ and workloads/: E_dyn over the workload's whole
+Gauss-Legendre grid (its own quadrature weights), the per-tau traces
+Tr[G(beta - tau_k) Sigma(tau_k)], and at the first, middle and last tau point the
+diagonal of Sigma and a seeded sample of off-diagonal elements.
+
+Bars: FP64 path 1e-10 Ha in Sigma and E_dyn; THC_BF16X3 1e-6 Ha in Sigma and 1e-5 Ha in
+E_dyn (every measured margin is printed).
+
+* thc200 (200 AOs, 1000 THC points, 100 tau, beta 100): both paths, all tau points;
+* thc500 (500 AOs, 2500 THC points, 120 tau, beta 1000): THC_BF16X3 on all 120 tau
+  points against the oracle's energy and samples; FP64 at the three stored tau points;
+* thc1100 (1100 AOs, 5500 THC points): one tau point next to 0, THC_BF16X3 against
+  the FP64 GPU path (a secondary check: the oracle needs 53 GB for U_Pqs and hours per
+  tau point there, so it has no stored values at this size).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -15,28 +28,27 @@ from workloads import synth
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-
-def _edge_case(name):
-    """The workload with two tau points next to 0 and beta, where Sigma is largest."""
-    case = synth.make_workload(name, n_tau=2)
-    case.tau = np.array([0.1, case.beta - 0.1])
-    case.tau_w = np.array([0.1, 0.1])
-    case.G_tau = synth.noninteracting_G(case.F, case.S, 0.0, case.beta, case.tau)
-    case.G_bmt = case.G_tau[::-1].copy()
-    return case
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def _eval(case, precision):
+def _golden(name):
+    with open(os.path.join(HERE, "golden", f"{name}_oracle.json")) as f:
+        return json.load(f)
+
+
+def _eval(case, precision, G_tau, G_bmt, weights):
     from paper_2404_17744_gb300 import thc
     dev = torch.device("cuda:0")
     X = torch.from_numpy(case.X).to(dev)
     V = torch.from_numpy(case.V).to(dev)
-    ctx = thc.thc_sigma_init(case.n, case.N, case.n_tau, case.beta, X, V, case.tau, precision, 3)
+    ctx = thc.thc_sigma_init(case.n, case.N, len(G_tau), case.beta, X, V, np.ascontiguousarray(case.tau_eval),
+                             precision, 3)
     try:
-        G = torch.from_numpy(case.G_tau).to(dev)
+        G = torch.from_numpy(np.ascontiguousarray(G_tau)).to(dev)
+        Gb = None if G_bmt is None else torch.from_numpy(np.ascontiguousarray(G_bmt)).to(dev)
         S = torch.empty_like(G)
-        thc.thc_sigma_eval(ctx, G, None, S)
-        E = thc.thc_energy(ctx, G, None, S, case.tau_w)
+        thc.thc_sigma_eval(ctx, G, Gb, S)
+        E = thc.thc_energy(ctx, G, Gb, S, np.ascontiguousarray(weights))
         thc.thc_sync(ctx)
         return S.cpu().numpy(), E
     finally:
@@ -45,21 +57,80 @@ def _eval(case, precision):
         torch.cuda.empty_cache()
 
 
-def test_500_ao_split_against_fp64():
-    case = _edge_case("thc500")
-    S64, E64 = _eval(case, 0)
-    Ssp, Esp = _eval(case, 1)
-    assert np.abs(S64 - np.swapaxes(S64, 1, 2)).max() <= 1e-10
+def _full_grid(name, precision):
+    case = synth.make_workload(name)
+    case.tau_eval = case.tau
+    S, E = _eval(case, precision, case.G_tau, None, case.tau_w)
+    return case, S, E
+
+
+def _check_samples(g, S_at, tol, label):
+    """S_at(k) -> Sigma(tau_k) of the GPU; compares the stored diagonal and samples."""
+    worst = 0.0
+    for k, smp in g["samples"].items():
+        S = S_at(int(k))
+        d = np.abs(np.diag(S) - np.array(smp["diag"])).max()
+        ij = np.array([[i, j] for i, j, _ in smp["offdiag"]])
+        od = np.abs(S[ij[:, 0], ij[:, 1]] - np.array([v for _, _, v in smp["offdiag"]])).max()
+        err = max(d, od)
+        worst = max(worst, err)
+        print(f"{label} tau[{k}] = {smp['tau']:.4g}: max|Sigma| {smp['max_abs']:.3e}, "
+              f"max|dSigma| on {len(smp['diag']) + len(ij)} stored elements {err:.2e}")
+        assert abs(np.abs(S).max() - smp["max_abs"]) <= tol
+        assert err <= tol, (k, err)
+    return worst
+
+
+@pytest.mark.parametrize("precision,s_tol,e_tol", [(0, 1e-10, 1e-10), (1, 1e-6, 1e-5)])
+def test_thc200_full_grid_against_oracle(precision, s_tol, e_tol):
+    g = _golden("thc200")
+    case, S, E = _full_grid("thc200", precision)
+    tr = np.array([np.trace(case.G_bmt[k] @ S[k]) for k in range(case.n_tau)])
+    dtr = np.abs(tr - np.array(g["trace_per_tau"])).max()
+    print(f"thc200 precision {precision}: E_dyn {E:.12f} oracle {g['E_dyn']:.12f} |dE| {abs(E - g['E_dyn']):.2e} "
+          f"(bar {e_tol:g}), max per-tau |dTr| {dtr:.2e}")
+    _check_samples(g, lambda k: S[k], s_tol, f"thc200 p{precision}")
+    assert np.abs(S - np.swapaxes(S, 1, 2)).max() <= s_tol
+    assert abs(E - g["E_dyn"]) <= e_tol
+
+
+def test_thc500_split_full_grid_against_oracle():
+    """c3: 500 AOs, 2500 THC points, 120 tau points, beta = 1000, THC_BF16X3 on every tau
+    point; error against the FP64 oracle reported per tau (trace) and per stored point."""
+    g = _golden("thc500")
+    case, S, E = _full_grid("thc500", 1)
+    tr = np.array([np.trace(case.G_bmt[k] @ S[k]) for k in range(case.n_tau)])
+    dtr = np.abs(tr - np.array(g["trace_per_tau"]))
+    print(f"thc500 3xBF16: E_dyn {E:.12f} oracle {g['E_dyn']:.12f} |dE| {abs(E - g['E_dyn']):.2e} (bar 1e-5); "
+          f"per-tau |dTr| max {dtr.max():.2e} at tau[{int(dtr.argmax())}]")
+    _check_samples(g, lambda k: S[k], 1e-6, "thc500 3xBF16")
+    assert abs(E - g["E_dyn"]) <= 1e-5
+
+
+def test_thc500_fp64_at_stored_tau_points():
+    """FP64 path at full size on the three stored tau points (a non-mirrored grid, so
+    G(beta - tau) is passed explicitly) against the oracle's samples at 1e-10."""
+    g = _golden("thc500")
+    case = synth.make_workload("thc500")
+    ks = sorted(int(k) for k in g["samples"])
+    case.tau_eval = case.tau[ks]
+    S, _ = _eval(case, 0, case.G_tau[ks], case.G_bmt[ks], case.tau_w[ks])
+    pos = {k: i for i, k in enumerate(ks)}
+    _check_samples(g, lambda k: S[pos[k]], 1e-10, "thc500 fp64")
+
+
+def test_thc1100_split_against_fp64_one_tau():
+    """c5 sizes (1100 AOs, 5500 THC points), tau = 0.1: THC_BF16X3 against the FP64 GPU
+    path (which matches the oracle at 1e-10 at every size tested above)."""
+    case = synth.make_workload("thc1100", n_tau=2)
+    case.tau_eval = np.array([0.1])
+    G = synth.noninteracting_G(case.F, case.S, 0.0, case.beta, case.tau_eval)
+    Gb = synth.noninteracting_G(case.F, case.S, 0.0, case.beta, case.beta - case.tau_eval)
+    w = np.array([0.1])
+    S64, E64 = _eval(case, 0, G, Gb, w)
+    Ssp, Esp = _eval(case, 1, G, Gb, w)
     err = np.abs(Ssp - S64).max()
-    print(f"500 AOs: max|Sigma| {np.abs(S64).max():.3e}, max|dSigma| split vs FP64 {err:.2e}, dE {abs(Esp - E64):.2e}")
+    print(f"thc1100: max|Sigma| {np.abs(S64).max():.3e}, max|dSigma| 3xBF16 vs FP64 {err:.2e}, "
+          f"|dE| {abs(Esp - E64):.2e}")
+    assert np.abs(S64 - np.swapaxes(S64, 1, 2)).max() <= 1e-10
     assert err <= 1e-6
-    assert abs(Esp - E64) <= 1e-5
-
-
-def test_1100_ao_split_runs_at_full_size():
-    case = _edge_case("thc1100")
-    S, E = _eval(case, 1)
-    assert np.isfinite(S).all() and np.isfinite(E)
-    assert np.abs(S - np.swapaxes(S, 1, 2)).max() <= 1e-6 * max(1e-12, np.abs(S).max()) + 1e-12
-    print(f"1100 AOs: max|Sigma| {np.abs(S).max():.3e}, E_dyn {E:.6e}")
-    assert np.abs(S).max() > 0

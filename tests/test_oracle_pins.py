@@ -269,3 +269,43 @@ def test_mlp_oracle_gradients_against_finite_differences():
             lm = mo.loss_and_grads(X, T, W1, b1, W2, b2)[0]
             flat[i] = old
             assert abs((lp - lm) / (2 * h) - G.reshape(-1)[i]) < 1e-7
+
+
+def test_mlp_oracle_forward_hand_computed():
+    """A 2-sample, 3 -> 2 -> 2 network evaluated by hand:
+    sample 1: z = (1 - 1 + 0.5, -1 + 2 - 1) = (0.5, 0), relu keeps (0.5, 0), y = (2*0.5 + 1, -2) = (2, -2);
+    sample 2: z = (3 + 0.5, -1 - 1) = (3.5, -2), relu (3.5, 0), y = (2*3.5 + 1, -2) = (8, -2);
+    targets (1, -2), (8, 0): residuals (1, 0), (0, -2), loss (1 + 4) / 4 = 1.25."""
+    from oracle import mlp_oracle as mo
+    X = np.array([[1.0, 2.0, -1.0], [0.0, -1.0, 3.0]])
+    W1 = np.array([[1.0, 0.0, 1.0], [-1.0, 1.0, 0.0]])
+    b1 = np.array([0.5, -1.0])
+    W2 = np.array([[2.0, -1.0], [0.0, 3.0]])
+    b2 = np.array([1.0, -2.0])
+    T = np.array([[1.0, -2.0], [8.0, 0.0]])
+    for fp16 in (False, True):   # every weight is exact in FP16
+        Y, _ = mo.forward(X, W1, b1, W2, b2, fp16_weights=fp16)
+        assert np.array_equal(Y, np.array([[2.0, -2.0], [8.0, -2.0]]))
+        loss, gW1, gb1, gW2, gb2 = mo.loss_and_grads(X, T, W1, b1, W2, b2, fp16_weights=fp16)
+        assert loss == 1.25
+        # dL/dy = 2 r / 4 = ((0.5, 0), (0, -1)); dL/db2 = column sums
+        assert np.array_equal(gb2, np.array([0.5, -1.0]))
+        # dL/dW2 = dY^T A1 with A1 = ((0.5, 0), (3.5, 0))
+        assert np.array_equal(gW2, np.array([[0.25, 0.0], [-3.5, 0.0]]))
+        # hidden unit 2 is inactive in both samples (z <= 0): no gradient reaches W1[1], b1[1]
+        assert np.array_equal(gW1[1], np.zeros(3)) and gb1[1] == 0.0
+        # unit 1: dz = dY @ W2[:, 0] = (0.5*2 + 0, 0 + (-1)*0) = (1, 0) -> gW1[0] = x_1, gb1[0] = 1
+        assert np.array_equal(gW1[0], X[0]) and gb1[0] == 1.0
+
+
+@pytest.mark.parametrize("rows", [1, 7, 64])
+def test_sox_rowwise_equals_scheme(rows):
+    """sigma_sox_thc_rows (D formed a slice of P at a time, for the full-size golden values)
+    evaluates the same steps as sigma_sox_thc, on ragged slices too."""
+    case = synth.make_sigma_case(11, 45, 3, 20.0, 31)
+    U = o.thc_U(case.X, case.V)
+    for k in range(case.n_tau):
+        G, Gm = case.G_tau[k], o.g_minus_tau(case.G_bmt[k])
+        a = o.sigma_sox_thc(case.X, U, G, Gm)
+        b = o.sigma_sox_thc_rows(case.X, U, G, Gm, rows=rows)
+        assert np.abs(a - b).max() <= 1e-15 * np.abs(a).max()
