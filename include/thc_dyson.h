@@ -51,10 +51,10 @@ int thc_dyson_init(thc_dyson **d, int n_ao, int n_tau, int n_iw, int n_l, double
  *   mu         in: starting guess; out: the chemical potential found
  *   tol        tolerance on the electron count (<= 0: 1e-10)
  *   G_tau      dev out, n_tau x n_ao x n_ao
- * The count N(mu) is monotonic; the search takes secant steps from the
- * starting guess (first step 1e-3), kept inside a bracket once one is known
- * and safeguarded by bisection (each trial is a full set of n_iw complex
- * inversions).  THC_EINVAL if it does not converge.  Synchronises.
+ * The count N(mu) is monotonic; the search takes Newton steps on the analytic
+ * slope dN/dmu (see thc_dyson_count), capped at 0.5 Ha, kept inside a bracket
+ * once one is known and safeguarded by bisection (each trial is a full set of
+ * n_iw complex inversions).  THC_EINVAL if it does not converge.  Synchronises.
  */
 int thc_dyson_solve(thc_dyson *d, const double *Sigma_tau, double n_elec, double *mu, double tol,
                     double *G_tau);
@@ -68,6 +68,34 @@ int thc_dyson_solve(thc_dyson *d, const double *Sigma_tau, double n_elec, double
  */
 int thc_dyson_energy(thc_dyson *d, const double *G_tau, const double *Sigma_tau, double *E_dyn,
                      double *gamma_F, double *n_per_spin);
+
+/*
+ * thc_dyson_count -- electron count per spin N(mu) = Tr[gamma S] of the Green's
+ * function G(i w) = [(i w + mu) S - F - Sigma(i w)]^{-1} at the given mu (appendix,
+ * case 2), and its slope dN/dmu = -Tr[(d gamma / dmu) S] from dG/dmu = -G S G
+ * (the slope thc_dyson_solve's Newton steps use).
+ *   Sigma_tau  dev, n_tau x n_ao x n_ao (NULL: Sigma = 0)
+ *   mu         chemical potential
+ *   n_per_spin host out;  dn_dmu host out (may be NULL)
+ * Overwrites the G(i w) that thc_dyson_commutator reads.  Synchronises.
+ */
+int thc_dyson_count(thc_dyson *d, const double *Sigma_tau, double mu, double *n_per_spin,
+                    double *dn_dmu);
+
+/*
+ * thc_dyson_commutator -- frequency-dependent commutator residual of the
+ * self-consistency, the error vector of commutator DIIS (Sec. III.A names damping
+ * and a frequency-dependent commutator DIIS):
+ *   e(i w_m) = H_m G_m S - S G_m H_m,   H_m = F + Sigma_out(i w_m),
+ * for every sampled frequency, with G_m the G(i w_m) of the last thc_dyson_solve
+ * (the Green's function Sigma_out was evaluated from).  At self-consistency
+ * G^{-1} = (i w + mu) S - H, so e = 0.
+ *   Sigma_out_tau dev, n_tau x n_ao x n_ao
+ *   E_iw          dev out, n_iw x n_ao x n_ao complex, interleaved (re, im)
+ * Allocates an n_iw x n_ao^2 complex workspace on first use (kept by d).
+ * Stream-ordered.
+ */
+int thc_dyson_commutator(thc_dyson *d, const double *Sigma_out_tau, double *E_iw);
 
 /* thc_dyson_evals -- number of N(mu) evaluations in the last thc_dyson_solve. */
 int thc_dyson_evals(const thc_dyson *d);

@@ -110,6 +110,27 @@ int thc_sigma_init(thc_ctx **ctx, int n_ao, int n_thc, int n_tau, double beta,
 int thc_sigma_eval(thc_ctx *ctx, const double *G_tau, const double *G_bmt, double *Sigma_tau);
 
 /*
+ * thc_sigma_eval_uhf -- spin-unrestricted Sigma_a(tau_k), Sigma_b(tau_k) for every k.
+ * The paper writes the method for spin-orbitals (Sec. II.A); with spin-conserving
+ * integrals and a G block-diagonal in spin, the second-order terms per spin s are
+ *   Sigma^SOX_s: the Sec. II.C scheme with all three lines of spin s (+1), and
+ *   Sigma^dir_s = -X (G^X_s(tau) o (V Pi V)) X^T with Pi summed over both spins,
+ *                 Pi = sum_s' G^X_s'(tau) o G^X_s'(-tau)^T
+ * (for G_a = G_b this is the restricted result of thc_sigma_eval for both spins).
+ * The Galitskii-Migdal energy is one half of the sum over both spins of the
+ * per-spin expression: E_dyn = (thc_energy(a) + thc_energy(b)) / 2.
+ *   G_tau_a, G_tau_b    dev, n_tau x n x n, G of spin a and b
+ *   G_bmt_a, G_bmt_b    dev G(beta - tau_k) of each spin, or NULL on a mirrored grid
+ *   Sigma_a, Sigma_b    dev, n_tau x n x n, overwritten; distinct, aliasing no input
+ * Same context (X, V, U, precision, terms) as the restricted evaluation; the split
+ * path allocates one FP32 N x N buffer per tau chunk on its first unrestricted call.
+ * Non-finite inputs are reported as for thc_sigma_eval.
+ */
+int thc_sigma_eval_uhf(thc_ctx *ctx, const double *G_tau_a, const double *G_bmt_a,
+                       const double *G_tau_b, const double *G_bmt_b, double *Sigma_a,
+                       double *Sigma_b);
+
+/*
  * thc_sigma_eval_host -- thc_sigma_eval with host buffers: copies G in,
  * evaluates, copies Sigma out and synchronises.  The device staging buffers
  * are allocated on first use and kept by the context.  Pinned host memory

@@ -6,8 +6,9 @@ thc_oracle.py: the Dyson equation in the non-orthogonal AO basis,
 the chemical potential re-optimised at every iteration so that the electron
 count Tr[gamma S] (gamma = -G(beta^-), per spin) is fixed (appendix, case 2),
 the Galitskii-Migdal dynamical energy (Eq. E2b), and damping followed by
-DIIS on the self-energy (Sec. III.A names damping and a DIIS variant; any
-linear combination of self-energies is allowed, appendix comment 1).
+DIIS on the self-energy (Sec. III.A names damping and a frequency-dependent
+commutator DIIS; any linear combination of self-energies is allowed,
+appendix comment 1).
 
 The tau <-> i w transforms use the IR sparse-sampling matrices of
 workloads.ir (an input, like the tau grid); every transform, inverse,
@@ -42,14 +43,33 @@ def electron_count(grid, S, Giw):
     return float(np.trace(-G_beta @ S))
 
 
+def electron_count_slope(grid, S, Giw):
+    """dN/dmu of the count above at fixed Sigma: dG(i w)/dmu = -G S G, so
+    dN/dmu = Tr[(d gamma/dmu) S] = sum_l u_l(beta) Tr[(fit_iw (G S G))_l S]."""
+    n = S.shape[0]
+    GSG = np.stack([g @ S @ g for g in Giw])
+    d_l = grid.fit_iw @ GSG.reshape(len(grid.iw), n * n)
+    return float(np.trace((grid.u_beta @ d_l).real.reshape(n, n) @ S))
+
+
+def commutator_residual(grid, S, F, Giw, Sigma_out_tau):
+    """Frequency-dependent commutator residual of the self-consistency (CDIIS, Sec. III.A):
+    e(i w_m) = H(i w_m) G(i w_m) S - S G(i w_m) H(i w_m) with H = F + Sigma_out(i w_m),
+    G the Green's function the self-energy Sigma_out was evaluated from.  At the fixed
+    point G^{-1} = (i w + mu) S - H, so H G S = (i w + mu) S G S - S = S G H: e = 0."""
+    H = F[None, :, :] + sigma_iw(grid, Sigma_out_tau)
+    return np.einsum("wij,wjk,kl->wil", H, Giw, S) - np.einsum("ij,wjk,wkl->wil", S, Giw, H)
+
+
 def g_tau_from_iw(grid, Giw):
     n = Giw.shape[1]
     g_l = (grid.fit_iw @ Giw.reshape(len(grid.iw), n * n)).real
     return (grid.U_tau @ g_l).reshape(-1, n, n)
 
 
-def solve_dyson(grid, S, F, Sigma_tau, n_elec, mu0=0.0, tol=1e-12):
-    """(G(tau), mu) with the electron count fixed; Sigma_tau None means Sigma = 0."""
+def solve_dyson(grid, S, F, Sigma_tau, n_elec, mu0=0.0, tol=1e-12, return_iw=False):
+    """(G(tau), mu) with the electron count fixed; Sigma_tau None means Sigma = 0.
+    return_iw adds G(i w_m) at the sampled frequencies as a third value."""
     n = S.shape[0]
     Siw = np.zeros((len(grid.iw), n, n), dtype=complex) if Sigma_tau is None else sigma_iw(grid, Sigma_tau)
 
@@ -69,7 +89,10 @@ def solve_dyson(grid, S, F, Sigma_tau, n_elec, mu0=0.0, tol=1e-12):
         step *= 2
         fb = count(b)
     mu = scipy.optimize.brentq(count, a, b, xtol=1e-15, rtol=1e-15, maxiter=200)
-    return g_tau_from_iw(grid, dyson_iw(grid, S, F, Siw, mu)), mu
+    Giw = dyson_iw(grid, S, F, Siw, mu)
+    if return_iw:
+        return g_tau_from_iw(grid, Giw), mu, Giw
+    return g_tau_from_iw(grid, Giw), mu
 
 
 def parity(grid):
@@ -109,6 +132,8 @@ def energy_matsubara(grid, G_tau, Sigma_tau, n_max=20000):
 
 
 def _diis(history, size):
+    """Sum_i c_i out_i with sum_i c_i = 1 minimising |sum_i c_i res_i|^2 (real part of the
+    inner products for complex residuals) over the last `size` (out, res) pairs."""
     outs, res = [h[0] for h in history[-size:]], [h[1] for h in history[-size:]]
     k = len(res)
     B = np.empty((k + 1, k + 1))
@@ -129,7 +154,8 @@ def run_loop(case, grid, n_elec, tol=1e-8, max_iter=60, damping=0.5, n_damp=2, d
         E = 2 Tr[gamma F] + E_dyn.
     Mixing: Sigma_in <- damping Sigma_out + (1 - damping) Sigma_in for the first
     n_damp iterations, then DIIS on the residual Sigma_out - Sigma_in
-    (mix="damp": damping throughout).
+    (mix="damp": damping throughout; mix="cdiis": DIIS on the frequency-dependent
+    commutator residual of ``commutator_residual`` instead, extrapolating Sigma_out).
     """
     X, V, F, S = case.X, case.V, case.F, case.S
     n = F.shape[0]
@@ -142,7 +168,7 @@ def run_loop(case, grid, n_elec, tol=1e-8, max_iter=60, damping=0.5, n_damp=2, d
                 Gm = o.g_minus_tau(G_tau[G_tau.shape[0] - 1 - k])   # mirrored IR grid
                 out[k] = o.sigma_sox_thc(X, U, Gk, Gm) + o.sigma_direct_thc(X, V, Gk, Gm)
             return out
-    G, mu = solve_dyson(grid, S, F, None, n_elec, 0.0)
+    G, mu, Giw = solve_dyson(grid, S, F, None, n_elec, 0.0, return_iw=True)
     Sig_in = np.zeros_like(G)
     hist, E_prev, history = [], None, []
     converged = False
@@ -158,11 +184,11 @@ def run_loop(case, grid, n_elec, tol=1e-8, max_iter=60, damping=0.5, n_damp=2, d
             converged = True
             break
         E_prev = E
-        r = Sig_out - Sig_in
+        r = commutator_residual(grid, S, F, Giw, Sig_out) if mix == "cdiis" else Sig_out - Sig_in
         history.append((Sig_out, r))
         if mix == "damp" or it <= n_damp:
             Sig_in = damping * Sig_out + (1.0 - damping) * Sig_in
         else:
             Sig_in = _diis(history, diis_size)
-        G, mu = solve_dyson(grid, S, F, Sig_in, n_elec, mu)
+        G, mu, Giw = solve_dyson(grid, S, F, Sig_in, n_elec, mu, return_iw=True)
     return dict(history=hist, E=hist[-1]["E"], mu=mu, G=G, Sigma=Sig_out, converged=converged, iters=len(hist))

@@ -184,6 +184,57 @@ def sigma_four_index(v: np.ndarray, G_tau: np.ndarray, G_bmt: np.ndarray, terms:
     return out
 
 
+# ------------------------------------------------- unrestricted (two spins)
+def sigma_uhf_spin_orbital(v: np.ndarray, G_a: np.ndarray, G_b: np.ndarray, Gm_a: np.ndarray,
+                           Gm_b: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Second-order self-energy of a spin-unrestricted G at one tau, from the
+    spin-orbital definition (Sec. II.A works in spin-orbitals).
+
+    The 2n spin-orbitals are (orbital, spin); a chemist-notation integral (pq|rs)
+    is the spatial v_pqrs when p, q share a spin and r, s share a spin, else 0;
+    G is block-diagonal in spin.  In spin-orbitals the two second-order terms are
+      Sigma_tr = - sum (tu|vw)(xr|yz) G_ux G_vz G_yw(-tau)        (bubble)
+                 + sum (pr|qs)(tu|vw) G_wp G_uq G_sv(-tau)        (SOX),
+    the closed loop of the bubble running over both spins (which gives the -2 of
+    the restricted form).  Returns the alpha and beta blocks.  Plain einsum.
+    """
+    n = v.shape[0]
+    spin = np.repeat([0, 1], n)
+    orb = np.tile(np.arange(n), 2)
+    same = (spin[:, None] == spin[None, :]).astype(float)
+    vso = v[np.ix_(orb, orb, orb, orb)] * same[:, :, None, None] * same[None, None, :, :]
+    Z = np.zeros_like(G_a)
+    G = np.block([[G_a, Z], [Z, G_b]])
+    Gm = np.block([[Gm_a, Z], [Z, Gm_b]])
+    S = (-np.einsum("tuvw,xryz,ux,vz,yw->tr", vso, vso, G, G, Gm, optimize=False)
+         + np.einsum("prqs,tuvw,wp,uq,sv->tr", vso, vso, G, G, Gm, optimize=False))
+    return S[:n, :n], S[n:, n:]
+
+
+def sigma_uhf_thc(X: np.ndarray, V: np.ndarray, U: np.ndarray, G_a: np.ndarray, G_b: np.ndarray,
+                  Gm_a: np.ndarray, Gm_b: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Unrestricted self-energies at one tau in THC form.  Per spin s the SOX term is
+    the restricted scheme with G^s (all three lines carry spin s); the bubble sums
+    the polarisations of both spins and the outer line carries spin s:
+      Pi = G^X_a(tau) o G^X_a(-tau)^T + G^X_b(tau) o G^X_b(-tau)^T,
+      Sigma^dir_s = -X (G^X_s(tau) o (V Pi V)) X^T."""
+    def gx(G):
+        return X.T @ G @ X
+    Pi = gx(G_a) * gx(Gm_a).T + gx(G_b) * gx(Gm_b).T
+    W = V @ Pi @ V
+    out = []
+    for G, Gm in ((G_a, Gm_a), (G_b, Gm_b)):
+        out.append(-(X @ (gx(G) * W) @ X.T) + sigma_sox_thc(X, U, G, Gm))
+    return out[0], out[1]
+
+
+def energy_dyn_tau_uhf(G_bmt_a, G_bmt_b, S_a, S_b, weights) -> float:
+    """Galitskii-Migdal dynamical energy (Eq. E2b) of an unrestricted G: one half of
+    the sum over both spins of -int Tr[G_s(beta - tau) Sigma_s(tau)] dtau (equal to
+    the per-spin expression of ``energy_dyn_tau`` when the spins are equal)."""
+    return 0.5 * (energy_dyn_tau(G_bmt_a, S_a, weights) + energy_dyn_tau(G_bmt_b, S_b, weights))
+
+
 # ---------------------------------------------------------------- energy
 def energy_dyn_tau(G_bmt: np.ndarray, Sigma_tau: np.ndarray, weights: np.ndarray) -> float:
     """Galitskii-Migdal dynamical energy on the tau axis (Eq. E2b).

@@ -54,8 +54,11 @@ struct thc_dyson {
   int gj_cs = 1;                                        // CTAs per cluster of the Gauss-Jordan kernel
   bool gj_resident = false;                             // its rows kept in shared memory
   double *scal = nullptr;                               // small scalar scratch
+  double *work = nullptr;                               // n_iw x n^2 x 2: G S (count slope), H G (commutator)
+  double *work2 = nullptr;                              // n_iw x n^2 x 2: S G (commutator, allocated on first use)
+  double *trq = nullptr;                                // n_iw x 2: Tr[(G S)^2]
   int evals = 0;                                        // N(mu) evaluations of the last solve
-  double slope = 0.0;                                   // last secant estimate of dN/dmu (0: none)
+  double slope = 0.0;                                   // dN/dmu at the last evaluation (0: none)
   std::vector<void*> owned;
   std::string err;
 };
@@ -104,8 +107,8 @@ struct AccEpi {
 
 template <bool AK, bool BK_>
 int gemm(thc_dyson* d, long long M, long long Nn, long long K, const View& a, const View& b, const AccEpi& e,
-         const char* what) {
-  const dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((Nn + BN - 1) / BN), 1);
+         const char* what, long long batch = 1) {
+  const dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((Nn + BN - 1) / BN), (unsigned)batch);
   thc::f64::gemm_kernel<AK, BK_><<<grid, NT, 0, d->stream>>>(M, Nn, K, a, b, e);
   return dcheck(d, cudaGetLastError(), what);
 }
@@ -266,6 +269,49 @@ __global__ void trace_gs_kernel(int n, const double2* __restrict__ G, const doub
   }
 }
 
+// q_m = Tr[Y_m Y_m] = sum_ik Y_m[i][k] Y_m[k][i] (complex), one CTA per m.
+__global__ void trace_sq_kernel(int n, const double2* __restrict__ Y, double* __restrict__ q) {
+  const long long m = blockIdx.x, nn = (long long)n * n;
+  const double2* y = Y + m * nn;
+  double re = 0.0, im = 0.0;
+  for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+    const long long i = e / n, k = e - i * n;
+    const double2 a = y[e], b = y[k * n + i];
+    re = fma(a.x, b.x, fma(-a.y, b.y, re));
+    im = fma(a.x, b.y, fma(a.y, b.x, im));
+  }
+  __shared__ double r1[32], r2[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = re;
+    r2[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    re = threadIdx.x < (blockDim.x >> 5) ? r1[threadIdx.x] : 0.0;
+    im = threadIdx.x < (blockDim.x >> 5) ? r2[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (threadIdx.x == 0) {
+      q[2 * m] = re;
+      q[2 * m + 1] = im;
+    }
+  }
+}
+
+// H_m = F + Sigma(i w_m): F added to the real parts of the interleaved complex matrices.
+__global__ void add_real_kernel(long long nn, int nw, const double* __restrict__ F, double* __restrict__ H) {
+  const long long total = nn * nw;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    H[2 * i] += F[i % nn];
+}
+
 // part[2 b], part[2 b + 1]: block b's share of
 //   sum_l p_l sum_ij a_l[i][j] b_l[j][i]   and   sum_l ub_l sum_ij a_l[i][j] M[j][i]
 // over the rows (l, i) it owns (one warp per row, lanes along j).
@@ -419,8 +465,8 @@ int invert(thc_dyson* d, long long m0, long long count) {
 }
 
 // G(i w_m) at chemical potential mu for every m (the positive half only when the
-// frequencies come in pairs); returns the electron count per spin.
-int dyson_at(thc_dyson* d, double mu, double* n_out) {
+// frequencies come in pairs); returns the electron count per spin and its slope dN/dmu.
+int dyson_at(thc_dyson* d, double mu, double* n_out, double* dn_out) {
   const long long n = d->n, nn = n * n, nw = d->n_iw;
   const long long m0 = d->half ? nw / 2 : 0, cnt = nw - m0;
   const double* iw_d = d->scal + 8 + m0;  // frequencies live after 8 scalar slots
@@ -431,21 +477,35 @@ int dyson_at(thc_dyson* d, double mu, double* n_out) {
   trace_gs_kernel<<<(unsigned)cnt, 256, 0, d->stream>>>((int)n, reinterpret_cast<const double2*>(d->Giw) + m0 * nn,
                                                         d->S, d->tr + 2 * m0);
   THC_TRY(dcheck(d, cudaGetLastError(), "Tr[G S]"));
-  std::vector<double> t(2 * nw);
+  // slope: dG/dmu = -G S G, so dt_m/dmu = -Tr[(G_m S)^2] = -q_m; Y_m = G_m S (real and imaginary parts)
+  for (int part = 0; part < 2; ++part)
+    THC_TRY(gemm<true, false>(d, n, n, n, View{d->Giw + 2 * m0 * nn + part, 2 * nn, 2 * n, 2}, View{d->S, 0, n, 1},
+                              AccEpi{d->work + 2 * m0 * nn + part, 2 * nn, 2 * n, 2, 1.0, false}, "G S", cnt));
+  trace_sq_kernel<<<(unsigned)cnt, 256, 0, d->stream>>>((int)n, reinterpret_cast<const double2*>(d->work) + m0 * nn,
+                                                        d->trq + 2 * m0);
+  THC_TRY(dcheck(d, cudaGetLastError(), "Tr[(G S)^2]"));
+  std::vector<double> t(2 * nw), q(2 * nw);
   THC_TRY(dcheck(d, cudaMemcpyAsync(t.data() + 2 * m0, d->tr + 2 * m0, sizeof(double) * 2 * cnt,
                                     cudaMemcpyDeviceToHost, d->stream),
                  "copy traces"));
+  THC_TRY(dcheck(d, cudaMemcpyAsync(q.data() + 2 * m0, d->trq + 2 * m0, sizeof(double) * 2 * cnt,
+                                    cudaMemcpyDeviceToHost, d->stream),
+                 "copy slope traces"));
   THC_TRY(dcheck(d, cudaStreamSynchronize(d->stream), "Dyson sync"));
-  // Tr[gamma S] = -Re sum_m c_m t_m, with t_{n_iw - 1 - m} = conj(t_m) for the mirrored half
-  double acc = 0.0;
+  // Tr[gamma S] = -Re sum_m c_m t_m and dN/dmu = Re sum_m c_m q_m, with t_{n_iw - 1 - m} = conj(t_m)
+  // (likewise q) for the mirrored half
+  double acc = 0.0, dacc = 0.0;
   for (long long m = m0; m < nw; ++m) {
     acc += d->cre[m] * t[2 * m] - d->cim[m] * t[2 * m + 1];
+    dacc += d->cre[m] * q[2 * m] - d->cim[m] * q[2 * m + 1];
     if (d->half) {
       const long long mm = nw - 1 - m;
       acc += d->cre[mm] * t[2 * m] + d->cim[mm] * t[2 * m + 1];
+      dacc += d->cre[mm] * q[2 * m] + d->cim[mm] * q[2 * m + 1];
     }
   }
   *n_out = -acc;
+  if (dn_out) *dn_out = dacc;
   d->evals += 1;
   return THC_OK;
 }
@@ -518,6 +578,8 @@ int thc_dyson_init(thc_dyson** out, int n_ao, int n_tau, int n_iw, int n_l, doub
   if (rc == THC_OK) rc = dalloc(d, &d->Siw, 2 * n2 * n_iw, "Sigma(iw)");
   if (rc == THC_OK) rc = dalloc(d, &d->Giw, 2 * n2 * n_iw, "G(iw)");
   if (rc == THC_OK) rc = dalloc(d, &d->tr, 2 * (size_t)n_iw, "traces");
+  if (rc == THC_OK) rc = dalloc(d, &d->trq, 2 * (size_t)n_iw, "slope traces");
+  if (rc == THC_OK) rc = dalloc(d, &d->work, 2 * n2 * n_iw, "G S");
   if (rc == THC_OK) rc = dalloc(d, &d->scal, 8 + (size_t)n_iw, "scalars");
   if (rc == THC_OK) rc = dalloc(d, &d->part, 2 * (size_t)kEnergyBlocks, "energy partial sums");
   if (rc == THC_OK)
@@ -544,49 +606,39 @@ int thc_dyson_solve(thc_dyson* d, const double* Sigma_tau, double n_elec, double
     THC_TRY(dcheck(d, cudaMemsetAsync(d->Siw, 0, sizeof(double) * 2 * n2 * nw, d->stream), "zero Sigma"));
   }
   if (!(tol > 0)) tol = 1e-10;
-  // N(mu) is increasing.  Secant steps from the starting guess (a small first
-  // step: mu moves little between iterations), kept inside a bracket once one
-  // is known and replaced by bisection when they leave it or stall.
-  double m = *mu, nm = 0.0;
-  THC_TRY(dyson_at(d, m, &nm));
-  double lo = -INFINITY, hi = INFINITY, nlo = 0.0, nhi = 0.0;
+  // N(mu) is increasing.  Newton steps on the analytic slope dN/dmu (from
+  // dG/dmu = -G S G, evaluated with every count), each capped at 0.5 Ha, kept
+  // inside a bracket once one is known and replaced by bisection when they leave
+  // it, when the slope vanishes (mu in a gap) or every fourth step.
+  double m = *mu, nm = 0.0, dm = 0.0;
+  THC_TRY(dyson_at(d, m, &nm, &dm));
+  double lo = -INFINITY, hi = INFINITY;
   auto note = [&](double x, double nx) {
     if (nx < n_elec) {
-      if (x > lo) lo = x, nlo = nx;
+      if (x > lo) lo = x;
     } else if (x < hi) {
-      hi = x, nhi = nx;
+      hi = x;
     }
   };
   note(m, nm);
-  double mp = m, np_ = nm;
-  double step = (nm < n_elec ? 1.0 : -1.0) * 1e-3;
-  if (d->slope > 0.0 && std::isfinite(d->slope)) {  // Newton-like first step from the last slope
-    const double st = (n_elec - nm) / d->slope;
-    if (std::fabs(st) < 0.5) step = st;
-  }
   for (int it = 0; it < 200 && std::fabs(nm - n_elec) > tol; ++it) {
+    const bool bracket = std::isfinite(lo) && std::isfinite(hi);
+    if (bracket && hi - lo < 1e-15) break;
     double x;
-    if (it == 0) {
-      x = m + step;
-    } else if (np_ != nm && std::isfinite(lo) && std::isfinite(hi) && it % 4 == 3) {
-      x = 0.5 * (lo + hi);  // guaranteed progress every fourth step
+    if (dm > 1e-12 && std::isfinite(dm) && !(bracket && it % 4 == 3)) {
+      const double st = (n_elec - nm) / dm;
+      x = m + std::min(std::max(st, -0.5), 0.5);
+    } else if (bracket) {
+      x = 0.5 * (lo + hi);
     } else {
-      const double slope = (nm - np_) / (m - mp);
-      x = (slope > 0 && std::isfinite(slope)) ? m + (n_elec - nm) / slope : m + 4 * (m - mp);
-      const double cap = std::max(0.5, 4 * std::fabs(m - mp));
-      x = std::min(std::max(x, m - cap), m + cap);
+      x = m + (nm < n_elec ? 0.5 : -0.5);  // flat count (a gap) and no bracket yet: walk out
     }
-    if (std::isfinite(lo) && std::isfinite(hi) && !(x > lo && x < hi)) x = 0.5 * (lo + hi);
-    if (std::isfinite(lo) && std::isfinite(hi) && hi - lo < 1e-15) break;
-    mp = m, np_ = nm;
+    if (bracket && !(x > lo && x < hi)) x = 0.5 * (lo + hi);
     m = x;
-    THC_TRY(dyson_at(d, m, &nm));
+    THC_TRY(dyson_at(d, m, &nm, &dm));
     note(m, nm);
-    if (m != mp && nm != np_) {
-      const double sl = (nm - np_) / (m - mp);
-      if (sl > 0.0 && std::isfinite(sl)) d->slope = sl;
-    }
   }
+  d->slope = dm;
   if (std::fabs(nm - n_elec) > 1e3 * tol)
     return dfail(d, THC_EINVAL, "thc_dyson_solve: chemical potential search did not converge");
   *mu = m;
@@ -603,6 +655,55 @@ int thc_dyson_solve(thc_dyson* d, const double* Sigma_tau, double n_elec, double
   THC_TRY(gemm<true, false>(d, nt, n2, L, View{d->U_tau, 0, L, 1}, View{d->g_l, 0, n2, 1},
                             AccEpi{G_tau, 0, n2, 1, 1.0, false}, "G(tau)"));
   return dcheck(d, cudaStreamSynchronize(d->stream), "dyson solve sync");
+}
+
+int thc_dyson_count(thc_dyson* d, const double* Sigma_tau, double mu, double* n_per_spin, double* dn_dmu) {
+  if (!d) return thc::fail(nullptr, THC_EINVAL, "thc_dyson_count: NULL context");
+  if (!n_per_spin) return dfail(d, THC_EINVAL, "thc_dyson_count: NULL argument");
+  const long long n2 = (long long)d->n * d->n;
+  if (Sigma_tau) {
+    THC_TRY(sigma_to_iw(d, Sigma_tau));
+  } else {
+    THC_TRY(dcheck(d, cudaMemsetAsync(d->Siw, 0, sizeof(double) * 2 * n2 * d->n_iw, d->stream), "zero Sigma"));
+  }
+  double dn = 0.0;
+  THC_TRY(dyson_at(d, mu, n_per_spin, &dn));
+  if (dn_dmu) *dn_dmu = dn;
+  return THC_OK;
+}
+
+int thc_dyson_commutator(thc_dyson* d, const double* Sigma_out_tau, double* E_iw) {
+  if (!d) return thc::fail(nullptr, THC_EINVAL, "thc_dyson_commutator: NULL context");
+  if (!Sigma_out_tau || !E_iw) return dfail(d, THC_EINVAL, "thc_dyson_commutator: NULL argument");
+  const long long n = d->n, nn = n * n, nw = d->n_iw;
+  if (!d->work2) THC_TRY(dalloc(d, &d->work2, 2 * nn * nw, "S G"));
+  // H_m = F + Sigma_out(i w_m) in d->Siw; G_m of the last solve in d->Giw (all frequencies)
+  THC_TRY(sigma_to_iw(d, Sigma_out_tau));
+  add_real_kernel<<<blocks_for(nn * nw), 256, 0, d->stream>>>(nn, (int)nw, d->F, d->Siw);
+  THC_TRY(dcheck(d, cudaGetLastError(), "F + Sigma(iw)"));
+  // complex interleaved views: part 0 real, 1 imaginary; batch m
+  auto cv = [&](const double* base, int part) { return View{base + part, 2 * nn, 2 * n, 2}; };
+  auto ce = [&](double* base, int part, double alpha, bool acc) {
+    return AccEpi{base + part, 2 * nn, 2 * n, 2, alpha, acc};
+  };
+  const View Sv{d->S, 0, n, 1};
+  double *H = d->Siw, *G = d->Giw, *P = d->work, *Q = d->work2;
+  // P = H G
+  THC_TRY(gemm<true, false>(d, n, n, n, cv(H, 0), cv(G, 0), ce(P, 0, 1.0, false), "H G", nw));
+  THC_TRY(gemm<true, false>(d, n, n, n, cv(H, 1), cv(G, 1), ce(P, 0, -1.0, true), "H G", nw));
+  THC_TRY(gemm<true, false>(d, n, n, n, cv(H, 0), cv(G, 1), ce(P, 1, 1.0, false), "H G", nw));
+  THC_TRY(gemm<true, false>(d, n, n, n, cv(H, 1), cv(G, 0), ce(P, 1, 1.0, true), "H G", nw));
+  // E = P S
+  THC_TRY(gemm<true, false>(d, n, n, n, cv(P, 0), Sv, ce(E_iw, 0, 1.0, false), "H G S", nw));
+  THC_TRY(gemm<true, false>(d, n, n, n, cv(P, 1), Sv, ce(E_iw, 1, 1.0, false), "H G S", nw));
+  // Q = S G
+  THC_TRY(gemm<true, false>(d, n, n, n, Sv, cv(G, 0), ce(Q, 0, 1.0, false), "S G", nw));
+  THC_TRY(gemm<true, false>(d, n, n, n, Sv, cv(G, 1), ce(Q, 1, 1.0, false), "S G", nw));
+  // E -= Q H
+  THC_TRY(gemm<true, false>(d, n, n, n, cv(Q, 0), cv(H, 0), ce(E_iw, 0, -1.0, true), "S G H", nw));
+  THC_TRY(gemm<true, false>(d, n, n, n, cv(Q, 1), cv(H, 1), ce(E_iw, 0, 1.0, true), "S G H", nw));
+  THC_TRY(gemm<true, false>(d, n, n, n, cv(Q, 0), cv(H, 1), ce(E_iw, 1, -1.0, true), "S G H", nw));
+  return gemm<true, false>(d, n, n, n, cv(Q, 1), cv(H, 0), ce(E_iw, 1, -1.0, true), "S G H", nw);
 }
 
 int thc_dyson_energy(thc_dyson* d, const double* G_tau, const double* Sigma_tau, double* E_dyn, double* gamma_F,

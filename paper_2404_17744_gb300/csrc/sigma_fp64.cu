@@ -95,16 +95,18 @@ __global__ void __launch_bounds__(NT) sox_cd_kernel(int n, int N, int P0, int Pc
   }
 }
 
-// Pi = G^X(tau) o G^X(-tau)^T for a batch of tau points (Pi_QS = G^X_QS(tau) G^X_SQ(-tau)).
+// Pi (+)= G^X(tau) o G^X(-tau)^T for a batch of tau points (Pi_QS = G^X_QS(tau) G^X_SQ(-tau));
+// accumulate adds the polarisation of a second spin.
 __global__ void polarisation_kernel(long long N, long long batch, const double* __restrict__ GXp,
-                                    const double* __restrict__ GXm, double* __restrict__ Pi) {
+                                    const double* __restrict__ GXm, double* __restrict__ Pi, int accumulate) {
   const long long NN = N * N;
   const long long total = NN * batch;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long b = idx / NN, r = idx - b * NN;
     const long long i = r / N, j = r - i * N;
-    Pi[idx] = GXp[idx] * GXm[b * NN + j * N + i];
+    const double p = GXp[idx] * GXm[b * NN + j * N + i];
+    Pi[idx] = accumulate ? Pi[idx] + p : p;
   }
 }
 
@@ -128,15 +130,18 @@ __global__ void mirror_upper_kernel(long long N, double* __restrict__ D) {
 }
 
 // Epilogue of W = (V Pi) V: merged THC-space self-energy
-//   M_RP = C_SOX * D_PR + C_DIRECT * G^X_RP(tau) W_RP
+//   M_RP = C_SOX * D_PR + cd * G^X_RP(tau) W_RP
+// with cd = C_DIRECT for a restricted G (Pi of one spin, the loop's factor 2 in cd) and
+// cd = -1 per spin of an unrestricted G (Pi summed over both spins).
 struct MergeEpi {
   double* M;
   const double* D;    // may be null (direct term only)
   const double* GXp;
   long long N;
+  double cd;
   __device__ __forceinline__ void operator()(long long b, long long r, long long p, double w) const {
     const long long o = b * N * N;
-    double m = C_DIRECT * GXp[o + r * N + p] * w;
+    double m = cd * GXp[o + r * N + p] * w;
     if (D) m = fma(C_SOX, D[o + p * N + r], m);
     M[o + r * N + p] = m;
   }
@@ -191,106 +196,151 @@ int fp64_build_U(thc_ctx* ctx) {
   return launch_gemm<true, true>(ctx, K_UBUILD, N, n * n, N, 1, a, b, e, "U build");
 }
 
-int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
-  const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau;
-  const long long nn = n * n, NN = N * N, Nn = N * n;
+namespace {
+
+// Views of G(tau_k) and G(beta - tau_k) for the tau points c0 .. of one chunk.
+struct SpinIn {
+  View g, gb;
+};
+SpinIn spin_views(thc_ctx* ctx, const double* G_tau, const double* G_bmt, long long c0) {
+  const long long n = ctx->n, nn = n * n, nt = ctx->n_tau;
+  SpinIn v;
+  v.g = View{G_tau + c0 * nn, nn, n, 1};
+  v.gb = G_bmt ? View{G_bmt + c0 * nn, nn, n, 1} : View{G_tau + (nt - 1 - c0) * nn, -nn, n, 1};
+  return v;
+}
+
+// Y = X^T G(tau) (always), and with the direct term Ym = X^T G(-tau), G^X(+-tau)
+// (G^X(-tau) only when need_minus) for one spin and chunk.
+int fp64_project(thc_ctx* ctx, const SpinIn& in, long long tc, bool dir, bool need_minus) {
+  const long long n = ctx->n, N = ctx->N, NN = N * N, Nn = N * n;
+  // Y_Rq = sum_u X_uR G_uq(tau): computed as (m = q, c = R), A(q, u) = G[u, q], B(u, R) = X[u, R]
+  const View b{ctx->X, 0, N, 1};
+  THC_TRY(launch_gemm<false, false>(ctx, K_PROJECT, n, N, n, tc, View{in.g.p, in.g.sb, 1, n}, b,
+                                    f64::StoreEpi{ctx->Y, Nn, 1, n, 1.0}, "Y"));
+  if (!dir) return THC_OK;
+  if (need_minus)  // Ym = X^T G(-tau) = -X^T G(beta - tau)
+    THC_TRY(launch_gemm<false, false>(ctx, K_PROJECT, n, N, n, tc, View{in.gb.p, in.gb.sb, 1, n}, b,
+                                      f64::StoreEpi{ctx->Ym, Nn, 1, n, -1.0}, "Ym"));
+  // G^X(+-tau) = Y(+-) X : (m = P, c = R), A(P, q) = Y[P, q], B(q, R) = X[q, R]
+  THC_TRY(launch_gemm<true, false>(ctx, K_PROJECT, N, N, n, tc, View{ctx->Y, Nn, n, 1}, b,
+                                   f64::StoreEpi{ctx->GXp, NN, N, 1, 1.0}, "GX+"));
+  if (need_minus)
+    THC_TRY(launch_gemm<true, false>(ctx, K_PROJECT, N, N, n, tc, View{ctx->Ym, Nn, n, 1}, b,
+                                     f64::StoreEpi{ctx->GXm, NN, N, 1, 1.0}, "GX-"));
+  return THC_OK;
+}
+
+int fp64_polarisation(thc_ctx* ctx, long long tc, bool accumulate) {
+  const long long N = ctx->N, NN = N * N;
+  const long long total = NN * tc;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, K_POLARISATION, 0.0, &rec));
+  polarisation_kernel<<<blocks, 256, 0, ctx->stream>>>(N, tc, ctx->GXp, ctx->GXm, ctx->Pi, accumulate ? 1 : 0);
+  return prof_end(ctx, &rec, cudaGetLastError(), "polarisation");
+}
+
+// D_PR (all tau of the chunk) of the SOX scheme from Y (this spin's projection) and G(-tau).
+int fp64_sox(thc_ctx* ctx, const SpinIn& in, long long tc) {
+  const long long n = ctx->n, N = ctx->N, nn = n * n, NN = N * N, Nn = N * n;
+  for (long long k = 0; k < tc; ++k) {
+    const double* Gb = in.gb.p + k * in.gb.sb;  // G(beta - tau_k)
+    const double* Yk = ctx->Y + k * Nn;
+    double* Dk = ctx->D + k * NN;
+    for (long long P0 = 0; P0 < N; P0 += ctx->Pb) {
+      const long long Pc = std::min<long long>(ctx->Pb, N - P0);
+      // A_Pqv = sum_s U_Pqs G_sv(-tau) = -sum_s U_Pqs G_sv(beta - tau):
+      // (m = v, c = (P, q)), A(v, s) = Gb[s, v], B(s, (P, q)) = U[P0 + P, q, s]
+      THC_TRY(launch_gemm<false, true>(ctx, K_SOX_A, n, Pc * n, n, 1, View{Gb, 0, 1, n},
+                                       View{ctx->U + P0 * nn, 0, 1, n}, f64::StoreEpi{ctx->Ablk, 0, 1, n, -1.0},
+                                       "A"));
+      // B_PRv = sum_q A_Pqv G_Rq (batched over P): (m = v, c = R), A(v, q) = A[P, q, v], B(q, R) = Y[R, q];
+      // only R >= P is used (D is symmetric): column tiles wholly left of P are skipped
+      double bflops = 0.0, cdflops = 0.0;  // multiply-adds the kernels carry out, x 2
+      for (long long b = 0; b < Pc; ++b) bflops += 2.0 * n * n * (N - (P0 + b) / BN * BN);
+      for (long long p0 = 0; p0 < Pc; p0 += BN)
+        if (P0 + p0 < N) cdflops += (2.0 * nn + 2.0 * n) * std::min<long long>(BN, Pc - p0) * (N - (P0 + p0));
+      {
+        ProfRec rec;
+        THC_TRY(prof_begin(ctx, K_SOX_B, bflops, &rec));
+        f64::gemm_kernel<false, true><<<grid_for(n, N, Pc), NT, 0, ctx->stream>>>(
+            n, N, n, View{ctx->Ablk, nn, 1, n}, View{Yk, 0, 1, n}, f64::TriStoreEpi{ctx->Bblk, Nn, 1, n, 1.0, P0});
+        THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "B"));
+      }
+      // C and D fused, P <= R
+      ProfRec rec;
+      THC_TRY(prof_begin(ctx, K_SOX_CD, cdflops, &rec));
+      sox_cd_kernel<<<dim3((unsigned)((Pc + BN - 1) / BN), (unsigned)N), NT, 0, ctx->stream>>>(
+          (int)n, (int)N, (int)P0, (int)Pc, ctx->U, Yk, ctx->Bblk, Dk);
+      THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "C/D"));
+    }
+  }
+  return launch_mirror_upper(ctx, ctx->D, N, tc);
+}
+
+// M = C_SOX D^T + cd G^X o (T V) with T = V Pi already in the GXm buffer (direct term), or
+// M = C_SOX D^T alone; then Sigma = X M X^T for the tau points of the chunk.
+int fp64_merge_back(thc_ctx* ctx, long long tc, bool sox, bool dir, double cd, double* Sigma_chunk) {
+  const long long n = ctx->n, N = ctx->N, nn = n * n, NN = N * N, Nn = N * n;
+  View mview;
+  if (dir) {
+    THC_TRY(launch_gemm<true, false>(ctx, K_DIRECT_W, N, N, N, tc, View{ctx->GXm, NN, N, 1}, View{ctx->V, 0, N, 1},
+                                     MergeEpi{ctx->Pi, sox ? ctx->D : nullptr, ctx->GXp, N, cd}, "W"));
+    mview = View{ctx->Pi, NN, N, 1};
+  } else {
+    mview = View{ctx->D, NN, 1, N};  // M_RP = D_PR (C_SOX = +1)
+  }
+  // T2 = M X^T : (m = R, c = r), A(R, P) = M[R, P], B(P, r) = X[r, P]
+  if (dir)
+    THC_TRY(launch_gemm<true, true>(ctx, K_BACK, N, n, N, tc, mview, View{ctx->X, 0, 1, N},
+                                    f64::StoreEpi{ctx->T2, Nn, n, 1, 1.0}, "M X^T"));
+  else
+    THC_TRY(launch_gemm<false, true>(ctx, K_BACK, N, n, N, tc, mview, View{ctx->X, 0, 1, N},
+                                     f64::StoreEpi{ctx->T2, Nn, n, 1, C_SOX}, "M X^T"));
+  // Sigma = X T2 : (m = t, c = r), A(t, R) = X[t, R], B(R, r) = T2[R, r]
+  return launch_gemm<true, false>(ctx, K_BACK, n, n, N, tc, View{ctx->X, 0, N, 1}, View{ctx->T2, Nn, n, 1},
+                                  f64::StoreEpi{Sigma_chunk, nn, n, 1, 1.0}, "X T2");
+}
+
+}  // namespace
+
+// Restricted (nspin = 1: one per-spin G, direct factor C_DIRECT) or unrestricted
+// (nspin = 2: G of spin a and b, polarisation summed over both spins, direct factor -1
+// per spin, SOX within each spin).  Order per chunk, unrestricted: project b and form
+// Pi_b; project a and add Pi_a; T = V Pi; SOX a, merge a, back-transform a; project b
+// again (Y, G^X(tau)), SOX b, merge b, back-transform b.
+int fp64_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const double* const* G_bmt,
+                    double* const* Sigma) {
+  const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau, nn = n * n, NN = N * N;
   const bool sox = ctx->terms & THC_SOX, dir = ctx->terms & THC_DIRECT;
+  const double cd = nspin == 1 ? C_DIRECT : -1.0;
   for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
     const long long tc = std::min<long long>(ctx->tc, nt - c0);
-    // G(tau_k) and G(beta - tau_k) views for this chunk
-    const View g{G_tau + c0 * nn, nn, n, 1};
-    View gb;
-    if (G_bmt)
-      gb = View{G_bmt + c0 * nn, nn, n, 1};
-    else
-      gb = View{G_tau + (nt - 1 - c0) * nn, -nn, n, 1};
-    // Y_Rq = sum_u X_uR G_uq(tau): computed as (m = q, c = R), A(q, u) = G[u, q], B(u, R) = X[u, R]
-    {
-      const View a{g.p, g.sb, 1, n};
-      const View b{ctx->X, 0, N, 1};
-      THC_TRY(launch_gemm<false, false>(ctx, K_PROJECT, n, N, n, tc, a, b, f64::StoreEpi{ctx->Y, Nn, 1, n, 1.0}, "Y"));
-      if (dir) {
-        // Ym = X^T G(-tau) = -X^T G(beta - tau)
-        const View am{gb.p, gb.sb, 1, n};
-        THC_TRY(launch_gemm<false, false>(ctx, K_PROJECT, n, N, n, tc, am, b, f64::StoreEpi{ctx->Ym, Nn, 1, n, -1.0}, "Ym"));
-      }
+    SpinIn in[2];
+    for (int s = 0; s < nspin; ++s) in[s] = spin_views(ctx, G_tau[s], G_bmt[s], c0);
+    if (nspin == 2 && dir) {  // Pi of spin b first
+      THC_TRY(fp64_project(ctx, in[1], tc, true, true));
+      THC_TRY(fp64_polarisation(ctx, tc, false));
     }
+    THC_TRY(fp64_project(ctx, in[0], tc, dir, true));
     if (dir) {
-      // G^X(+-tau) = Y(+-) X : (m = P, c = R), A(P, q) = Y[P, q], B(q, R) = X[q, R]
-      const View b{ctx->X, 0, N, 1};
-      THC_TRY(launch_gemm<true, false>(ctx, K_PROJECT, N, N, n, tc, View{ctx->Y, Nn, n, 1}, b,
-                                       f64::StoreEpi{ctx->GXp, NN, N, 1, 1.0}, "GX+"));
-      THC_TRY(launch_gemm<true, false>(ctx, K_PROJECT, N, N, n, tc, View{ctx->Ym, Nn, n, 1}, b,
-                                       f64::StoreEpi{ctx->GXm, NN, N, 1, 1.0}, "GX-"));
-      const long long total = NN * tc;
-      const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
-      ProfRec rec;
-      THC_TRY(prof_begin(ctx, K_POLARISATION, 0.0, &rec));
-      polarisation_kernel<<<blocks, 256, 0, ctx->stream>>>(N, tc, ctx->GXp, ctx->GXm, ctx->Pi);
-      THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "polarisation"));
-    }
-    if (sox) {
-      for (long long k = 0; k < tc; ++k) {
-        const double* Gb = gb.p + k * gb.sb;  // G(beta - tau_k)
-        const double* Yk = ctx->Y + k * Nn;
-        double* Dk = ctx->D + k * NN;
-        for (long long P0 = 0; P0 < N; P0 += ctx->Pb) {
-          const long long Pc = std::min<long long>(ctx->Pb, N - P0);
-          // A_Pqv = sum_s U_Pqs G_sv(-tau) = -sum_s U_Pqs G_sv(beta - tau):
-          // (m = v, c = (P, q)), A(v, s) = Gb[s, v], B(s, (P, q)) = U[P0 + P, q, s]
-          THC_TRY(launch_gemm<false, true>(ctx, K_SOX_A, n, Pc * n, n, 1, View{Gb, 0, 1, n},
-                                           View{ctx->U + P0 * nn, 0, 1, n},
-                                           f64::StoreEpi{ctx->Ablk, 0, 1, n, -1.0}, "A"));
-          // B_PRv = sum_q A_Pqv G_Rq (batched over P): (m = v, c = R), A(v, q) = A[P, q, v], B(q, R) = Y[R, q];
-          // only R >= P is used (D is symmetric): column tiles wholly left of P are skipped
-          double bflops = 0.0, cdflops = 0.0;  // multiply-adds the kernels carry out, x 2
-          for (long long b = 0; b < Pc; ++b) bflops += 2.0 * n * n * (N - (P0 + b) / BN * BN);
-          for (long long p0 = 0; p0 < Pc; p0 += BN)
-            if (P0 + p0 < N) cdflops += (2.0 * nn + 2.0 * n) * std::min<long long>(BN, Pc - p0) * (N - (P0 + p0));
-          {
-            ProfRec rec;
-            THC_TRY(prof_begin(ctx, K_SOX_B, bflops, &rec));
-            f64::gemm_kernel<false, true><<<grid_for(n, N, Pc), NT, 0, ctx->stream>>>(
-                n, N, n, View{ctx->Ablk, nn, 1, n}, View{Yk, 0, 1, n}, f64::TriStoreEpi{ctx->Bblk, Nn, 1, n, 1.0, P0});
-            THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "B"));
-          }
-          // C and D fused, P <= R
-          ProfRec rec;
-          THC_TRY(prof_begin(ctx, K_SOX_CD, cdflops, &rec));
-          sox_cd_kernel<<<dim3((unsigned)((Pc + BN - 1) / BN), (unsigned)N), NT, 0, ctx->stream>>>(
-              (int)n, (int)N, (int)P0, (int)Pc, ctx->U, Yk, ctx->Bblk, Dk);
-          THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "C/D"));
-        }
-      }
-      THC_TRY(launch_mirror_upper(ctx, ctx->D, N, tc));
-    }
-    // M = C_SOX D^T + C_DIRECT G^X o (V Pi V)
-    const double* Mbuf;
-    View mview;
-    if (dir) {
-      // T = V Pi -> GXm buffer;  W = T V with the merge epilogue -> Pi buffer
+      THC_TRY(fp64_polarisation(ctx, tc, nspin == 2));
+      // T = V Pi -> GXm buffer (G^X(-tau) is not needed after Pi)
       THC_TRY(launch_gemm<true, false>(ctx, K_DIRECT_VPI, N, N, N, tc, View{ctx->V, 0, N, 1}, View{ctx->Pi, NN, N, 1},
                                        f64::StoreEpi{ctx->GXm, NN, N, 1, 1.0}, "V Pi"));
-      THC_TRY(launch_gemm<true, false>(ctx, K_DIRECT_W, N, N, N, tc, View{ctx->GXm, NN, N, 1}, View{ctx->V, 0, N, 1},
-                                       MergeEpi{ctx->Pi, sox ? ctx->D : nullptr, ctx->GXp, N}, "W"));
-      Mbuf = ctx->Pi;
-      mview = View{Mbuf, NN, N, 1};
-    } else {
-      Mbuf = ctx->D;  // M_RP = D_PR (C_SOX = +1)
-      mview = View{Mbuf, NN, 1, N};
     }
-    // T2 = M X^T : (m = R, c = r), A(R, P) = M[R, P], B(P, r) = X[r, P]
-    if (dir)
-      THC_TRY(launch_gemm<true, true>(ctx, K_BACK, N, n, N, tc, mview, View{ctx->X, 0, 1, N},
-                                      f64::StoreEpi{ctx->T2, Nn, n, 1, 1.0}, "M X^T"));
-    else
-      THC_TRY(launch_gemm<false, true>(ctx, K_BACK, N, n, N, tc, mview, View{ctx->X, 0, 1, N},
-                                       f64::StoreEpi{ctx->T2, Nn, n, 1, C_SOX}, "M X^T"));
-    // Sigma = X T2 : (m = t, c = r), A(t, R) = X[t, R], B(R, r) = T2[R, r]
-    THC_TRY(launch_gemm<true, false>(ctx, K_BACK, n, n, N, tc, View{ctx->X, 0, N, 1}, View{ctx->T2, Nn, n, 1},
-                                     f64::StoreEpi{Sigma + c0 * nn, nn, n, 1, 1.0}, "X T2"));
+    for (int s = 0; s < nspin; ++s) {
+      if (s == 1) THC_TRY(fp64_project(ctx, in[1], tc, dir, false));  // Y and G^X(tau) of spin b
+      if (sox) THC_TRY(fp64_sox(ctx, in[s], tc));
+      THC_TRY(fp64_merge_back(ctx, tc, sox, dir, cd, Sigma[s] + c0 * nn));
+    }
   }
   return THC_OK;
+}
+
+int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
+  return fp64_eval_spins(ctx, 1, &G_tau, &G_bmt, &Sigma);
 }
 
 int energy_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const double* Sigma,

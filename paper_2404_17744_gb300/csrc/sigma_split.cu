@@ -39,7 +39,8 @@ constexpr double C_SOX = +1.0;
 
 inline long long pad8(long long x) { return (x + 7) / 8 * 8; }
 
-// BF16 hi/lo pair: element (b, r, c) at hi[b * bs + r * ld + c].
+// BF16 hi/lo pair: element (b, r, c) at hi[b * bs + r * ld + c]; lo2, when not null, is
+// the third term of a constant operand (x = hi + lo + lo2 to about 24 bits).
 struct Split {
   bf16* hi;
   bf16* lo;
@@ -47,8 +48,13 @@ struct Split {
   long long ld;
   long long batch;
   long long bs;
-  Split at_row(long long r0, long long nrows) const { return Split{hi + r0 * ld, lo + r0 * ld, nrows, ld, batch, bs}; }
-  Split at_batch(long long b0, long long nb) const { return Split{hi + b0 * bs, lo + b0 * bs, rows, ld, nb, bs}; }
+  bf16* lo2 = nullptr;
+  Split at_row(long long r0, long long nrows) const {
+    return Split{hi + r0 * ld, lo + r0 * ld, nrows, ld, batch, bs, lo2 ? lo2 + r0 * ld : nullptr};
+  }
+  Split at_batch(long long b0, long long nb) const {
+    return Split{hi + b0 * bs, lo + b0 * bs, rows, ld, nb, bs, lo2 ? lo2 + b0 * bs : nullptr};
+  }
 };
 
 // ------------------------------------------------------------- tensor maps
@@ -206,13 +212,15 @@ struct EpiF64 {
   }
 };
 
-// Merge epilogue of W = T V: M[b][R][P] = c_x D[b][P][R] + c_d G^X[b][R][P] W, split (lanes along P).
+// Merge epilogue of W = T V: M[b][R][P] = c_x D[b][P][R] + cd G^X[b][R][P] W, split (lanes along P);
+// cd = C_DIRECT for a restricted G, -1 per spin of an unrestricted one (Pi summed over both spins).
 struct EpiMerge {
   bf16 *hi, *lo;
   long long ld;
   const double* D;  // may be null
   const float* GX;
   int N;
+  double cd;
   __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols) const {
     const int P = col0 + lane;
     if (P >= Ncols) return;
@@ -221,7 +229,7 @@ struct EpiMerge {
     for (int r = 0; r < 32; ++r) {
       const int R = row0 + r;
       if (R >= M) break;
-      double m = C_DIRECT * (double)GX[b * NN + (long long)R * N + P] * (double)t(r, lane);
+      double m = cd * (double)GX[b * NN + (long long)R * N + P] * (double)t(r, lane);
       if (D) m += C_SOX * D[b * NN + (long long)P * N + R];
       split_store(hi, lo, (long long)b * N * ld + (long long)R * ld + P, (float)m);
     }
@@ -248,9 +256,10 @@ struct EpiU {
 
 // --------------------------------------------------------- split kernels
 // dst(b, r, c) = split(scale * src[b sb + r sr + c sc]) for c < cols; 0 on the padding cols..ld.
+// With lo2 non-null the residual x - hi - lo is kept as a third term.
 __global__ void split_f64_kernel(const double* __restrict__ src, long long sb, long long sr, long long sc,
-                                 double scale, bf16* __restrict__ hi, bf16* __restrict__ lo, long long rows,
-                                 long long cols, long long ld, long long batch, long long dbs) {
+                                 double scale, bf16* __restrict__ hi, bf16* __restrict__ lo, bf16* __restrict__ lo2,
+                                 long long rows, long long cols, long long ld, long long batch, long long dbs) {
   const long long per = rows * ld, total = per * batch;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -259,11 +268,15 @@ __global__ void split_f64_kernel(const double* __restrict__ src, long long sb, l
     if (c < cols) {
       const double x = scale * src[b * sb + r * sr + c * sc];
       const bf16 h = __float2bfloat16_rn((float)x);
+      const double r1 = x - (double)__bfloat162float(h);
+      const bf16 l = __float2bfloat16_rn((float)r1);
       hi[o] = h;
-      lo[o] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+      lo[o] = l;
+      if (lo2) lo2[o] = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(l)));
     } else {
       hi[o] = __float2bfloat16_rn(0.f);
       lo[o] = __float2bfloat16_rn(0.f);
+      if (lo2) lo2[o] = __float2bfloat16_rn(0.f);
     }
   }
 }
@@ -288,16 +301,27 @@ __global__ void kr_split_kernel(const double* __restrict__ X, int n, int N, int 
   }
 }
 
-// Pi[b][Q][S] = G^X[b][Q][S] G^X(-)[b][S][Q], split.
+// Pi[b][Q][S] = G^X[b][Q][S] G^X(-)[b][S][Q] (+ add[b][Q][S], the FP32 polarisation of the
+// other spin, when add is set), split; with keep set, the FP32 value is stored there instead.
 __global__ void polarisation_split_kernel(long long N, long long batch, const float* __restrict__ GX,
-                                          const float* __restrict__ GXm, bf16* __restrict__ hi,
-                                          bf16* __restrict__ lo, long long ld) {
+                                          const float* __restrict__ GXm, const float* __restrict__ add,
+                                          float* __restrict__ keep, bf16* __restrict__ hi, bf16* __restrict__ lo,
+                                          long long ld) {
   const long long per = N * ld, total = per * batch;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long b = i / per, rem = i - b * per, q = rem / ld, s = rem - q * ld;
     float v = 0.f;
-    if (s < N) v = GX[b * N * N + q * N + s] * GXm[b * N * N + s * N + q];
+    if (s < N) {
+      const long long o = b * N * N + q * N + s;
+      v = GX[o] * GXm[b * N * N + s * N + q];
+      if (add) v += add[o];
+      if (keep) {
+        keep[o] = v;
+        continue;
+      }
+    }
+    if (keep) continue;
     const bf16 h = __float2bfloat16_rn(v);
     hi[i] = h;
     lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
@@ -311,26 +335,29 @@ int launch_split_f64(thc_ctx* ctx, const double* src, long long sb, long long sr
   const long long total = d.rows * d.ld * std::max<long long>(1, d.batch);
   ProfRec rec;
   THC_TRY(prof_begin(ctx, K_SPLIT, 0.0, &rec));
-  split_f64_kernel<<<blocks_for(total), 256, 0, ctx->stream>>>(src, sb, sr, sc, scale, d.hi, d.lo, d.rows, cols, d.ld,
-                                                               std::max<long long>(1, d.batch), d.bs);
+  split_f64_kernel<<<blocks_for(total), 256, 0, ctx->stream>>>(src, sb, sr, sc, scale, d.hi, d.lo, d.lo2, d.rows, cols,
+                                                               d.ld, std::max<long long>(1, d.batch), d.bs);
   return prof_end(ctx, &rec, cudaGetLastError(), what);
 }
 
 // ----------------------------------------------------------- GEMM launch
 // C[b](M x N) = A[b](M x K) B[b](N x K)^T in split precision; epi consumes C.
-template <int BN, bool MULTI, class Epi>
+// AT = 3 multiplies the third term of A as well (A.lo2 must be set).
+template <int BN, bool MULTI, class Epi, int AT = 2>
 int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, const Split& B, bool b_batched,
                       long long M, long long N, long long K, long long batch, const Epi& epi, const char* what) {
   if (M <= 0 || N <= 0 || batch <= 0) return THC_OK;
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX || batch > INT32_MAX)
     return fail(ctx, THC_EINVAL, std::string(what) + ": contraction too large");
-  CUtensorMap ah, al, bh, bl;
+  if (AT == 3 && !A.lo2) return fail(ctx, THC_EINVAL, std::string(what) + ": third operand term missing");
+  CUtensorMap ah, al, al2, bh, bl;
   THC_TRY(make_map(ctx, &ah, A.hi, K, A, tc::BM));
   THC_TRY(make_map(ctx, &al, A.lo, K, A, tc::BM));
+  THC_TRY(make_map(ctx, &al2, AT == 3 ? A.lo2 : A.lo, K, A, tc::BM));
   THC_TRY(make_map(ctx, &bh, B.hi, K, B, BN));
   THC_TRY(make_map(ctx, &bl, B.lo, K, B, BN));
-  auto kern = tc::split_gemm_kernel<BN, MULTI, Epi>;
-  using CfgE = tc::Cfg<BN>;
+  auto kern = tc::split_gemm_kernel<BN, MULTI, AT, Epi>;
+  using CfgE = tc::Cfg<BN, AT>;
   int sms = 0;  // the kernel's shared-memory attribute is set once per device with it
   THC_TRY(per_device(reinterpret_cast<const void*>(kern), &sms, [&](int dev, int* v) {
     THC_TRY(check_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgE::SMEM),
@@ -341,7 +368,7 @@ int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, 
   const dim3 grid((unsigned)std::min<long long>(tiles, sms), 1, 1);  // persistent: one CTA per SM at most
   ProfRec rec;
   THC_TRY(prof_begin(ctx, kclass, 2.0 * M * N * K * batch, &rec));
-  kern<<<grid, tc::NTHREADS, CfgE::SMEM, ctx->stream>>>(ah, al, bh, bl, (int)M, (int)N, (int)K, (int)batch,
+  kern<<<grid, tc::NTHREADS, CfgE::SMEM, ctx->stream>>>(ah, al, al2, bh, bl, (int)M, (int)N, (int)K, (int)batch,
                                                             tc::Operands{a_batched ? 1 : 0, b_batched ? 1 : 0}, epi,
                                                             ctx->d_err);
   return prof_end(ctx, &rec, cudaGetLastError(), what);
@@ -375,6 +402,8 @@ constexpr long long kSingleChunkK = 256;
 template <class Epi>
 int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool bb, long long M, long long N,
          long long K, long long batch, const Epi& epi, const char* what) {
+  if (A.lo2)  // three-term A operand (X or V): promoted, BN = 128 (five operand tiles per stage)
+    return launch_split_gemm<128, true, Epi, 3>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
   if (K > kSingleChunkK) return launch_split_gemm<128, true>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
   const ShapeKey key{kclass, M, N, K, batch};
   int bn = 0;
@@ -411,6 +440,9 @@ int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool
 
 Split split_of(bf16* hi, bf16* lo, long long rows, long long ld, long long batch = 1) {
   return Split{hi, lo, rows, ld, batch, rows * ld};
+}
+Split split3_of(bf16* hi, bf16* lo, bf16* lo2, long long rows, long long ld) {
+  return Split{hi, lo, rows, ld, 1, rows * ld, lo2};
 }
 
 // Fused B and C/D of one tau point and P block (tc::sox_bcd_kernel):
@@ -529,6 +561,9 @@ int split_init(thc_ctx* ctx, size_t budget) {
   THC_TRY(pair(&ctx->Xt_h, &ctx->Xt_l, N * ldn, "Xt"));
   THC_TRY(pair(&ctx->Xs_h, &ctx->Xs_l, n * ldN, "Xs"));
   THC_TRY(pair(&ctx->Vs_h, &ctx->Vs_l, N * ldN, "Vs"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->Xt_l2, h * N * ldn, "Xt third term"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->Xs_l2, h * n * ldN, "Xs third term"));
+  THC_TRY(ctx_alloc(ctx, (void**)&ctx->Vs_l2, h * N * ldN, "Vs third term"));
   // blocking: per tau point and per P of the SOX block
   const size_t per_t = h * 2 * (2 * n * ldn + 2 * N * ldn + 3 * N * ldN + n * ldN) + 4 * 2 * N * N + 8 * N * N;
   const size_t per_p = h * 2 * n * ldn;
@@ -556,9 +591,12 @@ int split_init(thc_ctx* ctx, size_t budget) {
     THC_TRY(pair(&ctx->Ats_h, &ctx->Ats_l, pb * n * ldn, "A^T blocks"));
   }
   // constant operands
-  THC_TRY(launch_split_f64(ctx, ctx->X, 0, 1, N, 1.0, split_of(ctx->Xt_h, ctx->Xt_l, N, ldn), n, "split X^T"));
-  THC_TRY(launch_split_f64(ctx, ctx->X, 0, N, 1, 1.0, split_of(ctx->Xs_h, ctx->Xs_l, n, ldN), N, "split X"));
-  THC_TRY(launch_split_f64(ctx, ctx->V, 0, N, 1, 1.0, split_of(ctx->Vs_h, ctx->Vs_l, N, ldN), N, "split V"));
+  THC_TRY(launch_split_f64(ctx, ctx->X, 0, 1, N, 1.0, split3_of(ctx->Xt_h, ctx->Xt_l, ctx->Xt_l2, N, ldn), n,
+                           "split X^T"));
+  THC_TRY(launch_split_f64(ctx, ctx->X, 0, N, 1, 1.0, split3_of(ctx->Xs_h, ctx->Xs_l, ctx->Xs_l2, n, ldN), N,
+                           "split X"));
+  THC_TRY(launch_split_f64(ctx, ctx->V, 0, N, 1, 1.0, split3_of(ctx->Vs_h, ctx->Vs_l, ctx->Vs_l2, N, ldN), N,
+                           "split V"));
   if (!sox) return THC_OK;
   // U_Pqs = sum_Q V_PQ X_qQ X_sQ over blocks of q with the Khatri-Rao block materialised
   long long qb = std::max<long long>(1, std::min<long long>(n, (long long)(budget / 2 / (h * 2 * n * ldN))));
@@ -571,7 +609,7 @@ int split_init(thc_ctx* ctx, size_t budget) {
     kr_split_kernel<<<blocks_for(nq * n * ldN), 256, 0, ctx->stream>>>(ctx->X, (int)n, (int)N, (int)q0, (int)nq, kh,
                                                                         kl, ldN);
     THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Khatri-Rao block"));
-    THC_TRY(gemm(ctx, K_UBUILD, split_of(ctx->Vs_h, ctx->Vs_l, N, ldN), false, split_of(kh, kl, nq * n, ldN), false,
+    THC_TRY(gemm(ctx, K_UBUILD, split3_of(ctx->Vs_h, ctx->Vs_l, ctx->Vs_l2, N, ldN), false, split_of(kh, kl, nq * n, ldN), false,
                  N, nq * n, N, 1, EpiU{ctx->Us_h, ctx->Us_l, (int)n, (int)q0, ldn}, "U build"));
   }
   // the Khatri-Rao block is released at init's end; keep the stream ordered first
@@ -588,77 +626,131 @@ int split_init(thc_ctx* ctx, size_t budget) {
 }
 
 // ------------------------------------------------------------------ eval
-int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
-  const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau, ldn = ctx->ldn, ldN = ctx->ldN;
-  const long long nn = n * n, NN = N * N;
+namespace {
+
+// Split G(tau_k) and G(-tau_k) = -G(beta - tau_k) of one spin and chunk, then Y = X^T G(tau),
+// and with the direct term Ym = X^T G(-tau) and G^X(+-tau) (G^X(-tau) only when need_minus).
+int split_project(thc_ctx* ctx, const double* G_tau, const double* G_bmt, long long c0, long long tc, bool dir,
+                  bool need_minus) {
+  const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau, ldn = ctx->ldn, nn = n * n, NN = N * N;
+  const Split Xt = split3_of(ctx->Xt_h, ctx->Xt_l, ctx->Xt_l2, N, ldn);
+  const Split Gs = split_of(ctx->Gs_h, ctx->Gs_l, n, ldn, tc);
+  const Split Gms = split_of(ctx->Gms_h, ctx->Gms_l, n, ldn, tc);
+  const Split Ys = split_of(ctx->Ys_h, ctx->Ys_l, N, ldn, tc);
+  const Split Yms = split_of(ctx->Yms_h, ctx->Yms_l, N, ldn, tc);
+  THC_TRY(launch_split_f64(ctx, G_tau + c0 * nn, nn, n, 1, 1.0, Gs, n, "split G"));
+  if (G_bmt)
+    THC_TRY(launch_split_f64(ctx, G_bmt + c0 * nn, nn, n, 1, -1.0, Gms, n, "split G(-tau)"));
+  else
+    THC_TRY(launch_split_f64(ctx, G_tau + (nt - 1 - c0) * nn, -nn, n, 1, -1.0, Gms, n, "split G(-tau)"));
+  THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Gs, true, N, n, n, tc, EpiSplit<false>{Ys.hi, Ys.lo, ldn, N * ldn, 1.f},
+               "Y"));
+  if (!dir) return THC_OK;
+  if (need_minus)
+    THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Gms, true, N, n, n, tc,
+                 EpiSplit<false>{Yms.hi, Yms.lo, ldn, N * ldn, 1.f}, "Ym"));
+  // G^X[P][R] = sum_q X^T[P][q] Y[R][q] (X as the three-term A operand)
+  THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Ys, true, N, N, n, tc, EpiF32{ctx->GXf, N, NN}, "G^X"));
+  if (need_minus)
+    THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Yms, true, N, N, n, tc, EpiF32{ctx->GXmf, N, NN}, "G^X(-)"));
+  return THC_OK;
+}
+
+// Pi from G^X(+-tau) (+ add, FP32) into the split Pi operand, or kept in FP32 (keep).
+int split_polarisation(thc_ctx* ctx, long long tc, const float* add, float* keep) {
+  const long long N = ctx->N, ldN = ctx->ldN;
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, K_POLARISATION, 0.0, &rec));
+  polarisation_split_kernel<<<blocks_for(tc * N * ldN), 256, 0, ctx->stream>>>(N, tc, ctx->GXf, ctx->GXmf, add, keep,
+                                                                               ctx->Pis_h, ctx->Pis_l, ldN);
+  return prof_end(ctx, &rec, cudaGetLastError(), "polarisation");
+}
+
+// D_PR of the chunk from the split Y and G(-tau) of one spin (fused B and C/D, P <= R, mirrored).
+int split_sox(thc_ctx* ctx, long long tc) {
+  const long long n = ctx->n, N = ctx->N, ldn = ctx->ldn, NN = N * N;
+  const Split Gms = split_of(ctx->Gms_h, ctx->Gms_l, n, ldn, tc);
+  const Split Ys = split_of(ctx->Ys_h, ctx->Ys_l, N, ldn, tc);
+  THC_TRY(check_cuda(ctx, cudaMemsetAsync(ctx->Dd, 0, 8 * tc * NN, ctx->stream), "clear D"));
+  const Split U = split_of(ctx->Us_h, ctx->Us_l, N * n, ldn);
+  for (long long k = 0; k < tc; ++k) {
+    const Split Gmk = Gms.at_batch(k, 1);
+    const Split Yk = Ys.at_batch(k, 1);
+    double* Dk = ctx->Dd + k * NN;
+    for (long long P0 = 0; P0 < N; P0 += ctx->Pb) {
+      const long long Pc = std::min<long long>(ctx->Pb, N - P0);
+      const Split At = Split{ctx->Ats_h, ctx->Ats_l, n, ldn, Pc, n * ldn};
+      // A^T_P[v][q] = sum_s U[P q][s] G(-tau)[v][s]  (G(-tau) carries its sign in Gms)
+      THC_TRY(gemm(ctx, K_SOX_A, U.at_row(P0 * n, Pc * n), false, Gmk, false, Pc * n, n, n, 1,
+                   EpiAt{At.hi, At.lo, (int)n, ldn}, "A"));
+      // D[P][R] += sum_v (sum_w Y[P][w] U[R][v][w]) (sum_q Y[R][q] A^T_P[v][q])  (B and C never stored)
+      THC_TRY(launch_bcd(ctx, Yk, U, At, P0, Pc, Dk));
+    }
+  }
+  return launch_mirror_upper(ctx, ctx->Dd, N, tc);  // D_PR = D_RP: fill P > R
+}
+
+// M (merge of D and the direct term with T = V Pi in Ts, or D alone), then Sigma = X M X^T.
+int split_merge_back(thc_ctx* ctx, long long tc, bool sox, bool dir, double cd, double* Sigma_chunk) {
+  const long long n = ctx->n, N = ctx->N, ldN = ctx->ldN, nn = n * n, NN = N * N;
+  const Split Xs = split3_of(ctx->Xs_h, ctx->Xs_l, ctx->Xs_l2, n, ldN);
+  const Split Vs = split3_of(ctx->Vs_h, ctx->Vs_l, ctx->Vs_l2, N, ldN);
+  const Split Ts = split_of(ctx->Ts_h, ctx->Ts_l, N, ldN, tc);
+  const Split Ms = split_of(ctx->Ms_h, ctx->Ms_l, N, ldN, tc);
+  const Split T2s = split_of(ctx->T2s_h, ctx->T2s_l, n, ldN, tc);
+  if (dir) {
+    // W[P][R] = sum_S V[P][S] T[R][S] = (V Pi V)[P][R], symmetric, so the merge epilogue
+    // reads the tile as W[R][P]
+    THC_TRY(gemm(ctx, K_DIRECT_W, Vs, false, Ts, true, N, N, N, tc,
+                 EpiMerge{Ms.hi, Ms.lo, ldN, sox ? ctx->Dd : nullptr, ctx->GXf, (int)N, cd}, "W"));
+  } else {
+    // M[R][P] = c_x D[P][R]
+    THC_TRY(launch_split_f64(ctx, ctx->Dd, NN, 1, N, C_SOX, Ms, N, "split D^T"));
+  }
+  // T2t[r][R] = sum_P X[r][P] M[R][P]
+  THC_TRY(gemm(ctx, K_BACK, Xs, false, Ms, true, n, N, N, tc, EpiSplit<false>{T2s.hi, T2s.lo, ldN, n * ldN, 1.f},
+               "M X^T"));
+  return gemm(ctx, K_BACK, Xs, false, T2s, true, n, n, N, tc, EpiF64{Sigma_chunk, n, nn}, "X T2");
+}
+
+}  // namespace
+
+// Restricted (nspin = 1) or unrestricted (nspin = 2) evaluation; the steps and their order
+// are those of fp64_eval_spins.  The polarisation of spin b is kept in FP32 (Pif) and added
+// to that of spin a before the split of Pi.
+int split_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const double* const* G_bmt,
+                     double* const* Sigma) {
+  const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau, ldN = ctx->ldN, nn = n * n;
   const bool sox = ctx->terms & THC_SOX, dir = ctx->terms & THC_DIRECT;
-  const Split Xt = split_of(ctx->Xt_h, ctx->Xt_l, N, ldn);
-  const Split Xs = split_of(ctx->Xs_h, ctx->Xs_l, n, ldN);
-  const Split Vs = split_of(ctx->Vs_h, ctx->Vs_l, N, ldN);
+  const double cd = nspin == 1 ? C_DIRECT : -1.0;
+  if (nspin == 2 && dir && !ctx->Pif)
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->Pif, sizeof(float) * (size_t)ctx->tc * N * N, "Pi of spin b"));
+  const Split Vs = split3_of(ctx->Vs_h, ctx->Vs_l, ctx->Vs_l2, N, ldN);
   for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
     const long long tc = std::min<long long>(ctx->tc, nt - c0);
-    const Split Gs = split_of(ctx->Gs_h, ctx->Gs_l, n, ldn, tc);
-    const Split Gms = split_of(ctx->Gms_h, ctx->Gms_l, n, ldn, tc);
-    const Split Ys = split_of(ctx->Ys_h, ctx->Ys_l, N, ldn, tc);
-    const Split Yms = split_of(ctx->Yms_h, ctx->Yms_l, N, ldn, tc);
     const Split Pis = split_of(ctx->Pis_h, ctx->Pis_l, N, ldN, tc);
     const Split Ts = split_of(ctx->Ts_h, ctx->Ts_l, N, ldN, tc);
-    const Split Ms = split_of(ctx->Ms_h, ctx->Ms_l, N, ldN, tc);
-    const Split T2s = split_of(ctx->T2s_h, ctx->T2s_l, n, ldN, tc);
-    // G(tau_k) and G(-tau_k) = -G(beta - tau_k) as split operands
-    THC_TRY(launch_split_f64(ctx, G_tau + c0 * nn, nn, n, 1, 1.0, Gs, n, "split G"));
-    if (G_bmt)
-      THC_TRY(launch_split_f64(ctx, G_bmt + c0 * nn, nn, n, 1, -1.0, Gms, n, "split G(-tau)"));
-    else
-      THC_TRY(launch_split_f64(ctx, G_tau + (nt - 1 - c0) * nn, -nn, n, 1, -1.0, Gms, n, "split G(-tau)"));
-    // Y = X^T G(tau), Ym = X^T G(-tau)
-    THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Gs, true, N, n, n, tc,
-                 EpiSplit<false>{Ys.hi, Ys.lo, ldn, N * ldn, 1.f}, "Y"));
+    if (nspin == 2 && dir) {
+      THC_TRY(split_project(ctx, G_tau[1], G_bmt[1], c0, tc, true, true));
+      THC_TRY(split_polarisation(ctx, tc, nullptr, ctx->Pif));
+    }
+    THC_TRY(split_project(ctx, G_tau[0], G_bmt[0], c0, tc, dir, true));
     if (dir) {
-      THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Gms, true, N, n, n, tc,
-                   EpiSplit<false>{Yms.hi, Yms.lo, ldn, N * ldn, 1.f}, "Ym"));
-      THC_TRY(gemm(ctx, K_PROJECT, Ys, true, Xt, false, N, N, n, tc, EpiF32{ctx->GXf, N, NN}, "G^X"));
-      THC_TRY(gemm(ctx, K_PROJECT, Yms, true, Xt, false, N, N, n, tc, EpiF32{ctx->GXmf, N, NN}, "G^X(-)"));
-      ProfRec rec;
-      THC_TRY(prof_begin(ctx, K_POLARISATION, 0.0, &rec));
-      polarisation_split_kernel<<<blocks_for(tc * N * ldN), 256, 0, ctx->stream>>>(N, tc, ctx->GXf, ctx->GXmf,
-                                                                                   Pis.hi, Pis.lo, ldN);
-      THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "polarisation"));
+      THC_TRY(split_polarisation(ctx, tc, nspin == 2 ? ctx->Pif : nullptr, nullptr));
       THC_TRY(gemm(ctx, K_DIRECT_VPI, Vs, false, Pis, true, N, N, N, tc,
                    EpiSplit<false>{Ts.hi, Ts.lo, ldN, N * ldN, 1.f}, "V Pi"));
     }
-    if (sox) {
-      THC_TRY(check_cuda(ctx, cudaMemsetAsync(ctx->Dd, 0, 8 * tc * NN, ctx->stream), "clear D"));
-      const Split U = split_of(ctx->Us_h, ctx->Us_l, N * n, ldn);
-      for (long long k = 0; k < tc; ++k) {
-        const Split Gmk = Gms.at_batch(k, 1);
-        const Split Yk = Ys.at_batch(k, 1);
-        double* Dk = ctx->Dd + k * NN;
-        for (long long P0 = 0; P0 < N; P0 += ctx->Pb) {
-          const long long Pc = std::min<long long>(ctx->Pb, N - P0);
-          const Split At = Split{ctx->Ats_h, ctx->Ats_l, n, ldn, Pc, n * ldn};
-          // A^T_P[v][q] = sum_s U[P q][s] G(-tau)[v][s]  (G(-tau) carries its sign in Gms)
-          THC_TRY(gemm(ctx, K_SOX_A, U.at_row(P0 * n, Pc * n), false, Gmk, false, Pc * n, n, n, 1,
-                       EpiAt{At.hi, At.lo, (int)n, ldn}, "A"));
-          // D[P][R] += sum_v (sum_w Y[P][w] U[R][v][w]) (sum_q Y[R][q] A^T_P[v][q])  (B and C never stored)
-          THC_TRY(launch_bcd(ctx, Yk, U, At, P0, Pc, Dk));
-        }
-      }
-      THC_TRY(launch_mirror_upper(ctx, ctx->Dd, N, tc));  // D_PR = D_RP: fill P > R
+    for (int s = 0; s < nspin; ++s) {
+      if (s == 1) THC_TRY(split_project(ctx, G_tau[1], G_bmt[1], c0, tc, dir, false));
+      if (sox) THC_TRY(split_sox(ctx, tc));
+      THC_TRY(split_merge_back(ctx, tc, sox, dir, cd, Sigma[s] + c0 * nn));
     }
-    // merged M, back-transform
-    if (dir) {
-      THC_TRY(gemm(ctx, K_DIRECT_W, Ts, true, Vs, false, N, N, N, tc,
-                   EpiMerge{Ms.hi, Ms.lo, ldN, sox ? ctx->Dd : nullptr, ctx->GXf, (int)N}, "W"));
-    } else {
-      // M[R][P] = c_x D[P][R]
-      THC_TRY(launch_split_f64(ctx, ctx->Dd, NN, 1, N, C_SOX, Ms, N, "split D^T"));
-    }
-    THC_TRY(gemm(ctx, K_BACK, Ms, true, Xs, false, N, n, N, tc, EpiSplit<true>{T2s.hi, T2s.lo, ldN, n * ldN, 1.f},
-                 "M X^T"));
-    THC_TRY(gemm(ctx, K_BACK, Xs, false, T2s, true, n, n, N, tc, EpiF64{Sigma + c0 * nn, n, nn}, "X T2"));
   }
   return THC_OK;
+}
+
+int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
+  return split_eval_spins(ctx, 1, &G_tau, &G_bmt, &Sigma);
 }
 
 // ------------------------------------------------------- autotuner cache

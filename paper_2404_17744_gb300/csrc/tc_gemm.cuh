@@ -4,7 +4,10 @@
 //             ~= sum_k (Ahi Bhi + Ahi Blo + Alo Bhi)       (FP32 accumulation in TMEM)
 //
 // with every FP64 operand x stored as a pair of BF16 values hi = bf16(x),
-// lo = bf16(x - hi) (about 17 significant bits together).  Both operands are
+// lo = bf16(x - hi) (about 17 significant bits together).  The constant
+// operands X and V may carry a third term lo2 = bf16(x - hi - lo) (AT = 3,
+// one more product Alo2 Bhi per step): their rounding is coherent across the
+// whole scheme and otherwise dominates the error of the energy.  Both operands are
 // K-major (k contiguous), which every contraction of the THC scheme can be
 // brought to by the symmetry of G, U_Pqs and V or by writing its producer's
 // output transposed.
@@ -17,8 +20,9 @@
 // ahead into the two TMEM stage buffers during the store phase.
 // Each tile is 128 x BN, computed by three warp roles:
 //   warp 0    one lane issues the TMA loads (128-byte swizzle) of the four
-//             operand tiles of each 64-deep K stage into a STAGES-deep ring;
-//   warp 1    allocates TMEM; one lane issues the 3 x 4 tcgen05.mma
+//             (AT = 3: five) operand tiles of each 64-deep K stage into a
+//             STAGES-deep ring;
+//   warp 1    allocates TMEM; one lane issues the (AT + 1) x 4 tcgen05.mma
 //             (kind::f16, M = 128, N = BN, K = 16) of a stage into one of two
 //             TMEM accumulators (stages alternate between them) and commits
 //             the stage back to the producer and to the epilogue (ragged
@@ -31,15 +35,21 @@
 //             tile, to the epilogue functor, which the whole warp runs with
 //             coalesced global accesses.
 // Draining every stage ("promotion") keeps the tensor core's internal
-// accumulation to one 64-deep stage: measured on GB300, accumulating a
-// 1000-deep K inside the tensor core loses several times more precision than
-// IEEE FP32 additions of 64-deep partial sums, enough to break a 1e-6
-// absolute bound on the self-energy.  Up to K = 256 the in-TMEM accumulation
-// measured as accurate as promotion, so contractions that short run in the
-// single-chunk mode (MULTI = false): the whole K accumulates in one TMEM
-// buffer, tiles alternate between the two buffers (the epilogue of one tile
-// overlaps the MMAs of the next), and the epilogue streams 32-column slices
-// straight from TMEM without a register accumulator.
+// accumulation to one 64-deep stage.  Measured on GB300 with exactly
+// representable products, the FP32 accumulator is rounded toward zero after
+// every MMA instruction: sums of one sign lose about a quarter ulp per
+// instruction, a bias that grows with the number of instructions accumulated in
+// TMEM (-2.7e-7 relative at K = 200 in one chunk, -7.7e-8 for 64-deep stages
+// added in FP32 registers) and that the chained contractions of the direct term
+// carry into the energy.  The promoted mode therefore also keeps the hi*hi
+// products and the 2^-8 smaller correction products in separate TMEM
+// accumulators (their truncation then scales with their own magnitude), and it
+// runs every contraction with the three-term operands X and V (K from n to N).
+// The remaining contractions (the SOX A step) run in the single-chunk mode
+// (MULTI = false): the whole K accumulates in one TMEM buffer, tiles alternate
+// between the two buffers (the epilogue of one tile overlaps the MMAs of the
+// next), and the epilogue streams 32-column slices straight from TMEM without a
+// register accumulator.
 // Every mbarrier wait is bounded in time (globaltimer); a wait that runs out
 // sets *err and the CTA unwinds: the producer waits (bounded) for every TMA
 // stage it issued, the MMA lane commits its outstanding MMAs to a drain
@@ -61,12 +71,18 @@ constexpr int NTHREADS = 320;  // 10 warps: TMA, MMA, 8 epilogue
 constexpr int NEPI = 256;      // epilogue threads
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s per wait
 
-template <int BN>
+// AT = number of BF16 terms of the A operand: 2 (hi, lo) or 3 (hi, lo, lo2 =
+// bf16(x - hi - lo), about 24 significant bits together, for the constant
+// operands X and V whose rounding otherwise dominates the energy error).
+template <int BN, int AT = 2>
 struct Cfg {
   static constexpr int A_BYTES = BM * BKE * 2;
   static constexpr int B_BYTES = BN * BKE * 2;
-  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int STAGE = AT * A_BYTES + 2 * B_BYTES;
   static constexpr int TMEM_COLS = 2 * BN;   // two accumulators; BN in {128, 256}
+  // promoted mode: each of the two stage buffers holds the hi*hi products and, in a second
+  // accumulator, the small correction products (BN = 128 only)
+  static constexpr int TMEM_COLS_MULTI = 4 * BN;
   static constexpr int HALF = BN / 2;         // columns per epilogue thread
   static constexpr int STAGING = 8 * 32 * 32 * 4;  // one swizzled 32 x 32 FP32 tile per warp
   static constexpr int FIXED = STAGING + 1024 /*align*/ + 256 /*barriers*/;
@@ -74,6 +90,7 @@ struct Cfg {
   static constexpr int SMEM = STAGES * STAGE + FIXED;
   static_assert(SMEM <= 232448, "shared memory per CTA");
   static_assert(BN == 128 || BN == 256, "tile width");
+  static_assert(AT == 2 || AT == 3, "A operand terms");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -232,12 +249,16 @@ struct Operands {
   int a_batched, b_batched;
 };
 
-template <int BN, bool MULTI, class Epi>
+template <int BN, bool MULTI, int AT, class Epi>
 __global__ void __launch_bounds__(NTHREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
-                      const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, int M,
-                      int N, int K, int batch, Operands ops, Epi epi, int* err) {
-  using C = Cfg<BN>;
+                      const __grid_constant__ CUtensorMap mAlo2, const __grid_constant__ CUtensorMap mBhi,
+                      const __grid_constant__ CUtensorMap mBlo, int M, int N, int K, int batch, Operands ops, Epi epi,
+                      int* err) {
+  using C = Cfg<BN, AT>;
+  constexpr int B_OFF = AT * C::A_BYTES;  // B hi, then B lo, after the A terms of a stage
+  constexpr int TCOLS = MULTI ? C::TMEM_COLS_MULTI : C::TMEM_COLS;
+  static_assert(TCOLS <= 512, "TMEM columns");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* staging = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE);
@@ -266,11 +287,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     fence_mbar_init();
     prefetch_map(&mAhi);
     prefetch_map(&mAlo);
+    if (AT == 3) prefetch_map(&mAlo2);
     prefetch_map(&mBhi);
     prefetch_map(&mBlo);
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, C::TMEM_COLS);
+    tmem_alloc(tmem_slot, TCOLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -297,8 +319,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           mbar_arrive_expect_tx(&full[s], C::STAGE);
           tma_load_3d(st, &mAhi, &full[s], kb * BKE, mt * BM, ab);
           tma_load_3d(st + C::A_BYTES, &mAlo, &full[s], kb * BKE, mt * BM, ab);
-          tma_load_3d(st + 2 * C::A_BYTES, &mBhi, &full[s], kb * BKE, nt * BN, bb);
-          tma_load_3d(st + 2 * C::A_BYTES + C::B_BYTES, &mBlo, &full[s], kb * BKE, nt * BN, bb);
+          if (AT == 3) tma_load_3d(st + 2 * C::A_BYTES, &mAlo2, &full[s], kb * BKE, mt * BM, ab);
+          tma_load_3d(st + B_OFF, &mBhi, &full[s], kb * BKE, nt * BN, bb);
+          tma_load_3d(st + B_OFF + C::B_BYTES, &mBlo, &full[s], kb * BKE, nt * BN, bb);
         }
       }
       // every copy issued has landed before the CTA may leave (immediate unless a wait ran out)
@@ -331,10 +354,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t d = tmem + static_cast<uint32_t>(buf * BN);
+          // single-chunk: one accumulator per buffer; promoted: hi*hi into d, corrections into dc
+          const uint32_t d = tmem + static_cast<uint32_t>(buf * (MULTI ? 2 * BN : BN));
+          const uint32_t dc = MULTI ? d + BN : d;
           const uint32_t base = smem_u32(smem + s * C::STAGE);
           const uint64_t ah = sw128_desc(base), al = sw128_desc(base + C::A_BYTES);
-          const uint64_t bh = sw128_desc(base + 2 * C::A_BYTES), bl = sw128_desc(base + 2 * C::A_BYTES + C::B_BYTES);
+          const uint64_t al2 = sw128_desc(base + 2 * C::A_BYTES);
+          const uint64_t bh = sw128_desc(base + B_OFF), bl = sw128_desc(base + B_OFF + C::B_BYTES);
           // the last stage of a ragged K issues only the 16-deep steps that reach below K
           const int ksteps = min(BKE / 16, (K - kb * BKE + 15) >> 4);
 #pragma unroll
@@ -342,8 +368,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (k < ksteps) {
               const uint64_t off = static_cast<uint64_t>((k * 32) >> 4);  // 16 BF16 = 32 bytes along K
               mma_bf16(d, ah + off, bh + off, idesc, (MULTI ? k : (kb | k)) != 0);
-              mma_bf16(d, ah + off, bl + off, idesc, 1u);
-              mma_bf16(d, al + off, bh + off, idesc, 1u);
+              mma_bf16(dc, ah + off, bl + off, idesc, MULTI ? (k != 0) : 1u);
+              mma_bf16(dc, al + off, bh + off, idesc, 1u);
+              if (AT == 3) mma_bf16(dc, al2 + off, bh + off, idesc, 1u);
             }
           }
           mma_commit(&empty[s]);  // frees the smem stage once these MMAs have read it
@@ -406,13 +433,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         tc_fence_after();
-        {  // all loads of the stage in flight, one wait
-          uint32_t r[C::HALF];
+        // the stage's hi*hi sum and its correction sum, 32 columns of each at a time
 #pragma unroll
-          for (int c = 0; c < C::HALF; c += 16) tmem_ld16(lane_base + buf * BN + c, r + c);
+        for (int c0 = 0; c0 < C::HALF; c0 += 32) {
+          uint32_t r[32], q[32];
+          const uint32_t src = lane_base + buf * 2 * BN + c0;
+          tmem_ld16(src, r);
+          tmem_ld16(src + 16, r + 16);
+          tmem_ld16(src + BN, q);
+          tmem_ld16(src + BN + 16, q + 16);
           tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < C::HALF; ++i) acc[i] += __uint_as_float(r[i]);
+          for (int i = 0; i < 32; ++i) acc[c0 + i] += __uint_as_float(r[i]) + __uint_as_float(q[i]);
         }
         tc_fence_before();
         mbar_arrive(&acc_free[buf]);
@@ -435,7 +467,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, C::TMEM_COLS);
+    tmem_dealloc(tmem, TCOLS);
   }
 }
 

@@ -285,6 +285,31 @@ int thc_sigma_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, doubl
   }
 }
 
+int thc_sigma_eval_uhf(thc_ctx* ctx, const double* G_tau_a, const double* G_bmt_a, const double* G_tau_b,
+                       const double* G_bmt_b, double* Sigma_a, double* Sigma_b) {
+  using namespace thc;
+  if (!ctx) return fail(nullptr, THC_EINVAL, "ctx is NULL");
+  if (!G_tau_a || !G_tau_b || !Sigma_a || !Sigma_b) return fail(ctx, THC_EINVAL, "NULL argument to thc_sigma_eval_uhf");
+  if ((!G_bmt_a || !G_bmt_b) && !ctx->mirrored)
+    return fail(ctx, THC_EINVAL, "tau grid is not mirror-symmetric: pass G_bmt for both spins");
+  const double* in[4] = {G_tau_a, G_bmt_a, G_tau_b, G_bmt_b};
+  for (const double* p : in)
+    if (p && (p == Sigma_a || p == Sigma_b)) return fail(ctx, THC_EINVAL, "a Sigma output aliases an input");
+  if (Sigma_a == Sigma_b) return fail(ctx, THC_EINVAL, "Sigma_a and Sigma_b must differ");
+  const long long len = (long long)ctx->n_tau * ctx->n * ctx->n;
+  for (const double* p : in)
+    if (p) THC_TRY(launch_finite_scan(ctx, p, len, ctx->d_err + 1));
+  const double* G[2] = {G_tau_a, G_tau_b};
+  const double* Gb[2] = {G_bmt_a, G_bmt_b};
+  double* S[2] = {Sigma_a, Sigma_b};
+  try {
+    if (ctx->precision == THC_FP64) return fp64_eval_spins(ctx, 2, G, Gb, S);
+    return split_eval_spins(ctx, 2, G, Gb, S);
+  } catch (...) {
+    return fail(ctx, THC_ENOMEM, "host allocation failed during eval");
+  }
+}
+
 int thc_sigma_eval_host(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma_tau) {
   using namespace thc;
   if (!ctx) return fail(nullptr, THC_EINVAL, "ctx is NULL");

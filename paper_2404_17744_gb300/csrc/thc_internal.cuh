@@ -72,9 +72,10 @@ struct thc_ctx {
 
   // split-precision (THC_BF16X3) path: BF16 hi/lo pairs, leading dimensions padded to 8
   int ldn = 0, ldN = 0;                       // padded n and N
-  __nv_bfloat16 *Xt_h = nullptr, *Xt_l = nullptr;   // X^T, N x ldn
-  __nv_bfloat16 *Xs_h = nullptr, *Xs_l = nullptr;   // X,   n x ldN
-  __nv_bfloat16 *Vs_h = nullptr, *Vs_l = nullptr;   // V,   N x ldN
+  // the constant operands X and V carry a third term (x = hi + lo + lo2 to about 24 bits)
+  __nv_bfloat16 *Xt_h = nullptr, *Xt_l = nullptr, *Xt_l2 = nullptr;   // X^T, N x ldn
+  __nv_bfloat16 *Xs_h = nullptr, *Xs_l = nullptr, *Xs_l2 = nullptr;   // X,   n x ldN
+  __nv_bfloat16 *Vs_h = nullptr, *Vs_l = nullptr, *Vs_l2 = nullptr;   // V,   N x ldN
   __nv_bfloat16 *Us_h = nullptr, *Us_l = nullptr;   // U,   (N n) x ldn
   __nv_bfloat16 *Gs_h = nullptr, *Gs_l = nullptr;   // G(tau),  tc x n x ldn
   __nv_bfloat16 *Gms_h = nullptr, *Gms_l = nullptr; // G(-tau), tc x n x ldn
@@ -87,6 +88,7 @@ struct thc_ctx {
   __nv_bfloat16 *T2s_h = nullptr, *T2s_l = nullptr; // (M X^T)^T, tc x n x ldN
   __nv_bfloat16 *Ats_h = nullptr, *Ats_l = nullptr; // A^T blocks, Pb x n x ldn
   double *Dd = nullptr;                             // D, tc x N x N
+  float *Pif = nullptr;                             // Pi of spin b, tc x N x N (unrestricted only)
   // device status words: [0] a tensor-core pipeline wait that ran out (its code),
   // [1] a non-finite value met in G_tau / G_bmt by an evaluation; read and cleared by status_check
   int *d_err = nullptr;
@@ -127,6 +129,9 @@ void prof_release(thc_ctx* ctx);
 size_t fp64_workspace_bytes(int n, int N, int tc, int Pb);
 int fp64_build_U(thc_ctx* ctx);
 int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma);
+// nspin = 1: restricted; nspin = 2: unrestricted spins a (index 0) and b (index 1)
+int fp64_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const double* const* G_bmt,
+                    double* const* Sigma);
 // D[b][P][R] = D[b][R][P] for P > R, b < batch (D_PR is symmetric; both paths compute P <= R)
 int launch_mirror_upper(thc_ctx* ctx, double* D, long long N, long long batch);
 int energy_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const double* Sigma,
@@ -146,6 +151,8 @@ int autotune_entries();
 // split-precision path (sigma_split.cu)
 int split_init(thc_ctx* ctx, size_t budget);
 int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma);
+int split_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const double* const* G_bmt,
+                     double* const* Sigma);
 // Synchronises and reads the status words: THC_ETIMEOUT if a tensor-core wait ran out,
 // THC_EINVAL if an evaluation met a non-finite input; both are cleared.
 int status_check(thc_ctx* ctx);

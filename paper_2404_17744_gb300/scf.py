@@ -42,7 +42,7 @@ class GF2Loop:
     """
 
     def __init__(self, X, V, F, S, grid, n_elec, precision=thc.THC_FP64, device="cuda:0", stream=None,
-                 damping=0.5, n_damp=2, diis_size=6):
+                 damping=0.5, n_damp=2, diis_size=6, mixing="diis"):
         import torch
         self.torch = torch
         self.dev = torch.device(device)
@@ -52,6 +52,9 @@ class GF2Loop:
         self.n_tau = len(grid.tau)
         self.n_elec = float(n_elec)
         self.damping, self.n_damp, self.diis_size = damping, n_damp, min(diis_size, 16)
+        if mixing not in ("diis", "cdiis", "damp"):
+            raise ValueError("mixing must be 'diis', 'cdiis' or 'damp'")
+        self.mixing = mixing
         with torch.cuda.stream(self.stream):
             self.X = torch.from_numpy(np.ascontiguousarray(X)).to(self.dev)
             self.V = torch.from_numpy(np.ascontiguousarray(V)).to(self.dev)
@@ -91,7 +94,7 @@ class GF2Loop:
         return self.n_tau * self.n * self.n
 
     def _dot(self, a, b):
-        return thc.thc_vec_dot(self._len(), a, b, self.scratch, self.stream.cuda_stream)
+        return thc.thc_vec_dot(a.numel(), a, b, self.scratch, self.stream.cuda_stream)
 
     def _lincomb(self, coeffs, vecs, out):
         thc.thc_vec_lincomb(coeffs, vecs, self._len(), out, self.stream.cuda_stream)
@@ -109,16 +112,24 @@ class GF2Loop:
         return 2.0 * trgf + e_dyn, e_dyn, n
 
     def mix(self, it):
-        """Next input self-energy from the history (damping, then DIIS)."""
+        """Next input self-energy from the history: damping, then DIIS on the residual
+        Sigma_out - Sigma_in ("diis"), on the frequency-dependent commutator residual
+        H G S - S G H of thc_dyson_commutator ("cdiis", Sec. III.A), or damping only
+        ("damp").  The returned residual norm is that of Sigma_out - Sigma_in in every mode."""
         torch = self.torch
         with torch.cuda.stream(self.stream):
             r = torch.empty_like(self.G)
         self._lincomb([1.0, -1.0], [self.Sig_out, self.Sig_in], r)
+        res = float(np.sqrt(self._dot(r, r)))
+        if self.mixing == "cdiis":
+            with torch.cuda.stream(self.stream):
+                e = torch.empty((len(self.grid.iw), self.n, self.n, 2), dtype=torch.float64, device=self.dev)
+            thc.thc_dyson_commutator(self.dy, self.Sig_out, e)
+            r = e
         out = self.Sig_out.clone()
         self.history.append((out, r))
         self.history = self.history[-self.diis_size:]
-        res = float(np.sqrt(self._dot(r, r)))
-        if it <= self.n_damp:
+        if it <= self.n_damp or self.mixing == "damp":
             a = self.damping
             self._lincomb([a, 1.0 - a], [self.Sig_out, self.Sig_in], self.Sig_in)
             return res

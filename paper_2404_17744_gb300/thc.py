@@ -50,6 +50,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_sigma_init.restype = i
     lib.thc_sigma_eval.argtypes = [vp, dp, dp, dp]
     lib.thc_sigma_eval.restype = i
+    lib.thc_sigma_eval_uhf.argtypes = [vp, dp, dp, dp, dp, dp, dp]
+    lib.thc_sigma_eval_uhf.restype = i
     lib.thc_sigma_eval_host.argtypes = [vp, dp, dp, dp]
     lib.thc_sigma_eval_host.restype = i
     lib.thc_energy.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(d)]
@@ -85,6 +87,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_dyson_energy.restype = i
     lib.thc_dyson_evals.argtypes = [vp]
     lib.thc_dyson_evals.restype = i
+    lib.thc_dyson_count.argtypes = [vp, dp, d, ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.thc_dyson_count.restype = i
+    lib.thc_dyson_commutator.argtypes = [vp, dp, dp]
+    lib.thc_dyson_commutator.restype = i
     lib.thc_dyson_last_error.argtypes = [vp]
     lib.thc_dyson_last_error.restype = ctypes.c_char_p
     lib.thc_dyson_destroy.argtypes = [vp]
@@ -193,6 +199,11 @@ def thc_sigma_init(n_ao, n_thc, n_tau, beta, X, V, tau, precision=THC_FP64,
 
 def thc_sigma_eval(ctx, G_tau, G_bmt, Sigma_tau):
     _check(load_library().thc_sigma_eval(ctx, _ptr(G_tau), _ptr(G_bmt), _ptr(Sigma_tau)), ctx)
+
+
+def thc_sigma_eval_uhf(ctx, G_tau_a, G_bmt_a, G_tau_b, G_bmt_b, Sigma_a, Sigma_b):
+    _check(load_library().thc_sigma_eval_uhf(ctx, _ptr(G_tau_a), _ptr(G_bmt_a), _ptr(G_tau_b), _ptr(G_bmt_b),
+                                             _ptr(Sigma_a), _ptr(Sigma_b)), ctx)
 
 
 def thc_sigma_eval_host(ctx, G_tau, G_bmt, Sigma_tau):
@@ -310,6 +321,18 @@ def thc_dyson_energy(d, G_tau, Sigma_tau):
     _dcheck(load_library().thc_dyson_energy(d, _ptr(G_tau), _ptr(Sigma_tau), ctypes.byref(e), ctypes.byref(f),
                                             ctypes.byref(n)), d)
     return e.value, f.value, n.value
+
+
+def thc_dyson_count(d, Sigma_tau, mu):
+    """(N(mu), dN/dmu) per spin at fixed Sigma."""
+    n, dn = ctypes.c_double(), ctypes.c_double()
+    _dcheck(load_library().thc_dyson_count(d, _ptr(Sigma_tau), float(mu), ctypes.byref(n), ctypes.byref(dn)), d)
+    return n.value, dn.value
+
+
+def thc_dyson_commutator(d, Sigma_out_tau, E_iw):
+    """E_iw (dev, n_iw x n x n x 2 float64) <- H G S - S G H with H = F + Sigma_out(i w)."""
+    _dcheck(load_library().thc_dyson_commutator(d, _ptr(Sigma_out_tau), _ptr(E_iw)), d)
 
 
 def thc_dyson_evals(d) -> int:

@@ -153,3 +153,59 @@ def test_split_loop_reaches_fp64_energy():
     print(f"FP64 E {r64[-1].E:.10f} ({len(r64)} it), split E {rsp[-1].E:.10f} ({len(rsp)} it), |dE| {dE[-6:]}")
     assert c1 and c2
     assert abs(r64[-1].E - rsp[-1].E) < 1e-5
+
+
+def test_count_slope_and_commutator_match_oracle():
+    """thc_dyson_count (N and the analytic dN/dmu of the Newton search) and
+    thc_dyson_commutator (the CDIIS error vector) against the oracle's formulas."""
+    from paper_2404_17744_gb300 import thc
+    case = synth.make_sigma_case(9, 25, 4, 50.0, 41, identity_S=False, n_occ=4)
+    g = grid_for(50.0, 10.0)
+    G0, mu0 = so.solve_dyson(g, case.S, case.F, None, 4.0, 0.0)
+    U = o.thc_U(case.X, case.V)
+    nt = len(g.tau)
+    Sig = np.stack([o.sigma_sox_thc(case.X, U, G0[k], -G0[nt - 1 - k]) +
+                    o.sigma_direct_thc(case.X, case.V, G0[k], -G0[nt - 1 - k]) for k in range(nt)])
+    Siw = so.sigma_iw(g, Sig)
+    d = _dyson(case, g)
+    try:
+        dev = torch.device("cuda:0")
+        Sd = torch.from_numpy(Sig).to(dev)
+        for mu in (mu0, mu0 + 0.2, mu0 - 0.7):
+            n_gpu, dn_gpu = thc.thc_dyson_count(d, Sd, mu)
+            Giw = so.dyson_iw(g, case.S, case.F, Siw, mu)
+            n_ref = so.electron_count(g, case.S, Giw)
+            dn_ref = so.electron_count_slope(g, case.S, Giw)
+            assert abs(n_gpu - n_ref) < 1e-11 and abs(dn_gpu - dn_ref) < 1e-9 * max(1.0, abs(dn_ref))
+        # commutator: G of the last solve (here the Sigma = 0 solve at the oracle's mu0)
+        Gd = torch.empty((nt, case.n, case.n), dtype=torch.float64, device=dev)
+        assert thc.thc_dyson_solve(d, None, 4.0, mu0, 10.0, Gd) == mu0
+        E = torch.empty((len(g.iw), case.n, case.n, 2), dtype=torch.float64, device=dev)
+        thc.thc_dyson_commutator(d, Sd, E)
+        G0iw = so.dyson_iw(g, case.S, case.F, np.zeros_like(Siw), mu0)
+        e_ref = so.commutator_residual(g, case.S, case.F, G0iw, Sig)
+        e_gpu = E.cpu().numpy()
+        e_gpu = e_gpu[..., 0] + 1j * e_gpu[..., 1]
+        assert np.abs(e_ref).max() > 1e-4
+        assert np.abs(e_gpu - e_ref).max() < 1e-10 * max(1.0, np.abs(e_ref).max())
+    finally:
+        thc.thc_dyson_destroy(d)
+
+
+def test_cdiis_loop_matches_oracle_cdiis_loop():
+    from paper_2404_17744_gb300 import scf, thc
+    case = synth.make_sigma_case(20, 60, 4, 100.0, 17745, identity_S=False, n_occ=8)
+    g = grid_for(100.0, 10.0)
+    ref = so.run_loop(case, g, 8.0, tol=1e-10, mix="cdiis")
+    L = scf.GF2Loop(case.X, case.V, case.F, case.S, g, 8.0, precision=thc.THC_FP64, mixing="cdiis")
+    try:
+        conv = L.run(tol=1e-10, max_iter=80)
+        recs = L.records
+    finally:
+        L.close()
+    plain = so.run_loop(case, g, 8.0, tol=1e-10)
+    print(f"CDIIS: oracle E {ref['E']:.12f} ({ref['iters']} it), GPU E {recs[-1].E:.12f} ({len(recs)} it); "
+          f"residual DIIS {plain['iters']} it")
+    assert conv and ref["converged"]
+    assert abs(recs[-1].E - ref["E"]) < 1e-9 and abs(recs[-1].E - plain["E"]) < 1e-9
+    assert abs(len(recs) - ref["iters"]) <= 2

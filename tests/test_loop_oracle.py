@@ -107,3 +107,42 @@ def test_planted_wrong_parity_fails_energy_pin(monkeypatch):
     cd, cx = o.mp2_finite_T(o.mo_eri(o.eri_from_thc(case.X, case.V), C), eps - mu, 50.0)
     monkeypatch.setattr(so, "parity", lambda grid: np.ones(grid.basis.L))
     assert abs(so.energy_ir(g, G, Sig) - (cd + cx)) > 1e-6
+
+
+def test_count_slope_matches_finite_difference():
+    """dN/dmu from dG/dmu = -G S G equals a central difference of the count."""
+    case = _case()
+    g = grid_for(50.0, 10.0)
+    G, mu = so.solve_dyson(g, case.S, case.F, None, 3.0, 0.0)
+    Sig = _sigma_at(case, G)
+    Siw = so.sigma_iw(g, Sig)
+    for m in (mu, mu + 0.3):
+        h = 1e-5
+        fd = (so.electron_count(g, case.S, so.dyson_iw(g, case.S, case.F, Siw, m + h))
+              - so.electron_count(g, case.S, so.dyson_iw(g, case.S, case.F, Siw, m - h))) / (2 * h)
+        an = so.electron_count_slope(g, case.S, so.dyson_iw(g, case.S, case.F, Siw, m))
+        assert an > 0 and abs(an - fd) < 1e-6 * max(1.0, abs(an))
+
+
+def test_commutator_residual_vanishes_at_fixed_points():
+    """e = H G S - S G H is zero for the noninteracting G with Sigma = 0 and for the
+    converged loop, and clearly non-zero for an unconverged pair."""
+    case = _case()
+    g = grid_for(50.0, 10.0)
+    G0, mu0, G0iw = so.solve_dyson(g, case.S, case.F, None, 3.0, 0.0, return_iw=True)
+    e0 = so.commutator_residual(g, case.S, case.F, G0iw, np.zeros_like(G0))
+    assert np.abs(e0).max() < 1e-12
+    Sig = _sigma_at(case, G0)                 # Sigma[G0] with G0: not self-consistent
+    assert np.abs(so.commutator_residual(g, case.S, case.F, G0iw, Sig)).max() > 1e-4
+    r = so.run_loop(case, g, 3.0, tol=1e-12)
+    G, mu, Giw = so.solve_dyson(g, case.S, case.F, r["Sigma"], 3.0, r["mu"], return_iw=True)
+    assert np.abs(so.commutator_residual(g, case.S, case.F, Giw, r["Sigma"])).max() < 1e-7
+
+
+def test_cdiis_reaches_the_diis_fixed_point():
+    case = _case()
+    g = grid_for(50.0, 10.0)
+    r1 = so.run_loop(case, g, 3.0, tol=1e-11)
+    r2 = so.run_loop(case, g, 3.0, tol=1e-11, mix="cdiis")
+    assert r1["converged"] and r2["converged"]
+    assert abs(r1["E"] - r2["E"]) < 1e-9

@@ -309,3 +309,46 @@ def test_sox_rowwise_equals_scheme(rows):
         a = o.sigma_sox_thc(case.X, U, G, Gm)
         b = o.sigma_sox_thc_rows(case.X, U, G, Gm, rows=rows)
         assert np.abs(a - b).max() <= 1e-15 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("n,N,seed", [(3, 7, 1), (4, 9, 2)])
+def test_uhf_thc_equals_spin_orbital_definition(n, N, seed):
+    """The unrestricted THC route equals the spin-orbital four-index definition for two
+    different (non-symmetric) spin Green's functions."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, N)) / np.sqrt(n)
+    V = synth.draw_V(N, rng)
+    v = o.eri_from_thc(X, V)
+    U = o.thc_U(X, V)
+    Ga, Gb, Gma, Gmb = (rng.standard_normal((n, n)) for _ in range(4))
+    Sa, Sb = o.sigma_uhf_thc(X, V, U, Ga, Gb, Gma, Gmb)
+    Ra, Rb = o.sigma_uhf_spin_orbital(v, Ga, Gb, Gma, Gmb)
+    scale = max(np.abs(Ra).max(), np.abs(Rb).max())
+    assert np.abs(Sa - Ra).max() <= 1e-13 * scale and np.abs(Sb - Rb).max() <= 1e-13 * scale
+    # exchanging the spins exchanges the self-energies
+    Tb, Ta = o.sigma_uhf_thc(X, V, U, Gb, Ga, Gmb, Gma)
+    assert np.abs(Ta - Sa).max() <= 1e-13 * scale and np.abs(Tb - Sb).max() <= 1e-13 * scale
+
+
+def test_uhf_reduces_to_restricted_for_equal_spins():
+    """With G_alpha = G_beta both spin self-energies equal the restricted (per-spin) one,
+    and the unrestricted energy equals the restricted energy; with unequal spins the
+    bubble of one spin feels the other."""
+    case = synth.make_sigma_case(7, 19, 4, 30.0, 12, n_occ=3)
+    U = o.thc_U(case.X, case.V)
+    R = o.sigma_thc(case.X, case.V, case.G_tau, case.G_bmt)
+    Sa = np.empty_like(R)
+    Sb = np.empty_like(R)
+    for k in range(case.n_tau):
+        G, Gm = case.G_tau[k], o.g_minus_tau(case.G_bmt[k])
+        Sa[k], Sb[k] = o.sigma_uhf_thc(case.X, case.V, U, G, G, Gm, Gm)
+    scale = np.abs(R).max()
+    assert np.abs(Sa - R).max() <= 1e-13 * scale and np.abs(Sb - R).max() <= 1e-13 * scale
+    E_r = o.energy_dyn_tau(case.G_bmt, R, case.tau_w)
+    assert abs(o.energy_dyn_tau_uhf(case.G_bmt, case.G_bmt, Sa, Sb, case.tau_w) - E_r) <= 1e-13 * abs(E_r)
+    # a beta spin with one electron fewer (mu between the second and third levels) changes
+    # the alpha self-energy through the bubble
+    Gb_tau = synth.noninteracting_G(case.F, case.S, 0.5 * (case.eps[1] + case.eps[2]), case.beta, case.tau)
+    G, Gm = case.G_tau[0], o.g_minus_tau(case.G_bmt[0])
+    Sa2, _ = o.sigma_uhf_thc(case.X, case.V, U, G, Gb_tau[0], Gm, o.g_minus_tau(Gb_tau[-1]))
+    assert np.abs(Sa2 - Sa[0]).max() > 1e-6 * scale
