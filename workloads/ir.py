@@ -64,27 +64,6 @@ def logistic_kernel(tau: np.ndarray, w: np.ndarray, beta: float) -> np.ndarray:
     return out
 
 
-def _leading_svd(A: np.ndarray, eps: float) -> tuple[np.ndarray, np.ndarray]:
-    """Left singular vectors and singular values of A down to s_l / s_0 >= eps (and a
-    few more).  Small matrices: the full SVD.  Large ones (Lambda ~ 1e5 discretises to
-    ~20000 x 10000): the singular values of the logistic kernel decay exponentially,
-    so a seeded Gaussian sketch A Omega with k columns spans the leading singular
-    subspace to about s_k / s_0, and the SVD of Q^T A (Q from the sketch) gives the
-    leading triplets; k grows until s_k / s_0 < eps * 1e-3 (no power iterations,
-    which would square away the small singular values)."""
-    if min(A.shape) <= 3000:
-        U, s, _ = np.linalg.svd(A, full_matrices=False)
-        return U, s
-    rng = np.random.default_rng(17744)
-    k = 128
-    while True:
-        Q, _ = np.linalg.qr(A @ rng.standard_normal((A.shape[1], k)))
-        Ub, s, _ = np.linalg.svd(Q.T @ A, full_matrices=False)
-        if s[-1] / s[0] < eps * 1e-3 or k >= min(A.shape):
-            return Q @ Ub, s
-        k *= 2
-
-
 @dataclasses.dataclass
 class IRBasis:
     beta: float
@@ -141,7 +120,7 @@ def build_ir(beta: float, wmax: float, eps: float = 1e-10, order: int = 16, L_ma
     tn, tw = _gauss_on_panels(t_edges, order)
     wn, ww = _gauss_on_panels(w_edges, order)
     A = np.sqrt(tw)[:, None] * logistic_kernel(tn, wn, beta) * np.sqrt(ww)[None, :]
-    U, s = _leading_svd(A, eps)
+    U, s, _ = np.linalg.svd(A, full_matrices=False)
     keep = s / s[0] >= eps
     L = int(np.sum(keep))
     if L_max is not None:
