@@ -64,8 +64,10 @@ extern "C" {
                              BF16 tensor rate, so THC_BF16X3 is the reduced-precision mode */
 
 /* terms (bit mask) */
-#define THC_DIRECT   1
-#define THC_SOX      2
+#define THC_DIRECT   1    /* second-order direct (bubble) term */
+#define THC_SOX      2    /* second-order screened exchange */
+#define THC_GW       4    /* screened direct term of scGW / scGWSOX (RPA W) in place of
+                             THC_DIRECT; FP64 path, restricted; needs thc_sigma_set_bosonic */
 
 typedef struct thc_ctx thc_ctx;   /* opaque, library-owned */
 
@@ -84,7 +86,8 @@ typedef struct thc_ctx thc_ctx;   /* opaque, library-owned */
  *             is mirror-symmetric (|tau_k + tau_{n_tau-1-k} - beta| <= 1e-10 beta
  *             for all k) G(beta - tau_k) is read from G_tau itself
  *   precision THC_FP64 or THC_BF16X3 (THC_TF32: THC_ENOTSUP)
- *   terms     THC_DIRECT | THC_SOX (non-zero)
+ *   terms     THC_DIRECT | THC_SOX, or THC_GW | THC_SOX (scGWSOX), non-zero;
+ *             THC_DIRECT and THC_GW exclude each other
  *   stream    cudaStream_t the context launches on (NULL: legacy default stream)
  * X and V are scanned on the device: a NaN or infinite value gives THC_EINVAL.
  * Device memory held: U (N n^2 doubles) plus a workspace sized at init from
@@ -108,6 +111,26 @@ int thc_sigma_init(thc_ctx **ctx, int n_ao, int n_thc, int n_tau, double beta,
  * synchronises (thc_sync, thc_energy, thc_sigma_eval_host, thc_sigma_tune).
  */
 int thc_sigma_eval(thc_ctx *ctx, const double *G_tau, const double *G_bmt, double *Sigma_tau);
+
+/*
+ * thc_sigma_set_bosonic -- bosonic Matsubara transforms of the tau grid for the
+ * screened direct term (THC_GW).  With the spin-summed THC polarisation
+ * Pi~(tau) = 2 G^X(tau) o G^X(-tau)^T (G^X = X^T G X), evaluations compute
+ *   Pi~(i W_m)  = sum_k to_iw[m][k] Pi~(tau_k),
+ *   W(i W_m)    = V [1 - Pi~(i W_m) V]^{-1}   (formed as (V^{-1} - Pi~)^{-1}),
+ *   W~(tau_k)   = sum_m to_tau[k][m] (W - V)(i W_m),
+ *   Sigma^GW    = -X (G^X(tau) o W~(tau)) X^T     (Sec. II.C, THC-GW),
+ * and add Sigma^SOX when THC_SOX is set (scGWSOX).  The first term of the series
+ * W - V = V Pi~ V + ... is the THC_DIRECT term.
+ *   n_omega  number of sampled bosonic frequencies (fixed once set)
+ *   to_iw    host, n_omega x n_tau: values at the tau points -> values at i W_m
+ *   to_tau   host, n_tau x n_omega: values at i W_m -> values at the tau points
+ * Both map real functions symmetric under tau -> beta - tau (Pi~ and W~ of real
+ * symmetric G); the frequencies need not be listed.  The first call allocates
+ * 2 n_tau + n_omega + 1 N x N FP64 arrays and inverts V on the device.
+ * THC_ENOTSUP for THC_BF16X3 contexts, THC_EINVAL without THC_GW.  Synchronises.
+ */
+int thc_sigma_set_bosonic(thc_ctx *ctx, int n_omega, const double *to_iw, const double *to_tau);
 
 /*
  * thc_sigma_eval_uhf -- spin-unrestricted Sigma_a(tau_k), Sigma_b(tau_k) for every k.
@@ -224,8 +247,9 @@ int thc_profile(thc_ctx *ctx, int enable);
  * may be NULL.
  * Synchronises the stream.  Class names: u_build, project, sox_A, sox_B,
  * sox_CD, polarisation, direct_VPi, direct_W, back_transform, energy, split,
- * sox_BCD, check (sox_B and sox_CD are the FP64 path's; the split path runs both
- * contractions as the one fused sox_BCD kernel; check is the non-finite input scan).
+ * sox_BCD, check, screen (sox_B and sox_CD are the FP64 path's; the split path runs
+ * both contractions as the one fused sox_BCD kernel; check is the non-finite input
+ * scan; screen the bosonic transforms and inversions of THC_GW).
  */
 int thc_profile_get(thc_ctx *ctx, int kclass, const char **name, long long *launches,
                     double *ms, double *flops);
@@ -274,6 +298,20 @@ int thc_energy_static(int n_ao, int n_tau, const double *G_tau, const double *G_
  * thc_last_error(NULL).
  */
 int thc_wait_selftest(long long limit_ns, void *stream);
+
+/*
+ * thc_fp64_dfma_rate -- measured FP64 peak of the current device: the rate of
+ * independent fused multiply-adds (8 chains per thread, 4 CTAs of 256 threads
+ * per SM, iters FMAs per chain), timed with CUDA events after one warm-up
+ * launch.  GB300 has no FP64 tensor-core kind, so this DFMA rate bounds every
+ * FP64 contraction of the library (the paper has no counterpart: it is the
+ * denominator of the FP64 roofline).
+ *   iters   FMAs per chain, 1 .. 2^40 (5e4 gives a launch of about 0.1 s on GB300)
+ *   tflops  host out: 2 x FMAs / time / 1e12;  ms: host out (may be NULL)
+ *   stream  cudaStream_t (NULL: legacy default stream); synchronised
+ * Allocates and frees a few KB of device memory.
+ */
+int thc_fp64_dfma_rate(long long iters, double *tflops, double *ms, void *stream);
 
 /* thc_destroy -- free everything ctx owns (NULL is a no-op).  Synchronises. */
 void thc_destroy(thc_ctx *ctx);

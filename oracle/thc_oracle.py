@@ -184,6 +184,33 @@ def sigma_four_index(v: np.ndarray, G_tau: np.ndarray, G_bmt: np.ndarray, terms:
     return out
 
 
+# ------------------------------------------------------ screened (GW) bubble
+def sigma_gw_thc(X: np.ndarray, V: np.ndarray, G_tau: np.ndarray, G_bmt: np.ndarray,
+                 to_iw: np.ndarray, to_tau: np.ndarray) -> np.ndarray:
+    """Screened direct term of scGW / scGWSOX (Sec. II.C, first paragraph: the THC-GW
+    scheme with W screened by the RPA bubble) at every tau point, restricted, per spin.
+
+    With the spin-summed polarisation Pi~(tau) = 2 G^X(tau) o G^X(-tau)^T on the THC
+    grid, its bosonic transform Pi~(i Omega), the screened interaction
+      W(i Omega) = V [1 - Pi~(i Omega) V]^{-1}
+    and its dynamic part W~ = W - V transformed back to tau,
+      Sigma^GW(tau) = -X (G^X(tau) o W~(tau)) X^T.
+    The first term of W~ = V Pi~ V + V Pi~ V Pi~ V + ... gives the second-order direct
+    term of ``sigma_direct_thc``.  to_iw (n_Omega x n_tau) and to_tau (n_tau x n_Omega)
+    are the bosonic transforms of the tau grid (workloads.ir.make_bosonic_transforms).
+    """
+    nt = G_tau.shape[0]
+    N = V.shape[0]
+    GX = np.stack([X.T @ G_tau[k] @ X for k in range(nt)])
+    GXm = np.stack([X.T @ g_minus_tau(G_bmt[k]) @ X for k in range(nt)])
+    Pi = 2.0 * GX * np.swapaxes(GXm, 1, 2)
+    Pi_iw = np.einsum("mk,kab->mab", to_iw, Pi)
+    I = np.eye(N)
+    Wt_iw = np.stack([V @ np.linalg.inv(I - P @ V) - V for P in Pi_iw])
+    Wt = np.einsum("km,mab->kab", to_tau, Wt_iw)
+    return np.stack([-(X @ (GX[k] * Wt[k]) @ X.T) for k in range(nt)])
+
+
 # ------------------------------------------------- unrestricted (two spins)
 def sigma_uhf_spin_orbital(v: np.ndarray, G_a: np.ndarray, G_b: np.ndarray, Gm_a: np.ndarray,
                            Gm_b: np.ndarray) -> tuple[np.ndarray, np.ndarray]:

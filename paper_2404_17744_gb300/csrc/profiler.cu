@@ -6,7 +6,7 @@ namespace thc {
 const char* kernel_class_name(int k) {
   static const char* names[K_COUNT] = {"u_build",  "project",  "sox_A",        "sox_B",  "sox_CD", "polarisation",
                                        "direct_VPi", "direct_W", "back_transform", "energy", "split", "sox_BCD",
-                                       "check"};
+                                       "check", "screen"};
   return (k >= 0 && k < K_COUNT) ? names[k] : "";
 }
 

@@ -279,28 +279,56 @@ int fp64_sox(thc_ctx* ctx, const SpinIn& in, long long tc) {
   return launch_mirror_upper(ctx, ctx->D, N, tc);
 }
 
-// M = C_SOX D^T + cd G^X o (T V) with T = V Pi already in the GXm buffer (direct term), or
-// M = C_SOX D^T alone; then Sigma = X M X^T for the tau points of the chunk.
-int fp64_merge_back(thc_ctx* ctx, long long tc, bool sox, bool dir, double cd, double* Sigma_chunk) {
+// Sigma = X M X^T for the tau points of the chunk, M_RP = M[R][P] in the Pi buffer (merged)
+// or, without the direct term, M_RP = C_SOX D[P][R].
+int fp64_back(thc_ctx* ctx, long long tc, bool merged, double* Sigma_chunk) {
   const long long n = ctx->n, N = ctx->N, nn = n * n, NN = N * N, Nn = N * n;
-  View mview;
-  if (dir) {
-    THC_TRY(launch_gemm<true, false>(ctx, K_DIRECT_W, N, N, N, tc, View{ctx->GXm, NN, N, 1}, View{ctx->V, 0, N, 1},
-                                     MergeEpi{ctx->Pi, sox ? ctx->D : nullptr, ctx->GXp, N, cd}, "W"));
-    mview = View{ctx->Pi, NN, N, 1};
-  } else {
-    mview = View{ctx->D, NN, 1, N};  // M_RP = D_PR (C_SOX = +1)
-  }
   // T2 = M X^T : (m = R, c = r), A(R, P) = M[R, P], B(P, r) = X[r, P]
-  if (dir)
-    THC_TRY(launch_gemm<true, true>(ctx, K_BACK, N, n, N, tc, mview, View{ctx->X, 0, 1, N},
+  if (merged)
+    THC_TRY(launch_gemm<true, true>(ctx, K_BACK, N, n, N, tc, View{ctx->Pi, NN, N, 1}, View{ctx->X, 0, 1, N},
                                     f64::StoreEpi{ctx->T2, Nn, n, 1, 1.0}, "M X^T"));
   else
-    THC_TRY(launch_gemm<false, true>(ctx, K_BACK, N, n, N, tc, mview, View{ctx->X, 0, 1, N},
+    THC_TRY(launch_gemm<false, true>(ctx, K_BACK, N, n, N, tc, View{ctx->D, NN, 1, N}, View{ctx->X, 0, 1, N},
                                      f64::StoreEpi{ctx->T2, Nn, n, 1, C_SOX}, "M X^T"));
   // Sigma = X T2 : (m = t, c = r), A(t, R) = X[t, R], B(R, r) = T2[R, r]
   return launch_gemm<true, false>(ctx, K_BACK, n, n, N, tc, View{ctx->X, 0, N, 1}, View{ctx->T2, Nn, n, 1},
                                   f64::StoreEpi{Sigma_chunk, nn, n, 1, 1.0}, "X T2");
+}
+
+// M = C_SOX D^T + cd G^X o (T V) with T = V Pi already in the GXm buffer (direct term), or
+// M = C_SOX D^T alone; then the back-transform.
+int fp64_merge_back(thc_ctx* ctx, long long tc, bool sox, bool dir, double cd, double* Sigma_chunk) {
+  const long long N = ctx->N, NN = N * N;
+  if (dir)
+    THC_TRY(launch_gemm<true, false>(ctx, K_DIRECT_W, N, N, N, tc, View{ctx->GXm, NN, N, 1}, View{ctx->V, 0, N, 1},
+                                     MergeEpi{ctx->Pi, sox ? ctx->D : nullptr, ctx->GXp, N, cd}, "W"));
+  return fp64_back(ctx, tc, dir, Sigma_chunk);
+}
+
+// Screened direct term (THC_GW) with or without SOX, restricted: the bubble of every tau
+// point first (the bosonic transform couples them), then W~(tau), then per chunk SOX,
+// the merge M = C_SOX D^T - G^X o W~ and the back-transform.
+int fp64_eval_gw(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
+  const long long n = ctx->n, nt = ctx->n_tau, nn = n * n;
+  const bool sox = ctx->terms & THC_SOX;
+  if (!ctx->gw_nw) return fail(ctx, THC_EINVAL, "THC_GW needs the bosonic transforms (thc_sigma_set_bosonic)");
+  for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
+    const long long tc = std::min<long long>(ctx->tc, nt - c0);
+    THC_TRY(fp64_project(ctx, spin_views(ctx, G_tau, G_bmt, c0), tc, true, true));
+    THC_TRY(gw_store_bubble(ctx, c0, tc));
+  }
+  THC_TRY(gw_screen(ctx));
+  for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
+    const long long tc = std::min<long long>(ctx->tc, nt - c0);
+    const SpinIn in = spin_views(ctx, G_tau, G_bmt, c0);
+    if (sox) {
+      THC_TRY(fp64_project(ctx, in, tc, false, false));  // Y for the SOX scheme
+      THC_TRY(fp64_sox(ctx, in, tc));
+    }
+    THC_TRY(gw_merge(ctx, c0, tc, sox ? ctx->D : nullptr, ctx->Pi));
+    THC_TRY(fp64_back(ctx, tc, true, Sigma + c0 * nn));
+  }
+  return THC_OK;
 }
 
 }  // namespace
@@ -340,6 +368,7 @@ int fp64_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const d
 }
 
 int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
+  if (ctx->terms & THC_GW) return fp64_eval_gw(ctx, G_tau, G_bmt, Sigma);
   return fp64_eval_spins(ctx, 1, &G_tau, &G_bmt, &Sigma);
 }
 

@@ -220,8 +220,10 @@ int ctx_create(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, const
                 "THC_TF32 is not built: one TF32 product (11 significant bits) misses the 1e-6 Ha bound on "
                 "Sigma, and three TF32 products run at half the BF16 tensor rate for the bound THC_BF16X3 meets");
   if (precision != THC_FP64 && precision != THC_BF16X3) return fail(nullptr, THC_EINVAL, "unknown precision");
-  if (terms <= 0 || terms > (THC_DIRECT | THC_SOX))
-    return fail(nullptr, THC_EINVAL, "terms must be a non-empty subset of THC_DIRECT|THC_SOX");
+  if (terms <= 0 || terms > (THC_DIRECT | THC_SOX | THC_GW) || ((terms & THC_DIRECT) && (terms & THC_GW)))
+    return fail(nullptr, THC_EINVAL, "terms must be THC_DIRECT and/or THC_SOX, or THC_GW with or without THC_SOX");
+  if ((terms & THC_GW) && precision != THC_FP64)
+    return fail(nullptr, THC_ENOTSUP, "the screened (GW) term runs on the FP64 path only");
   thc_ctx* ctx = nullptr;
   try {
     ctx = new thc_ctx();
@@ -299,6 +301,7 @@ int thc_sigma_eval_uhf(thc_ctx* ctx, const double* G_tau_a, const double* G_bmt_
   const long long len = (long long)ctx->n_tau * ctx->n * ctx->n;
   for (const double* p : in)
     if (p) THC_TRY(launch_finite_scan(ctx, p, len, ctx->d_err + 1));
+  if (ctx->terms & THC_GW) return fail(ctx, THC_ENOTSUP, "the screened (GW) term is restricted only");
   const double* G[2] = {G_tau_a, G_tau_b};
   const double* Gb[2] = {G_bmt_a, G_bmt_b};
   double* S[2] = {Sigma_a, Sigma_b};
@@ -371,6 +374,11 @@ double thc_sigma_flops(const thc_ctx* ctx, double* u_flops) {
   // SOX: A for all P, then B and C/D for the N (N + 1) / 2 pairs P <= R (D_PR is symmetric)
   if (ctx->terms & THC_SOX) f += 2.0 * N * n * n * n + 2.0 * N * (N + 1) * n * n + N * (N + 1) * n;
   if (ctx->terms & THC_DIRECT) f += 2.0 * N * n * n + 4.0 * N * N * n + 4.0 * N * N * N;
+  if (ctx->terms & THC_GW) {  // projections per tau; per evaluation the transforms and the inversions
+    const double nw = ctx->gw_nw;
+    f += 2.0 * N * n * n + 4.0 * N * N * n;
+    if (nt > 0) f += (4.0 * nw * N * N * nt + 2.0 * nw * N * N * N) / nt;
+  }
   if (u_flops) *u_flops = (ctx->terms & THC_SOX) ? 2.0 * N * N * n * n : 0.0;
   return nt * f;
 }

@@ -27,6 +27,7 @@ enum KernelClass {
   K_SPLIT,        // FP64 <-> BF16 hi/lo conversions
   K_SOX_BCD,      // fused B_PRv and C/D (split precision)
   K_CHECK,        // non-finite input scans
+  K_SCREEN,       // screened interaction of THC_GW: transforms and inversions
   K_COUNT
 };
 const char* kernel_class_name(int k);
@@ -89,6 +90,14 @@ struct thc_ctx {
   __nv_bfloat16 *Ats_h = nullptr, *Ats_l = nullptr; // A^T blocks, Pb x n x ldn
   double *Dd = nullptr;                             // D, tc x N x N
   float *Pif = nullptr;                             // Pi of spin b, tc x N x N (unrestricted only)
+  // screened direct term (THC_GW, FP64 path)
+  int gw_nw = 0;                                    // sampled bosonic frequencies
+  double *gw_toiw = nullptr, *gw_totau = nullptr;   // n_omega x n_tau, n_tau x n_omega
+  double *gw_vinv = nullptr;                        // V^-1, N x N
+  double *gw_pi = nullptr;                          // Pi~(tau), then W~(tau): n_tau x N x N
+  double *gw_gx = nullptr;                          // G^X(tau), n_tau x N x N
+  double *gw_w = nullptr;                           // W(i Omega), n_omega x N x N
+  double *gw_scr = nullptr;                         // Gauss-Jordan scratch
   // device status words: [0] a tensor-core pipeline wait that ran out (its code),
   // [1] a non-finite value met in G_tau / G_bmt by an evaluation; read and cleared by status_check
   int *d_err = nullptr;
@@ -142,6 +151,13 @@ int energy_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, const do
 int ctx_create(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, const double* X, const double* V,
                const double* tau, int precision, int terms, cudaStream_t stream, size_t budget);
 void ctx_destroy(thc_ctx* ctx);
+
+// screened direct term (gw.cu)
+int gj_invert_spd(thc_ctx* ctx, double* A, long long n, long long batch);
+int gw_set_transforms(thc_ctx* ctx, int n_omega, const double* to_iw, const double* to_tau);
+int gw_store_bubble(thc_ctx* ctx, long long c0, long long tc);
+int gw_screen(thc_ctx* ctx);
+int gw_merge(thc_ctx* ctx, long long c0, long long tc, const double* D, double* M);
 
 // autotuner table of the split contractions (sigma_split.cu)
 int autotune_save(const char* path);

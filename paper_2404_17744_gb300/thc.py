@@ -24,6 +24,7 @@ THC_TF32 = 2      # not built: thc_sigma_init returns THC_ENOTSUP
 
 THC_DIRECT = 1
 THC_SOX = 2
+THC_GW = 4        # screened direct term (scGW / scGWSOX), FP64 path; needs thc_sigma_set_bosonic
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libthcsigma.so")
 
@@ -50,6 +51,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_sigma_init.restype = i
     lib.thc_sigma_eval.argtypes = [vp, dp, dp, dp]
     lib.thc_sigma_eval.restype = i
+    lib.thc_sigma_set_bosonic.argtypes = [vp, i, dp, dp]
+    lib.thc_sigma_set_bosonic.restype = i
     lib.thc_sigma_eval_uhf.argtypes = [vp, dp, dp, dp, dp, dp, dp]
     lib.thc_sigma_eval_uhf.restype = i
     lib.thc_sigma_eval_host.argtypes = [vp, dp, dp, dp]
@@ -73,6 +76,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_sync.restype = i
     lib.thc_wait_selftest.argtypes = [ctypes.c_longlong, vp]
     lib.thc_wait_selftest.restype = i
+    lib.thc_fp64_dfma_rate.argtypes = [ctypes.c_longlong, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+    lib.thc_fp64_dfma_rate.restype = i
     ll = ctypes.c_longlong
     lib.thc_gemm_bf16x3.argtypes = [i, i, i, i, dp, ll, dp, ll, dp, ll, vp]
     lib.thc_gemm_bf16x3.restype = i
@@ -201,6 +206,14 @@ def thc_sigma_eval(ctx, G_tau, G_bmt, Sigma_tau):
     _check(load_library().thc_sigma_eval(ctx, _ptr(G_tau), _ptr(G_bmt), _ptr(Sigma_tau)), ctx)
 
 
+def thc_sigma_set_bosonic(ctx, to_iw, to_tau):
+    """Bosonic transforms (n_omega x n_tau and n_tau x n_omega, host float64) for THC_GW."""
+    import numpy as np
+    a = np.ascontiguousarray(to_iw, dtype=np.float64)
+    b = np.ascontiguousarray(to_tau, dtype=np.float64)
+    _check(load_library().thc_sigma_set_bosonic(ctx, int(a.shape[0]), _ptr(a), _ptr(b)), ctx)
+
+
 def thc_sigma_eval_uhf(ctx, G_tau_a, G_bmt_a, G_tau_b, G_bmt_b, Sigma_a, Sigma_b):
     _check(load_library().thc_sigma_eval_uhf(ctx, _ptr(G_tau_a), _ptr(G_bmt_a), _ptr(G_tau_b), _ptr(G_bmt_b),
                                              _ptr(Sigma_a), _ptr(Sigma_b)), ctx)
@@ -260,6 +273,14 @@ def thc_energy_static(n_ao, n_tau, G_tau, G_bmt, Sigma_tau, tau_weights, stream=
 
 def thc_sync(ctx):
     _check(load_library().thc_sync(ctx), ctx)
+
+
+def thc_fp64_dfma_rate(iters=50_000, stream=None):
+    """(TFLOP/s, ms) of the FP64 FMA micro-benchmark on the current device."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(load_library().thc_fp64_dfma_rate(int(iters), ctypes.byref(t), ctypes.byref(ms), s), None)
+    return t.value, ms.value
 
 
 def thc_wait_selftest(limit_ns, stream=None):

@@ -8,6 +8,8 @@
   (appendix of arXiv:2404.17744), and G(0+) + G(beta-) = -S^{-1}
 Planted-mistake tests show that a sign or index error in the oracle fails a pin.
 """
+import functools
+
 import numpy as np
 import pytest
 import scipy.linalg
@@ -352,3 +354,52 @@ def test_uhf_reduces_to_restricted_for_equal_spins():
     G, Gm = case.G_tau[0], o.g_minus_tau(case.G_bmt[0])
     Sa2, _ = o.sigma_uhf_thc(case.X, case.V, U, G, Gb_tau[0], Gm, o.g_minus_tau(Gb_tau[-1]))
     assert np.abs(Sa2 - Sa[0]).max() > 1e-6 * scale
+
+
+@functools.lru_cache(maxsize=None)
+def _bosonic(beta, wmax=10.0):
+    from workloads import ir
+    g = ir.make_loop_grid(beta, wmax)
+    return g, ir.make_bosonic_transforms(g)
+
+
+def test_gw_weak_coupling_is_the_second_order_direct_term():
+    """Sigma^GW(lambda V) / lambda^2 tends to the second-order direct term as lambda -> 0,
+    with a remainder linear in lambda (the first screening correction)."""
+    g, bt = _bosonic(50.0)
+    case = synth.make_sigma_case(6, 14, 4, 50.0, 31, identity_S=False, n_occ=3)
+    G = synth.noninteracting_G(case.F, case.S, 0.0, 50.0, g.tau)
+    Gb = G[::-1]
+    ref = o.sigma_thc(case.X, case.V, G, Gb, terms="direct")
+    d = []
+    for lam in (1e-2, 5e-3):
+        S = o.sigma_gw_thc(case.X, lam * case.V, G, Gb, bt.to_iw, bt.to_tau) / lam ** 2
+        d.append(np.abs(S - ref).max() / np.abs(ref).max())
+    assert d[0] < 5e-2 and 1.6 < d[0] / d[1] < 2.4    # remainder ~ lambda
+
+
+def test_gw_one_orbital_closed_form():
+    """One orbital, one THC point: Pi~ is constant in tau, so only Omega = 0 screens:
+    Sigma^GW(tau) = Sigma^(2)(tau) / (1 + 2 v beta n (1 - n)), v = V X^4."""
+    beta = 50.0
+    g, bt = _bosonic(beta)
+    x, V, e = 0.9, 0.7, 0.03   # beta e = 1.5: n (1 - n) ~ 0.15, so screening is strong
+    X = np.array([[x]])
+    Vm = np.array([[V]])
+    G = np.array([[[o.fermi_pair(np.array([e]), beta)[1][0] * -np.exp(-e * t)]] for t in g.tau])
+    Gb = G[::-1].copy()
+    S = o.sigma_gw_thc(X, Vm, G, Gb, bt.to_iw, bt.to_tau)[:, 0, 0]
+    n_occ, n_vir = o.fermi_pair(np.array([e]), beta)
+    v = V * x ** 4
+    s2, _ = o.one_orbital_sigma(v, e, beta, g.tau)
+    expect = s2 / (1.0 + 2.0 * v * beta * n_occ[0] * n_vir[0])
+    assert np.abs(S - expect).max() <= 1e-9 * np.abs(expect).max()
+    assert np.abs(expect - s2).max() > 1e-3 * np.abs(s2).max()   # screening is not negligible here
+
+
+def test_gw_symmetric():
+    g, bt = _bosonic(50.0)
+    case = synth.make_sigma_case(7, 20, 4, 50.0, 12, n_occ=3)
+    G = synth.noninteracting_G(case.F, case.S, 0.0, 50.0, g.tau)
+    S = o.sigma_gw_thc(case.X, case.V, G, G[::-1], bt.to_iw, bt.to_tau)
+    assert np.abs(S - np.swapaxes(S, 1, 2)).max() <= 1e-13 * np.abs(S).max()

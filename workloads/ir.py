@@ -97,13 +97,17 @@ class IRBasis:
     def uhat(self, n: np.ndarray) -> np.ndarray:
         """uhat_l(i w_n) = int_0^beta e^{i w_n tau} u_l(tau) dtau, shape (L, len(n)), exact per panel."""
         n = np.atleast_1d(np.asarray(n))
-        w = (2 * n + 1) * np.pi / self.beta
+        return self.uhat_w((2 * n + 1) * np.pi / self.beta)
+
+    def uhat_w(self, w: np.ndarray) -> np.ndarray:
+        """int_0^beta e^{i w tau} u_l(tau) dtau at real frequencies w, shape (L, len(w))."""
+        w = np.atleast_1d(np.asarray(w, dtype=float))
         a, b = self.edges[:-1], self.edges[1:]
         c, h = 0.5 * (a + b), 0.5 * (b - a)
         # int_a^b e^{i w tau} P_p(x(tau)) dtau = 2 h e^{i w c} i^p j_p(w h)
         z = w[None, :] * h[:, None]                          # (panels, freqs)
         phase = np.exp(1j * w[None, :] * c[:, None]) * 2 * h[:, None]
-        out = np.zeros((self.L, len(n)), dtype=complex)
+        out = np.zeros((self.L, len(w)), dtype=complex)
         for p in range(self.order):
             jp = scipy.special.spherical_jn(p, z) * (1j ** p)  # (panels, freqs)
             out += self.coef[:, :, p] @ (phase * jp)
@@ -189,3 +193,51 @@ def make_loop_grid(beta: float, wmax: float, eps: float = 1e-10, L_max: int | No
     ub = b.u(np.array([beta]))[:, 0]
     u0 = b.u(np.array([0.0]))[:, 0]
     return LoopGrid(b, b.tau_s, b.n_s, b.iw_s, U_tau, fit_tau, U_iw, fit_iw, ub, u0)
+
+
+@dataclasses.dataclass
+class BosonicTransforms:
+    """Bosonic Matsubara transforms of functions sampled on a loop grid's tau points.
+
+    The screened interaction of GW (Sec. II.C names scGW and scGWSOX) needs the
+    polarisation Pi(tau) at bosonic frequencies i Omega_m = 2 pi m i / beta and the
+    screened W(i Omega) back on the tau grid.  Pi(tau) and W(tau) of real symmetric
+    matrices are real, symmetric under tau -> beta - tau, and their transforms are
+    real and even in Omega, so they are expanded in the even-parity functions u_l of
+    the grid's basis (which span e^{-w tau} + e^{-w (beta - tau)} for |w| <= w_max as
+    well as the odd-parity ones span the antisymmetric part), and sampled at m >= 0:
+      f(i Omega_m) = sum_k to_iw[m, k] f(tau_k),    f(tau_k) = sum_m to_tau[k, m] f(i Omega_m).
+    """
+    m: np.ndarray            # bosonic Matsubara indices (>= 0)
+    omega: np.ndarray        # Omega_m = 2 pi m / beta
+    to_iw: np.ndarray        # (n_Omega, n_tau) real
+    to_tau: np.ndarray       # (n_tau, n_Omega) real
+
+
+def make_bosonic_transforms(grid: LoopGrid) -> BosonicTransforms:
+    """Sampling matrices of the bosonic transforms on grid.tau.
+
+    R[m, l] = Re int_0^beta e^{i Omega_m tau} u_l(tau) dtau for the even-parity u_l;
+    the sampled m are 0, the sign changes of R[., l_e] of the highest even function
+    l_e over m < m_max, and m_max - 1 (the construction of the fermionic sampling,
+    applied to the even cosine transform), extended by the midpoints of the widest
+    gaps until there are at least as many frequencies as even functions."""
+    b = grid.basis
+    even = np.nonzero(grid.u_zero * grid.u_beta > 0)[0]
+    beta = b.beta
+    m_max = int(max(4 * b.L, b.beta * b.wmax / np.pi + 10 * b.L))
+    mm = np.arange(0, m_max)
+    R_all = b.uhat_w(2 * np.pi * mm / beta)[even].real        # (L_e, m_max)
+    f = R_all[-1]
+    ch = np.nonzero(np.sign(f[:-1]) * np.sign(f[1:]) < 0)[0]
+    sel = sorted(set([0] + [int(i) + 1 for i in ch] + [m_max - 1]))
+    while len(sel) < len(even):
+        gaps = np.diff(sel)
+        i = int(np.argmax(gaps))
+        sel.insert(i + 1, (sel[i] + sel[i + 1]) // 2)
+        sel = sorted(set(sel))
+    m = np.array(sel)
+    R = R_all[:, m].T                                          # (n_Omega, L_e)
+    to_iw = R @ grid.fit_tau[even, :]
+    to_tau = grid.U_tau[:, even] @ np.linalg.pinv(R)
+    return BosonicTransforms(m, 2 * np.pi * m / beta, to_iw, to_tau)
