@@ -32,13 +32,14 @@ def _pole(e, beta, tau):
     return -np.exp(e * (beta - tau)) / (1 + np.exp(beta * e))
 
 
-@pytest.mark.parametrize("beta,wmax", [(50.0, 10.0), (100.0, 10.0)])
+@pytest.mark.parametrize("beta,wmax", [(50.0, 10.0), (100.0, 10.0), (1000.0, 100.0)])
 def test_ir_basis_single_poles(beta, wmax):
     g = grid_for(beta, wmax)
     assert len(g.tau) == g.basis.L and len(g.iw) >= g.basis.L
     assert np.abs(g.tau + g.tau[::-1] - beta).max() < 1e-12 * beta
     assert np.abs(g.iw + g.iw[::-1]).max() < 1e-12
-    assert np.linalg.cond(g.U_tau) < 1e3 and np.linalg.cond(g.U_iw) < 1e3
+    # the sampling matrices stay well conditioned (the Matsubara one grows slowly with Lambda)
+    assert np.linalg.cond(g.U_tau) < 1e3 and np.linalg.cond(g.U_iw) < 3e3
     for e in (-1.9, -0.2, 0.0, 0.4, 2.5):
         gl = g.fit_tau @ _pole(e, beta, g.tau)
         assert np.abs(g.U_iw @ gl - 1.0 / (1j * g.iw - e)).max() < 1e-8
