@@ -9,6 +9,15 @@ once in thc_sigma_init, outside the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Beside the headline (FP64 Sigma TFLOP/s on that workload) the line carries the
+other workloads of the method as legs, each skippable: the 3xBF16 evaluation of
+the same workload (--no-split), 500 AOs / 2500 THC points / 120 tau at beta 1000
+in 3xBF16 with its error against the oracle's stored values (--no-c3), 64
+molecules in one CUDA graph (--no-c4), the self-consistent loop of the 200-AO
+system on an IR grid with Lambda = 1e5 in FP64 and 3xBF16 with every mixing
+scheme (--no-loop), two timed loop iterations at 1100 AOs / 5500 THC points
+(--no-c5), and the oracle on the host cores (--no-cpu-baseline).
+
 The method runs on one GPU.  Under torchrun with WORLD_SIZE > 1 the GPU arm
 launches nothing: rank 0 prints one line with "unavailable" and every rank
 exits 0 (the fused B C/D kernel multicasts TMA loads inside a CTA pair, which
@@ -54,7 +63,10 @@ def parse():
     p.add_argument("--workload", default="thc200")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-split", action="store_true", help="skip the mixed-precision measurement")
-    p.add_argument("--no-loop", action="store_true", help="skip the self-consistent loop measurement")
+    p.add_argument("--no-loop", action="store_true", help="skip the self-consistent loop measurements")
+    p.add_argument("--no-c3", action="store_true", help="skip the 500-AO 3xBF16 leg")
+    p.add_argument("--no-c4", action="store_true", help="skip the 64-molecule batched leg")
+    p.add_argument("--no-c5", action="store_true", help="skip the 1100-AO loop leg")
     return p.parse_args()
 
 
@@ -259,45 +271,31 @@ def measure(args, case, precision, dev, stream, X, V, G, S, flush, sampler_on):
                      energy=energies[-1] if energies else None)
 
 
-def loop_measure(case, precision, stream, tol=1e-8, learned_from=None):
-    """One self-consistent GF2 run to |dE| < tol on the IR grid; per-iteration records.
+def loop_measure(case, grid, precision, stream, tol=1e-8, mixing="diis", learned=None, max_iter=80):
+    """One self-consistent GF2 run to |E_k - E_(k-1)| < tol; wall time and per-iteration records.
 
-    learned_from: a related system (same sizes); its loop is run first with a recording
-    LearnedProposer, the network is fitted on that trajectory and then proposes for
-    this run (the recording run's time is reported separately, not in wall_s)."""
+    learned: None, or keyword arguments of scf.LearnedProposer (online: trained on the run's
+    own iterates, its training time inside wall_s)."""
     from paper_2404_17744_gb300 import scf
-    from workloads import ir
-    grid = ir.make_loop_grid(case.beta, 10.0)
     n_elec = float(np.sum(case.eps < 0))
-    proposer, extra = None, {}
-    if learned_from is not None:
-        LA = scf.GF2Loop(learned_from.X, learned_from.V, learned_from.F, learned_from.S, grid,
-                         float(np.sum(learned_from.eps < 0)), precision=precision, stream=stream)
-        proposer = scf.LearnedProposer(LA, record=True, steps=400)
-        t0 = time.perf_counter()
-        LA.run(tol=tol, max_iter=60, proposer=proposer)
-        loss = proposer.fit()
-        extra = {"training_run_s": time.perf_counter() - t0, "training_iterations": len(LA.records),
-                 "fit_loss": loss}
-        LA.close()
-        proposer.start_transfer()
-    L = scf.GF2Loop(case.X, case.V, case.F, case.S, grid, n_elec, precision=precision, stream=stream)
+    L = scf.GF2Loop(case.X, case.V, case.F, case.S, grid, n_elec, precision=precision, stream=stream, mixing=mixing)
+    P = scf.LearnedProposer(L, **learned) if learned is not None else None
     try:
         t0 = time.perf_counter()
-        conv = L.run(tol=tol, max_iter=60, proposer=proposer)
+        conv = L.run(tol=tol, max_iter=max_iter, proposer=P)
         wall = time.perf_counter() - t0
         recs = L.records
     finally:
+        extra = {}
+        if P is not None:
+            extra = {"proposals": P.proposed, "improved": P.accepted, "not_improved": P.rejected}
+            P.close()
         L.close()
-        if proposer is not None:
-            extra.update(accepted=proposer.accepted, rejected=proposer.rejected)
-            proposer.close()
-    return {"converged": bool(conv), "iterations": len(recs), "wall_s": wall,
+    return {"converged": bool(conv), "iterations": len(recs), "sigma_evaluations": len(recs), "wall_s": wall,
             "s_per_iteration": wall / max(1, len(recs)), "E": recs[-1].E, "mu": recs[-1].mu,
-            "n_tau": len(grid.tau), "n_iw": len(grid.iw),
             "sigma_s_per_iteration": float(np.mean([r.sigma_seconds for r in recs])),
             "dyson_evals_per_iteration": float(np.mean([r.dyson_evals for r in recs[:-1]])) if len(recs) > 1 else 0.0,
-            **extra}
+            "mixing": mixing + ("+learned" if learned is not None else ""), **extra}
 
 
 def batch_measure(cases, precision, steps, warmup, stream):
@@ -341,10 +339,154 @@ def batch_measure(cases, precision, steps, warmup, stream):
             "first_eval_s_incl_tuning_and_capture": t_first, "flops_per_eval": flops}
 
 
-def run_ours(args):
+def golden(name):
+    """Stored oracle values of a full-size workload (tests/golden, written from oracle/ only), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def roofline_of(kernels, bound, peak, peak_source, pipe_factor, traffic_key=None):
+    """Roofline of the kernel class with the most device time: achieved = the flops its
+    launches carried out (x pipe_factor products on the tensor pipe) over its event time."""
+    named = {k: v for k, v in kernels.items() if v["tflops"]}
+    dom_name, st = max(named.items(), key=lambda kv: kv[1]["ms"])
+    achieved = st["tflops"] * pipe_factor
+    r = {"kernel": dom_name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+         "frac": achieved / peak, "peak_source": peak_source,
+         "flops_per_launch": st["flops"] * pipe_factor / st["launches"],
+         "ms_per_launch": st["ms"] / st["launches"], "traffic": None}
+    tr = NCU_TRAFFIC.get((dom_name, traffic_key)) if traffic_key else None
+    if tr:
+        r["traffic"] = tr[0]
+        r["traffic_source"] = tr[1]
+    return r
+
+
+def leg_split_c3(args, stream, peaks):
+    """c3: 500 AOs, 2500 THC points, 120 Gauss-Legendre tau points, beta = 1000, THC_BF16X3:
+    time per evaluation and the error against the oracle's stored energy and traces."""
     import torch
     from paper_2404_17744_gb300 import thc
     from workloads import synth
+    case = synth.make_workload("thc500")
+    dev = stream.device
+    with torch.cuda.stream(stream):
+        X = torch.from_numpy(case.X).to(dev)
+        V = torch.from_numpy(case.V).to(dev)
+        G = torch.from_numpy(case.G_tau).to(dev)
+        S = torch.empty_like(G)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    a = argparse.Namespace(warmup=1, steps=max(1, min(args.steps, 2)))
+    ctx, r = measure(a, case, thc.THC_BF16X3, dev, stream, X, V, G, S, flush, False)
+    thc.thc_destroy(ctx)
+    flops = algorithmic_flops(case.n, case.N, case.n_tau)
+    out = {"workload": workload_desc(case, "thc500") + "; 3xBF16", "s_per_sigma_eval": r["total_ms"] / a.steps / 1e3,
+           "value": job_throughput(flops, a.steps, r["total_ms"] * 1e-3), "unit": "TFLOP/s (method flops)",
+           "E_dyn": r["energy"],
+           "roofline": roofline_of(r["kernels"], "tensor", peaks["bf16_sustained"],
+                                   f"BF16 dense sustained, {peaks['source']}; 3 products per useful multiply-add",
+                                   3.0)}
+    g = golden("thc500")
+    if g is not None:
+        Sh = S.cpu().numpy()
+        tr = np.array([np.trace(case.G_bmt[k] @ Sh[k]) for k in range(case.n_tau)])
+        out["abs_dE_vs_oracle"] = abs(r["energy"] - g["E_dyn"])
+        out["E_dyn_oracle"] = g["E_dyn"]
+        out["max_abs_dtrace_per_tau_vs_oracle"] = float(np.abs(tr - np.array(g["trace_per_tau"])).max())
+        errs = []
+        for k, smp in g["samples"].items():
+            ij = np.array([[i, j] for i, j, _ in smp["offdiag"]])
+            e = max(np.abs(np.diag(Sh[int(k)]) - np.array(smp["diag"])).max(),
+                    np.abs(Sh[int(k)][ij[:, 0], ij[:, 1]] - np.array([v for _, _, v in smp["offdiag"]])).max())
+            errs.append({"tau": smp["tau"], "max_abs_dsigma_on_stored": float(e)})
+        out["sigma_error_per_stored_tau"] = errs
+    del X, V, G, S, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def leg_loops(stream, case, grid):
+    """c2: the self-consistent GF2 loop of the 200-AO system on an IR grid (Lambda = 1e5,
+    Sec. III.A), FP64 and 3xBF16, with residual DIIS, commutator DIIS, plain damping and
+    damping with online-trained learned proposals (training inside the wall time)."""
+    from paper_2404_17744_gb300 import thc
+    runs = {"fp64_diis": loop_measure(case, grid, thc.THC_FP64, stream, tol=1e-8),
+            "bf16x3_diis": loop_measure(case, grid, thc.THC_BF16X3, stream, tol=1e-6),
+            "bf16x3_cdiis": loop_measure(case, grid, thc.THC_BF16X3, stream, tol=1e-6, mixing="cdiis"),
+            "bf16x3_damped": loop_measure(case, grid, thc.THC_BF16X3, stream, tol=1e-6, mixing="damp"),
+            "bf16x3_damped_learned": loop_measure(case, grid, thc.THC_BF16X3, stream, tol=1e-6, mixing="damp",
+                                                  learned=dict(max_proposals=8, cooldown=1, active_above=1e-7))}
+    f = runs["fp64_diis"]
+    for k, v in runs.items():
+        v["abs_dE_vs_fp64"] = abs(v["E"] - f["E"])
+        v["wall_time_speedup_vs_fp64"] = f["wall_s"] / v["wall_s"]
+    return runs
+
+
+def leg_batch_c4(stream):
+    """c4: 64 molecules, n_ao uniform in [50, 400], n_thc = 5 n_ao, 100 tau points, 3xBF16,
+    one CUDA-graph launch per batched evaluation (tile widths from the autotuner)."""
+    from paper_2404_17744_gb300 import thc
+    from workloads import batch as wb
+    cases = wb.make_batch(64, 50, 400, 100, 100.0, seed=17747)
+    r = batch_measure(cases, thc.THC_BF16X3, 1, 1, stream)
+    r["workload"] = ("c4: 64 molecules, n_ao uniform in [50, 400], n_thc = 5 n_ao, 100 Gauss-Legendre tau points, "
+                     "beta = 100, 3xBF16, 4 worker streams, one CUDA-graph launch per evaluation")
+    return r
+
+
+def leg_c5(stream, fp64_rate):
+    """c5 sizes: 1100 AOs, 5500 THC points, beta = 1000, IR grid with Lambda = 1e5: two iterations
+    of the 3xBF16 self-consistent loop (Sigma on every tau point, energy, mixing, Dyson with the
+    chemical-potential search) timed per iteration; the FP64 iteration time is extrapolated from
+    the FP64 Sigma rate measured on the 200-AO workload (the FP64 path is DFMA-bound at any size)."""
+    from paper_2404_17744_gb300 import scf, thc
+    from workloads import ir, synth
+    case = synth.make_workload("thc1100", n_tau=2)
+    grid = ir.make_loop_grid(1000.0, 100.0)
+    n_elec = float(np.sum(case.eps < 0))
+    t0 = time.perf_counter()
+    L = scf.GF2Loop(case.X, case.V, case.F, case.S, grid, n_elec, precision=thc.THC_BF16X3, stream=stream)
+    t_init = time.perf_counter() - t0
+    try:
+        L.run(tol=0.0, max_iter=2)
+        recs = L.records
+        flops = thc.thc_sigma_flops(L.ctx)[0]
+    finally:
+        L.close()
+    it = recs[-1]
+    return {"workload": f"c5: n_ao={case.n}, n_thc={case.N}, {len(grid.tau)} tau / {len(grid.iw)} Matsubara points "
+                        f"(IR, beta=1000, Lambda=1e5), 3xBF16 Sigma, FP64 Dyson",
+            "init_s": t_init, "s_per_iteration_bf16x3": it.seconds, "sigma_s": it.sigma_seconds,
+            "sigma_tflops": flops / it.sigma_seconds / 1e12, "dyson_evals": it.dyson_evals,
+            "s_per_iteration_fp64_extrapolated": flops / (fp64_rate * 1e12) + (it.seconds - it.sigma_seconds),
+            "iterations_timed": len(recs)}
+
+
+def cpu_baselines(case):
+    """The oracle on the host cores: all cores (about 15 s of tau points) and one core (one tau point)."""
+    v, pts, secs = oracle_sample(case)
+    out = {"value": v, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+           "sample": f"{pts} tau points of the workload (full Sigma(tau_k) each), {secs:.1f} s, U built outside "
+                     f"the timing; the oracle forms all (P, R) pairs, credited with the method's flops"}
+    try:
+        from threadpoolctl import threadpool_limits
+        with threadpool_limits(limits=1):
+            v1, p1, s1 = oracle_sample(case, seconds_target=0.0, max_points=1)
+        out["one_core"] = {"value": v1, "unit": UNIT, "cores": 1, "sample": f"{p1} tau point, {s1:.1f} s"}
+    except ImportError:
+        out["one_core"] = {"unavailable": "threadpoolctl not installed"}
+    return out
+
+
+def run_ours(args):
+    import torch
+    from paper_2404_17744_gb300 import thc
+    from workloads import ir, synth
 
     rank, world, local = dist_env()
     if world > 1:
@@ -363,13 +505,14 @@ def run_ours(args):
         S_split = torch.empty_like(G)
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
         stream.synchronize()
+        # the FP64 FMA chain rate of this device (reported beside the derived DFMA peak)
+        dfma_tflops, dfma_ms = thc.thc_fp64_dfma_rate(50_000, stream.cuda_stream)
 
         # ---- plain FP64 path (the headline workload)
-        ctx, r64 = measure(args, case, thc.THC_FP64, dev, stream, X, V, G, S, flush, rank == 0)
+        ctx, r64 = measure(args, case, thc.THC_FP64, dev, stream, X, V, G, S, flush, True)
         lib_flops, u_flops = thc.thc_sigma_flops(ctx)
         assert abs(lib_flops - flops_step) < 1e-6 * flops_step
         value = job_throughput(flops_step, args.steps, r64["total_ms"] * 1e-3)
-
         # end to end through the host-buffer entry point (H2D of G, D2H of Sigma inside)
         Gh = torch.from_numpy(case.G_tau).pin_memory()
         Sh = torch.empty_like(Gh).pin_memory()
@@ -378,71 +521,47 @@ def run_ours(args):
         e2e_steps = max(1, min(args.steps, 2))
         for _ in range(e2e_steps):
             thc.thc_sigma_eval_host(ctx, Gh, None, Sh)
-        e2e_dt = time.perf_counter() - t0
-        e2e_value = job_throughput(flops_step, e2e_steps, e2e_dt)
+        e2e_value = job_throughput(flops_step, e2e_steps, time.perf_counter() - t0)
         thc.thc_destroy(ctx)
 
-        # ---- mixed precision (3 x BF16 on tcgen05), same input; error against the FP64 result
+        # ---- mixed precision (3 x BF16 on tcgen05), same input
         split = None
         if not args.no_split:
-            ctx, rsp = measure(args, case, thc.THC_BF16X3, dev, stream, X, V, G, S_split, flush, False)
+            ctx, split = measure(args, case, thc.THC_BF16X3, dev, stream, X, V, G, S_split, flush, False)
             thc.thc_destroy(ctx)
             stream.synchronize()
-            split = rsp
-            split["value"] = job_throughput(flops_step, args.steps, rsp["total_ms"] * 1e-3)
+            split["value"] = job_throughput(flops_step, args.steps, split["total_ms"] * 1e-3)
             split["max_abs_dsigma_vs_fp64"] = float((S_split - S).abs().max().item())
-            split["abs_dE_vs_fp64"] = abs(rsp["energy"] - r64["energy"])
-
-        batched = None
-        if not args.no_split:
-            from workloads import batch as wb
-            bcases = wb.make_batch(16, 50, 200, 32, 100.0, seed=17748)
-            batched = batch_measure(bcases, thc.THC_BF16X3, args.steps, args.warmup, stream)
-            batched["workload"] = ("16 molecules, n_ao uniform in [50, 200], n_thc = 5 n_ao, 32 Gauss-Legendre tau "
-                                   "points, beta = 100, 3xBF16, 4 worker streams, one CUDA-graph launch per eval")
-
-        loop = None
+            split["abs_dE_vs_fp64"] = abs(split["energy"] - r64["energy"])
+        del X, V, G, S, S_split
+        torch.cuda.empty_cache()
+        c3 = leg_split_c3(args, stream, peaks) if not (args.no_split or args.no_c3) else None
+        c4 = leg_batch_c4(stream) if not (args.no_split or args.no_c4) else None
+        loops = None
         if not args.no_loop:
-            from paper_2404_17744_gb300 import thc as _t
-            l64 = loop_measure(case, _t.THC_FP64, stream, tol=1e-8)
-            lsp = loop_measure(case, _t.THC_BF16X3, stream, tol=1e-6)
-            related = synth.make_workload(args.workload, seed=synth.WORKLOADS[args.workload]["seed"] + 100)
-            lle = loop_measure(case, _t.THC_BF16X3, stream, tol=1e-6, learned_from=related)
-            loop = {"tau_grid": f"IR sparse sampling, beta={case.beta:g}, w_max=10 Ha, eps=1e-10: "
-                                f"{l64['n_tau']} tau / {l64['n_iw']} Matsubara points",
-                    "tolerance": "|E_k - E_(k-1)| < 1e-8 Ha (FP64); < 1e-6 Ha (3xBF16: its Sigma rounding "
-                                 "leaves a residual floor near 3e-6 and energies that scatter by ~5e-7)",
-                    "fp64": l64, "bf16x3": lsp, "bf16x3_learned": lle,
-                    "learned": "network fitted on the 3xBF16 loop of a related system (same sizes, another "
-                               "seed), one transferred proposal at the second iterate; its training run is "
-                               "reported in training_run_s, outside wall_s",
-                    "wall_time_speedup_bf16x3_vs_fp64": l64["wall_s"] / lsp["wall_s"],
-                    "wall_time_speedup_bf16x3_learned_vs_fp64": l64["wall_s"] / lle["wall_s"],
-                    "abs_dE_bf16x3_vs_fp64": abs(l64["E"] - lsp["E"]),
-                    "abs_dE_bf16x3_learned_vs_fp64": abs(l64["E"] - lle["E"])}
+            grid = ir.make_loop_grid(case.beta, 1e5 / case.beta)
+            loops = leg_loops(stream, case, grid)
+            loops["grid"] = (f"IR sparse sampling, beta={case.beta:g}, Lambda=1e5 (w_max={1e5 / case.beta:g} Ha), "
+                             f"eps=1e-10: {len(grid.tau)} tau / {len(grid.iw)} Matsubara points")
+            loops["tolerance"] = ("|E_k - E_(k-1)| < 1e-8 Ha (FP64); < 1e-6 Ha (3xBF16, whose Sigma rounding leaves "
+                                  "energies that scatter near 1e-7)")
+        c5 = leg_c5(stream, value) if not (args.no_loop or args.no_split or args.no_c5) else None
 
-    if rank != 0:
-        return 0
+    return finish(args, case, value, r64, e2e_value, Gh, Sh, split, c3, c4, loops, c5, peaks, dfma_tflops, dfma_ms)
 
-    def roofline_of(kernels, bound, peak, peak_source, pipe_factor, workload):
-        named = {k: v for k, v in kernels.items() if v["tflops"]}
-        dom_name, st = max(named.items(), key=lambda kv: kv[1]["ms"])
-        achieved = st["tflops"] * pipe_factor
-        r = {"kernel": dom_name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-             "frac": achieved / peak, "peak_source": peak_source,
-             "flops_per_launch": st["flops"] * pipe_factor / st["launches"],
-             "ms_per_launch": st["ms"] / st["launches"], "traffic": None}
-        tr = NCU_TRAFFIC.get((dom_name, workload))
-        if tr:
-            r["traffic"] = tr[0]
-            r["traffic_source"] = tr[1]
-        return r
 
+def finish(args, case, value, r64, e2e_value, Gh, Sh, split, c3, c4, loops, c5, peaks, dfma_tflops, dfma_ms):
+    """Assembles and prints the one JSON line."""
     roofline = roofline_of(r64["kernels"], "alu", FP64_PEAK_TFLOPS,
-                           "FP64 DFMA nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (MEASURED_PEAKS.json has no "
-                           "FP64 figure)", 1.0, args.workload)
+                           "FP64 DFMA, derived from the unit count and clock: 152 SMs x 2 DFMA/clk x 2 flop x "
+                           "2.07 GHz (MEASURED_PEAKS.json has no FP64 figure; GB300 has no FP64 tensor-core kind)",
+                           1.0, args.workload)
+    roofline["dfma_chain_tflops_measured"] = dfma_tflops
+    roofline["dfma_chain_note"] = (f"thc_fp64_dfma_rate: independent FMA chains, {dfma_ms:.0f} ms launch, this run; "
+                                   "the FP64 contraction tiles run above it (see profiles/fp64_dfma_rate.md)")
+    g200 = golden(args.workload)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r64["total_ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_desc(case, args.workload), "precision": "fp64", "terms": "direct+sox",
@@ -454,7 +573,8 @@ def run_ours(args):
                    "executed_tflops": executed_flops(r64["kernels"]) / (r64["total_ms"] * 1e-3) / 1e12,
                    "fp64_frac_of_peak": value / FP64_PEAK_TFLOPS,
                    "l2": "flushed between timed steps (258 MiB write); U_Pqs exceeds L2",
-                   "parallelism": "single GPU", "E_dyn": r64["energy"]},
+                   "parallelism": "single GPU", "E_dyn": r64["energy"],
+                   "abs_dE_vs_oracle": abs(r64["energy"] - g200["E_dyn"]) if g200 else None},
         "roofline": roofline,
         "gpu_launches": int(r64["launches"]),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Gh.numel() * 8),
@@ -464,29 +584,32 @@ def run_ours(args):
     }
     if split:
         line["mixed_precision"] = {
-            "precision": "bf16x3 (hi*hi + hi*lo + lo*hi) on tcgen05, FP32 accumulate, FP64 in/out",
+            "precision": "bf16x3 (hi*hi + hi*lo + lo*hi; X and V with a third term) on tcgen05, FP32 accumulate, "
+                         "FP64 in/out",
             "value": split["value"], "unit": "TFLOP/s (useful, FP64-equivalent flops of the method)",
             "executed_tflops": executed_flops(split["kernels"]) / (split["total_ms"] * 1e-3) / 1e12,
             "ms_per_step": split["total_ms"] / args.steps, "s_per_sigma_eval": split["total_ms"] / args.steps / 1e3,
             "speedup_vs_fp64": r64["total_ms"] / split["total_ms"],
             "max_abs_dsigma_vs_fp64": split["max_abs_dsigma_vs_fp64"], "abs_dE_vs_fp64": split["abs_dE_vs_fp64"],
+            "abs_dE_vs_oracle": abs(split["energy"] - g200["E_dyn"]) if g200 else None,
             "gpu_launches": int(split["launches"]),
             "roofline": roofline_of(split["kernels"], "tensor", peaks["bf16_sustained"],
                                     f"BF16 dense sustained, {peaks['source']}; achieved counts the 3 BF16 "
                                     f"products of every useful multiply-add", 3.0, args.workload + ":bf16x3"),
             "kernels": {k: {kk: v[kk] for kk in ("launches", "ms", "tflops")} for k, v in split["kernels"].items()},
         }
-    if batched:
-        line["batched"] = batched
-    if loop:
-        line["scgf2_loop"] = loop
-        line["config"]["s_per_scgf2_iteration_fp64"] = loop["fp64"]["s_per_iteration"]
-        line["config"]["s_per_scgf2_iteration_bf16x3"] = loop["bf16x3"]["s_per_iteration"]
+    if c3:
+        line["c3_split_500ao"] = c3
+    if c4:
+        line["c4_batched"] = c4
+    if loops:
+        line["scgf2_loop"] = loops
+        line["config"]["s_per_scgf2_iteration_fp64"] = loops["fp64_diis"]["s_per_iteration"]
+        line["config"]["s_per_scgf2_iteration_bf16x3"] = loops["bf16x3_diis"]["s_per_iteration"]
+    if c5:
+        line["c5_loop_1100ao"] = c5
     if not args.no_cpu_baseline:
-        v, pts, secs = oracle_sample(case)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-                                "sample": f"{pts} tau points of the workload (full Sigma(tau_k) each), "
-                                          f"{secs:.1f} s, U built outside the timing"}
+        line["cpu_baseline"] = cpu_baselines(case)
     print(json.dumps(line), flush=True)
     return 0
 
