@@ -419,7 +419,7 @@ def leg_loops(stream, case, grid):
             "bf16x3_cdiis": loop_measure(case, grid, thc.THC_BF16X3, stream, tol=1e-6, mixing="cdiis"),
             "bf16x3_damped": loop_measure(case, grid, thc.THC_BF16X3, stream, tol=1e-6, mixing="damp"),
             "bf16x3_damped_learned": loop_measure(case, grid, thc.THC_BF16X3, stream, tol=1e-6, mixing="damp",
-                                                  learned=dict(max_proposals=8, cooldown=1, active_above=1e-7))}
+                                                  learned=dict(max_proposals=1))}
     f = runs["fp64_diis"]
     for k, v in runs.items():
         v["abs_dE_vs_fp64"] = abs(v["E"] - f["E"])
