@@ -19,6 +19,8 @@
 #ifndef THC_LEARNED_H
 #define THC_LEARNED_H
 
+#include <stddef.h>
+
 #include "thc_sigma.h"
 
 #ifdef __cplusplus
@@ -86,6 +88,22 @@ int thc_proposer_train(thc_proposer *p, int steps, int batch, double lr, double 
 /* thc_proposer_propose -- write the proposed Sigma(tau) (dev, n_tau x n_ao x n_ao)
  * from the last two observed iterates (s_c, s_d taken from them).  Synchronises. */
 int thc_proposer_propose(thc_proposer *p, double *Sigma_tau);
+
+/* Resumable state of a proposer (checkpoint / resume of a self-consistent run):
+ * a header (sizes, observed-iterate count, Adam step, the scales s_c and s_d),
+ * the FP32 master weights and Adam moments of the network, and the observed
+ * coefficient window (the last min(count, max_hist) iterates, FP64).  The FP16
+ * working copies are rebuilt from the masters on load.
+ *
+ * thc_proposer_state_size -- bytes of the current state into *bytes.
+ * thc_proposer_save_state -- copy the state into the host buffer buf of `bytes`
+ *   bytes (>= the size; THC_EINVAL otherwise).  Synchronises.
+ * thc_proposer_load_state -- restore a state saved by a proposer of the same
+ *   n_ao, n_tau, n_l, hidden and max_hist; THC_EINVAL on any mismatch or a short
+ *   buffer (the proposer is then left unchanged).  Synchronises. */
+int thc_proposer_state_size(const thc_proposer *p, size_t *bytes);
+int thc_proposer_save_state(thc_proposer *p, void *buf, size_t bytes);
+int thc_proposer_load_state(thc_proposer *p, const void *buf, size_t bytes);
 
 const char *thc_proposer_last_error(const thc_proposer *p);
 void thc_proposer_destroy(thc_proposer *p);

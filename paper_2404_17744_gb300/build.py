@@ -52,7 +52,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-ldl"]  # -ldl: the NVTX loader
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

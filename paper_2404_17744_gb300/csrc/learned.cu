@@ -16,6 +16,8 @@
 // SIMT tile below.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -593,6 +595,105 @@ int thc_proposer_propose(thc_proposer* p, double* Sigma_tau) {
       nt, n2, L, View{p->U_tau, 0, L, 1}, View{p->prop, 0, n2, 1}, StoreD{Sigma_tau, n2, 1.0});
   THC_TRY(pcheck(p, cudaGetLastError(), "proposal to tau"));
   return pcheck(p, cudaStreamSynchronize(p->stream), "propose sync");
+}
+
+// ---------------------------------------------------------------- resumable state
+// Layout: StateHeader, then the FP32 arrays of the network in the order W1 b1 W2 b2 and
+// the Adam moments mW1 vW1 mb1 vb1 mW2 vW2 mb2 vb2, then the observed coefficient window
+// (iterates max(0, count - max_hist) .. count - 1, each n_l x n_ao^2 FP64).
+namespace {
+
+struct StateHeader {
+  char magic[8];
+  int32_t n, n_tau, L, H, max_hist, count;
+  int64_t t;
+  double s_c, s_d;
+};
+
+constexpr char kStateMagic[8] = {'T', 'H', 'C', 'P', 'R', 'O', 'P', '1'};
+
+struct StateArray {
+  float* p;
+  size_t n;
+};
+
+std::vector<StateArray> state_arrays(thc_proposer* p) {
+  thc_mlp* m = p->mlp;
+  const size_t n1 = (size_t)m->H * m->din, n2 = (size_t)m->dout * m->H, H = m->H, D = m->dout;
+  return {{m->W1, n1}, {m->b1, H},  {m->W2, n2},  {m->b2, D},  {m->mW1, n1}, {m->vW1, n1},
+          {m->mb1, H}, {m->vb1, H}, {m->mW2, n2}, {m->vW2, n2}, {m->mb2, D},  {m->vb2, D}};
+}
+
+size_t state_bytes(thc_proposer* p) {
+  size_t b = sizeof(StateHeader);
+  for (const StateArray& a : state_arrays(p)) b += 4 * a.n;
+  const int window = std::min(p->count, p->max_hist);
+  return b + 8 * (size_t)window * p->L * p->n2;
+}
+
+}  // namespace
+
+int thc_proposer_state_size(const thc_proposer* p, size_t* bytes) {
+  if (!p || !bytes) return thc::fail(nullptr, THC_EINVAL, "thc_proposer_state_size: NULL argument");
+  *bytes = state_bytes(const_cast<thc_proposer*>(p));
+  return THC_OK;
+}
+
+int thc_proposer_save_state(thc_proposer* p, void* buf, size_t bytes) {
+  if (!p || !buf) return thc::fail(nullptr, THC_EINVAL, "thc_proposer_save_state: NULL argument");
+  if (bytes < state_bytes(p)) return pfail(p, THC_EINVAL, "thc_proposer_save_state: buffer too small");
+  StateHeader h{};
+  std::memcpy(h.magic, kStateMagic, 8);
+  h.n = p->n, h.n_tau = p->n_tau, h.L = p->L, h.H = p->mlp->H, h.max_hist = p->max_hist, h.count = p->count;
+  h.t = p->mlp->t, h.s_c = p->s_c, h.s_d = p->s_d;
+  uint8_t* out = static_cast<uint8_t*>(buf);
+  std::memcpy(out, &h, sizeof h);
+  size_t off = sizeof h;
+  for (const StateArray& a : state_arrays(p)) {
+    THC_TRY(pcheck(p, cudaMemcpyAsync(out + off, a.p, 4 * a.n, cudaMemcpyDeviceToHost, p->stream), "save weights"));
+    off += 4 * a.n;
+  }
+  const size_t slot_bytes = 8 * (size_t)p->L * p->n2;
+  for (int k = std::max(0, p->count - p->max_hist); k < p->count; ++k, off += slot_bytes)
+    THC_TRY(pcheck(p, cudaMemcpyAsync(out + off, slot(p, k), slot_bytes, cudaMemcpyDeviceToHost, p->stream),
+                   "save window"));
+  return pcheck(p, cudaStreamSynchronize(p->stream), "save sync");
+}
+
+int thc_proposer_load_state(thc_proposer* p, const void* buf, size_t bytes) {
+  if (!p || !buf) return thc::fail(nullptr, THC_EINVAL, "thc_proposer_load_state: NULL argument");
+  StateHeader h{};
+  if (bytes < sizeof h) return pfail(p, THC_EINVAL, "thc_proposer_load_state: buffer too small");
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.n != p->n || h.n_tau != p->n_tau || h.L != p->L ||
+      h.H != p->mlp->H || h.max_hist != p->max_hist || h.count < 0)
+    return pfail(p, THC_EINVAL, "thc_proposer_load_state: not a state of a proposer of these sizes");
+  const int saved_count = p->count;
+  p->count = h.count;  // state_bytes sizes the window by count
+  const size_t need = state_bytes(p);
+  p->count = saved_count;
+  if (bytes < need) return pfail(p, THC_EINVAL, "thc_proposer_load_state: buffer too small");
+  const uint8_t* in = static_cast<const uint8_t*>(buf);
+  size_t off = sizeof h;
+  for (const StateArray& a : state_arrays(p)) {
+    THC_TRY(pcheck(p, cudaMemcpyAsync(a.p, in + off, 4 * a.n, cudaMemcpyHostToDevice, p->stream), "load weights"));
+    off += 4 * a.n;
+  }
+  const size_t slot_bytes = 8 * (size_t)p->L * p->n2;
+  for (int k = std::max(0, h.count - p->max_hist); k < h.count; ++k, off += slot_bytes)
+    THC_TRY(pcheck(p, cudaMemcpyAsync(slot(p, k), in + off, slot_bytes, cudaMemcpyHostToDevice, p->stream),
+                   "load window"));
+  thc_mlp* m = p->mlp;
+  const long long n1 = (long long)m->H * m->din, n2 = (long long)m->dout * m->H;
+  to_half_kernel<<<blocks(n1), 256, 0, p->stream>>>(n1, m->W1, m->W1h);
+  to_half_kernel<<<blocks(n2), 256, 0, p->stream>>>(n2, m->W2, m->W2h);
+  THC_TRY(pcheck(p, cudaGetLastError(), "half copies"));
+  THC_TRY(pcheck(p, cudaStreamSynchronize(p->stream), "load sync"));
+  p->count = h.count;
+  m->t = h.t;
+  p->s_c = h.s_c;
+  p->s_d = h.s_d;
+  return THC_OK;
 }
 
 const char* thc_proposer_last_error(const thc_proposer* p) { return p ? p->err.c_str() : ""; }

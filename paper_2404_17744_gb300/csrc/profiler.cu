@@ -1,4 +1,8 @@
-// Launch counter and optional per-kernel-class timing with CUDA events.
+// Launch counter, optional per-kernel-class timing with CUDA events, and one NVTX
+// range per launch named after its kernel class (free unless a profiler such as
+// Nsight Systems or ncu with NVTX filtering is attached).
+#include <nvtx3/nvToolsExt.h>
+
 #include "thc_internal.cuh"
 
 namespace thc {
@@ -25,14 +29,18 @@ int prof_begin(thc_ctx* ctx, int kclass, double flops, ProfRec* rec) {
   rec->kclass = kclass;
   rec->flops = flops;
   rec->e0 = rec->e1 = nullptr;
-  if (!ctx->prof_on) return THC_OK;
-  rec->e0 = pool_get(ctx);
-  rec->e1 = pool_get(ctx);
-  if (!rec->e0 || !rec->e1) return fail(ctx, THC_ECUDA, "cudaEventCreate failed");
-  return check_cuda(ctx, cudaEventRecord(rec->e0, ctx->stream), "profiler event");
+  if (ctx->prof_on) {
+    rec->e0 = pool_get(ctx);
+    rec->e1 = pool_get(ctx);
+    if (!rec->e0 || !rec->e1) return fail(ctx, THC_ECUDA, "cudaEventCreate failed");
+    THC_TRY(check_cuda(ctx, cudaEventRecord(rec->e0, ctx->stream), "profiler event"));
+  }
+  nvtxRangePushA(kernel_class_name(kclass));  // popped by prof_end, which every caller reaches
+  return THC_OK;
 }
 
 int prof_end(thc_ctx* ctx, ProfRec* rec, cudaError_t launch_status, const char* what) {
+  nvtxRangePop();
   THC_TRY(check_cuda(ctx, launch_status, what));
   ctx->launch_count += 1;
   if (!ctx->prof_on) return THC_OK;

@@ -8,10 +8,18 @@ library's kernels; this module holds the host-side control: the iteration,
 the convergence test and the small DIIS system (at most 16 x 16).
 
 Monitor energy with a fixed one-body matrix F:  E = 2 Tr[gamma F] + E_dyn.
+
+Auxiliary parts: `run(metrics=...)` writes one JSON line per iteration (energy,
+its change, mu, electron count, residual, proposal label, and the per-kernel-class
+GPU time of the iteration when the library profiler is on); `run(checkpoint=...)`
+saves the loop state after every iteration and `GF2Loop.resume(path)` restores
+it, so that an interrupted run continues from the iteration it had completed.
 """
 from __future__ import annotations
 
 import dataclasses
+import json
+import os
 import time
 
 import numpy as np
@@ -74,6 +82,9 @@ class GF2Loop:
         self.mu = 0.0
         self.history: list[tuple] = []   # (Sigma_out, residual) device tensors for DIIS
         self.records: list[IterationRecord] = []
+        self.iteration = 0               # iterations completed (mixing and Dyson step included)
+        self.E_prev = None
+        self._kernel_ms: dict[str, float] = {}
 
     def close(self):
         if self.ctx is not None:
@@ -147,33 +158,115 @@ class GF2Loop:
         return res
 
     # --------------------------------------------------------------- run
-    def run(self, tol=1e-8, max_iter=60, proposer=None, log=None):
+    def run(self, tol=1e-8, max_iter=60, proposer=None, log=None, metrics=None, checkpoint=None):
         """Iterates until |E_k - E_{k-1}| < tol.  proposer(loop, it, residual) may replace
         Sig_in before the Dyson step and returns a label (learned proposals); it is judged
-        by the exact Sigma of the next iteration like any other input."""
-        self.dyson(None)
-        E_prev = None
-        converged = False
-        for it in range(1, max_iter + 1):
-            t0 = time.perf_counter()
-            self.sigma()
-            t_sig = time.perf_counter() - t0
-            E, E_dyn, n = self.energy()
-            done = E_prev is not None and abs(E - E_prev) < tol
-            res = 0.0 if done else self.mix(it)
-            label = ""
-            if not done and proposer is not None:
-                label = proposer(self, it, res) or ""
-            evals = 0 if done else self.dyson(self.Sig_in)
-            rec = IterationRecord(it, E, E_dyn, self.mu, n, res, time.perf_counter() - t0, t_sig, evals, label)
-            self.records.append(rec)
-            if log:
-                log(rec)
-            if done:
-                converged = True
+        by the exact Sigma of the next iteration like any other input.
+
+        metrics: a path (appended to) or a writable text file for one JSON line per
+        iteration.  checkpoint: a path; after every iteration that does not end the run
+        the loop state (and the proposer's, when given) is written there, replacing the
+        previous one.  After resume() the run continues with the next iteration."""
+        out, own = None, False
+        if metrics is not None:
+            out, own = (open(metrics, "a"), True) if isinstance(metrics, (str, os.PathLike)) else (metrics, False)
+        try:
+            if self.iteration == 0:
+                self.dyson(None)
+                self.E_prev = None
+            converged = False
+            for it in range(self.iteration + 1, max_iter + 1):
+                t0 = time.perf_counter()
+                self.sigma()
+                t_sig = time.perf_counter() - t0
+                E, E_dyn, n = self.energy()
+                done = self.E_prev is not None and abs(E - self.E_prev) < tol
+                res = 0.0 if done else self.mix(it)
+                label = ""
+                if not done and proposer is not None:
+                    label = proposer(self, it, res) or ""
+                evals = 0 if done else self.dyson(self.Sig_in)
+                rec = IterationRecord(it, E, E_dyn, self.mu, n, res, time.perf_counter() - t0, t_sig, evals, label)
+                self.records.append(rec)
+                if log:
+                    log(rec)
+                if out is not None:
+                    self._write_metrics(out, rec)
+                if done:
+                    converged = True
+                    break
+                self.E_prev = E
+                self.iteration = it
+                if checkpoint is not None:
+                    self.save(checkpoint, proposer)
+            return converged
+        finally:
+            if own:
+                out.close()
+
+    # ---------------------------------------------------- metrics, checkpoints
+    def _kernel_times(self):
+        """Per-kernel-class GPU milliseconds since the last call (library profiler on), else {}."""
+        now, k = {}, 0
+        while True:
+            r = thc.thc_profile_get(self.ctx, k)
+            if r is None:
                 break
-            E_prev = E
-        return converged
+            name, launches, ms, _ = r
+            if launches:
+                now[name] = ms
+            k += 1
+        delta = {name: ms - self._kernel_ms.get(name, 0.0) for name, ms in now.items()}
+        self._kernel_ms = now
+        return {name: round(ms, 4) for name, ms in delta.items() if ms > 0}
+
+    def _write_metrics(self, out, rec):
+        d = dataclasses.asdict(rec)
+        d["dE"] = None if len(self.records) < 2 else rec.E - self.records[-2].E
+        d["kernel_ms"] = self._kernel_times()
+        out.write(json.dumps(d) + "\n")
+        out.flush()
+
+    def save(self, path, proposer=None):
+        """Writes the loop state after a completed iteration to `path` (.npz): Sigma_in, G,
+        mu, the iteration count, the last energy, the DIIS history, the records and, when
+        given, the proposer's state.  U_Pqs and the Dyson workspace are rebuilt on resume."""
+        h = [(o.cpu().numpy(), r.cpu().numpy()) for o, r in self.history]
+        state = dict(
+            version=np.array(1), n=np.array(self.n), N=np.array(self.N), n_tau=np.array(self.n_tau),
+            tau=np.asarray(self.grid.tau), mixing=np.array(self.mixing), iteration=np.array(self.iteration),
+            mu=np.array(self.mu), E_prev=np.array(np.nan if self.E_prev is None else self.E_prev),
+            Sig_in=self.Sig_in.cpu().numpy(), G=self.G.cpu().numpy(), n_hist=np.array(len(h)),
+            records=np.array(json.dumps([dataclasses.asdict(r) for r in self.records])))
+        for i, (o, r) in enumerate(h):
+            state[f"hist_out_{i}"] = o
+            state[f"hist_res_{i}"] = r
+        if proposer is not None:
+            state.update(proposer.state())
+        tmp = str(path) + ".tmp.npz"
+        np.savez(tmp, **state)
+        os.replace(tmp, path)
+
+    def resume(self, path, proposer=None):
+        """Restores a state written by save() into this loop (same sizes, tau grid and mixing)."""
+        torch = self.torch
+        z = np.load(path, allow_pickle=False)
+        if (int(z["n"]), int(z["N"]), int(z["n_tau"])) != (self.n, self.N, self.n_tau) or \
+                not np.array_equal(z["tau"], np.asarray(self.grid.tau)) or str(z["mixing"]) != self.mixing:
+            raise ValueError("checkpoint does not match this loop (sizes, tau grid or mixing)")
+        with torch.cuda.stream(self.stream):
+            self.Sig_in.copy_(torch.from_numpy(z["Sig_in"]))
+            self.G.copy_(torch.from_numpy(z["G"]))
+            self.history = [(torch.from_numpy(z[f"hist_out_{i}"]).to(self.dev),
+                             torch.from_numpy(z[f"hist_res_{i}"]).to(self.dev)) for i in range(int(z["n_hist"]))]
+        self.stream.synchronize()
+        self.mu = float(z["mu"])
+        self.iteration = int(z["iteration"])
+        e = float(z["E_prev"])
+        self.E_prev = None if np.isnan(e) else e
+        self.records = [IterationRecord(**r) for r in json.loads(str(z["records"]))]
+        if proposer is not None:
+            proposer.load_state(z)
 
 
 class LearnedProposer:
@@ -233,6 +326,20 @@ class LearnedProposer:
             self.close()
         except Exception:
             pass
+
+    def state(self) -> dict:
+        """Host arrays of the proposer's state (network, Adam moments, observed window, counters)."""
+        return {"prop_state": thc.thc_proposer_save_state(self.p),
+                "prop_counters": np.array([self.proposed, self.accepted, self.rejected, self.pause,
+                                           -1.0 if self.pending is None else self.pending,
+                                           float(self.record), float(self.transfer)])}
+
+    def load_state(self, z):
+        thc.thc_proposer_load_state(self.p, z["prop_state"])
+        c = z["prop_counters"]
+        self.proposed, self.accepted, self.rejected, self.pause = int(c[0]), int(c[1]), int(c[2]), int(c[3])
+        self.pending = None if c[4] < 0 else float(c[4])
+        self.record, self.transfer = bool(c[5]), bool(c[6])
 
     def fit(self, steps=None, lr=None):
         """Train on the recorded trajectory: inputs from each iterate, targets towards the last."""

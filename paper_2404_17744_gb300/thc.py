@@ -130,6 +130,12 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.thc_proposer_train.restype = i
     lib.thc_proposer_propose.argtypes = [vp, dp]
     lib.thc_proposer_propose.restype = i
+    lib.thc_proposer_state_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.thc_proposer_state_size.restype = i
+    lib.thc_proposer_save_state.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.thc_proposer_save_state.restype = i
+    lib.thc_proposer_load_state.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.thc_proposer_load_state.restype = i
     lib.thc_proposer_last_error.argtypes = [vp]
     lib.thc_proposer_last_error.restype = ctypes.c_char_p
     lib.thc_proposer_destroy.argtypes = [vp]
@@ -459,6 +465,26 @@ def thc_proposer_train(p, steps, batch, lr) -> float:
 def thc_proposer_propose(p, Sigma_tau):
     lib = load_library()
     _lcheck(lib.thc_proposer_propose(p, _ptr(Sigma_tau)), lib.thc_proposer_last_error, p)
+
+
+def thc_proposer_save_state(p):
+    """The proposer's resumable state as a host uint8 array."""
+    import numpy as np
+    lib = load_library()
+    size = ctypes.c_size_t()
+    _lcheck(lib.thc_proposer_state_size(p, ctypes.byref(size)), lib.thc_proposer_last_error, p)
+    buf = np.empty(size.value, dtype=np.uint8)
+    _lcheck(lib.thc_proposer_save_state(p, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes),
+            lib.thc_proposer_last_error, p)
+    return buf
+
+
+def thc_proposer_load_state(p, buf):
+    import numpy as np
+    lib = load_library()
+    b = np.ascontiguousarray(buf, dtype=np.uint8)
+    _lcheck(lib.thc_proposer_load_state(p, b.ctypes.data_as(ctypes.c_void_p), b.nbytes),
+            lib.thc_proposer_last_error, p)
 
 
 def thc_proposer_destroy(p):
