@@ -548,8 +548,9 @@ def run_ours(args):
             loops = leg_loops(stream, case, grid)
             loops["grid"] = (f"IR sparse sampling, beta={case.beta:g}, Lambda=1e5 (w_max={1e5 / case.beta:g} Ha), "
                              f"eps=1e-10: {len(grid.tau)} tau / {len(grid.iw)} Matsubara points")
-            loops["tolerance"] = ("|E_k - E_(k-1)| < 1e-8 Ha (FP64); < 1e-6 Ha (3xBF16, whose Sigma rounding leaves "
-                                  "energies that scatter near 1e-7)")
+            loops["tolerance"] = ("|E_k - E_(k-1)| < 1e-8 Ha (FP64); < 1e-6 Ha (3xBF16: the 16-bit rounding of its "
+                                  "data operands moves the energy by up to ~2e-5 Ha from one iteration to the next, "
+                                  "so the run stops where two consecutive energies agree)")
         c5 = leg_c5(stream, value) if not (args.no_loop or args.no_split or args.no_c5) else None
 
     return finish(args, case, value, r64, e2e_value, Gh, Sh, split, c3, c4, loops, c5, peaks, dfma_tflops, dfma_ms)

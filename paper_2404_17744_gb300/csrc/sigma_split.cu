@@ -26,6 +26,7 @@
 
 #include "tc_bcd.cuh"
 #include "tc_gemm.cuh"
+#include "tc_soxa.cuh"
 #include "thc_internal.cuh"
 
 namespace thc {
@@ -90,9 +91,10 @@ int make_map(thc_ctx* ctx, CUtensorMap* m, const bf16* base, long long K, const 
   return THC_OK;
 }
 
-// 3-D map with explicit extents (elements), byte strides of dims 1 and 2, and box; 128-byte swizzle.
+// 3-D map with explicit extents (elements), byte strides of dims 1 and 2, and box; 128-byte
+// swizzle (operand loads) or none (the store boxes of the A contraction).
 int make_map_3d(thc_ctx* ctx, CUtensorMap* m, const bf16* base, const long long dims_in[3], const long long strides_in[2],
-                const int box_in[3]) {
+                const int box_in[3], CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_128B) {
   cuuint64_t dims[3] = {(cuuint64_t)dims_in[0], (cuuint64_t)dims_in[1], (cuuint64_t)dims_in[2]};
   cuuint64_t strides[2] = {(cuuint64_t)strides_in[0], (cuuint64_t)strides_in[1]};
   cuuint32_t box[3] = {(cuuint32_t)box_in[0], (cuuint32_t)box_in[1], (cuuint32_t)box_in[2]};
@@ -100,7 +102,7 @@ int make_map_3d(thc_ctx* ctx, CUtensorMap* m, const bf16* base, const long long 
   if ((reinterpret_cast<uintptr_t>(base) & 15) || strides[0] % 16 || strides[1] % 16)
     return fail(ctx, THC_EINVAL, "tensor map operand not 16-byte aligned");
   CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, THC_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   return THC_OK;
@@ -137,50 +139,6 @@ struct EpiSplit {
       for (int r = 0; r < 32; ++r)
         if (row0 + r < M) split_store(hi, lo, (long long)b * bs + (long long)(row0 + r) * ld + col, scale * t(r, lane));
     }
-  }
-};
-
-// A^T blocks: row = P n + q (P local to the block), col = v  ->  At[P][v][q], split.
-// With n % 8 == 0 (groups of 8 rows never straddle two P) lane l writes 8 consecutive
-// q of column v = 8 i + l / 4 as one 16-byte store of each half; otherwise lanes run
-// along q with scalar stores.
-struct EpiAt {
-  bf16 *hi, *lo;
-  int n;
-  long long ld;
-  __device__ void operator()(int, int row0, int col0, Tile t, int lane, int M, int N) const {
-    if (!(n & 7)) {
-      const int qoff = 8 * (lane & 3), row = row0 + qoff;
-      if (row >= M) return;  // M = Pc n is a multiple of 8: a group is all in or all out
-      const int P = row / n, q = row - P * n;
-      const long long base = (long long)P * n * ld + q;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int c = 8 * i + (lane >> 2);
-        if (col0 + c >= N) continue;
-        uint32_t h[4], l[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float x0 = t(qoff + 2 * k, c), x1 = t(qoff + 2 * k + 1, c);
-          const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
-          const __nv_bfloat162 ll =
-              __floats2bfloat162_rn(x0 - __bfloat162float(hh.x), x1 - __bfloat162float(hh.y));
-          h[k] = *reinterpret_cast<const uint32_t*>(&hh);
-          l[k] = *reinterpret_cast<const uint32_t*>(&ll);
-        }
-        const long long o = base + (long long)(col0 + c) * ld;  // a multiple of 8 elements
-        *reinterpret_cast<uint4*>(hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
-      }
-      return;
-    }
-    const int row = row0 + lane;
-    if (row >= M) return;
-    const int P = row / n, q = row - P * n;
-    const long long base = (long long)P * n * ld + q;
-#pragma unroll 4
-    for (int j = 0; j < 32; ++j)
-      if (col0 + j < N) split_store(hi, lo, base + (long long)(col0 + j) * ld, t(lane, j));
   }
 };
 
@@ -536,6 +494,45 @@ int launch_bcd_shape(thc_ctx* ctx, const Split& Y, const Split& U, const Split& 
   return prof_end(ctx, &rec, e == cudaSuccess ? cudaGetLastError() : e, "B C/D");
 }
 
+// SOX contraction A of one tau point and P block (tc::sox_a_kernel):
+//   A^T[P][v][q] = sum_s U[P0 + P][q][s] G(-tau)[v][s],  split, P < Pc
+// U: the block's rows (P0 + P) n + q (K = s); G: rows v of G(-tau) (its sign included).
+int launch_sox_a(thc_ctx* ctx, const Split& U, const Split& G, const Split& At, long long Pc) {
+  if (Pc <= 0) return THC_OK;
+  using C = tc::SoxACfg;
+  const long long n = ctx->n, ldn = ctx->ldn;
+  if (Pc * n > INT32_MAX) return fail(ctx, THC_EINVAL, "A: block too large");
+  const int brows = (int)std::min<long long>(C::BV, (n + 15) / 16 * 16);
+  tc::SoxAMaps m;
+  THC_TRY(make_map(ctx, &m.uh, U.hi, n, U, tc::BM));
+  THC_TRY(make_map(ctx, &m.ul, U.lo, n, U, tc::BM));
+  THC_TRY(make_map(ctx, &m.gh, G.hi, n, G, brows));
+  THC_TRY(make_map(ctx, &m.gl, G.lo, n, G, brows));
+  const long long dims[3] = {n, n, Pc}, strides[2] = {ldn * 2, n * ldn * 2};
+  const int box[3] = {tc::BM, C::CHUNK, 1};
+  THC_TRY(make_map_3d(ctx, &m.ath, At.hi, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE));
+  THC_TRY(make_map_3d(ctx, &m.atl, At.lo, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE));
+  tc::SoxAArgs args;
+  args.Pc = (int)Pc;
+  args.n = (int)n;
+  args.nh = (int)((n + tc::BM - 1) / tc::BM);
+  args.nvt = (int)((n + C::BV - 1) / C::BV);
+  args.brows = brows;
+  args.tx = (uint32_t)(2 * (tc::BM + brows) * tc::BKE * 2);
+  int sms = 0;
+  THC_TRY(per_device(reinterpret_cast<const void*>(tc::sox_a_kernel), &sms, [&](int dev, int* v) {
+    THC_TRY(check_cuda(ctx, cudaFuncSetAttribute(tc::sox_a_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM),
+                       "A smem attribute"));
+    return check_cuda(ctx, cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  }));
+  const long long items = Pc * args.nh * args.nvt;
+  const dim3 grid((unsigned)std::min<long long>(items, sms), 1, 1);
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, K_SOX_A, 2.0 * Pc * n * n * n, &rec));
+  tc::sox_a_kernel<<<grid, tc::NTHREADS, C::SMEM, ctx->stream>>>(m, args, ctx->d_err);
+  return prof_end(ctx, &rec, cudaGetLastError(), "A");
+}
+
 int launch_bcd(thc_ctx* ctx, const Split& Y, const Split& U, const Split& At, long long P0, long long Pc,
                double* D) {
   if (Pc <= 0) return THC_OK;
@@ -681,8 +678,7 @@ int split_sox(thc_ctx* ctx, long long tc) {
       const long long Pc = std::min<long long>(ctx->Pb, N - P0);
       const Split At = Split{ctx->Ats_h, ctx->Ats_l, n, ldn, Pc, n * ldn};
       // A^T_P[v][q] = sum_s U[P q][s] G(-tau)[v][s]  (G(-tau) carries its sign in Gms)
-      THC_TRY(gemm(ctx, K_SOX_A, U.at_row(P0 * n, Pc * n), false, Gmk, false, Pc * n, n, n, 1,
-                   EpiAt{At.hi, At.lo, (int)n, ldn}, "A"));
+      THC_TRY(launch_sox_a(ctx, U.at_row(P0 * n, Pc * n), Gmk, At, Pc));
       // D[P][R] += sum_v (sum_w Y[P][w] U[R][v][w]) (sum_q Y[R][q] A^T_P[v][q])  (B and C never stored)
       THC_TRY(launch_bcd(ctx, Yk, U, At, P0, Pc, Dk));
     }
