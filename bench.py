@@ -643,6 +643,59 @@ def run_batch64(args):
     return 0
 
 
+def run_c5_loop(args):
+    """c5, learned part: the 3xBF16 GF2 loop at 1100 AOs, 5500 THC points, beta = 1000 (IR grid,
+    Lambda = 1e5), plain damping against damping with one online-trained learned proposal
+    (training inside the wall time), a fixed number of iterations each (args.steps, at least 8).
+    Reports per-iteration energies and residuals ||Sigma_out - Sigma_in||, and the iteration at
+    which each run's residual first falls below 1e-3 of its first value."""
+    import torch
+    from paper_2404_17744_gb300 import scf, thc
+    from workloads import ir, synth
+    rank, world, local = dist_env()
+    if world > 1:
+        return single_gpu_only(args, rank, world)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(device=torch.device("cuda", local))
+    case = synth.make_workload("thc1100", n_tau=2)
+    grid = ir.make_loop_grid(1000.0, 100.0)
+    n_elec = float(np.sum(case.eps < 0))
+    iters = max(8, args.steps)
+    runs = {}
+    for name, learned in (("damped", False), ("damped_learned", True)):
+        L = scf.GF2Loop(case.X, case.V, case.F, case.S, grid, n_elec, precision=thc.THC_BF16X3, stream=stream,
+                        mixing="damp")
+        P = scf.LearnedProposer(L, max_proposals=1) if learned else None
+        try:
+            t0 = time.perf_counter()
+            L.run(tol=0.0, max_iter=iters, proposer=P)
+            wall = time.perf_counter() - t0
+            recs = L.records
+        finally:
+            extra = {"proposals": P.proposed} if P else {}
+            if P:
+                P.close()
+            L.close()
+        res = [r.residual for r in recs]
+        below = next((r.iter for r in recs if r.residual < 1e-3 * res[0]), None)
+        runs[name] = {"wall_s": wall, "s_per_iteration": wall / len(recs), "E": [r.E for r in recs],
+                      "residual": res, "labels": [r.proposal for r in recs],
+                      "iteration_residual_below_1e-3_of_first": below, **extra}
+        print(f"{name}: {len(recs)} iterations, {wall:.1f} s, residual {res[0]:.2e} -> {res[-1]:.2e}, "
+              f"below 1e-3 x first at iteration {below}", file=sys.stderr, flush=True)
+    d, l = runs["damped"], runs["damped_learned"]
+    line = {"metric": METRIC, "value": None, "unit": "s per scGF2 iteration", "n_gpus": world, "steps": iters,
+            "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+            "data": "synthetic",
+            "config": {"workload": f"c5 loop: n_ao={case.n}, n_thc={case.N}, {len(grid.tau)} tau / "
+                                   f"{len(grid.iw)} Matsubara points (IR, beta=1000, Lambda=1e5), 3xBF16 Sigma, "
+                                   f"FP64 Dyson, damping 0.5, {iters} iterations per run"},
+            "c5_learned": {"runs": runs, "final_E_difference": l["E"][-1] - d["E"][-1]}}
+    line["value"] = d["s_per_iteration"]
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def single_gpu_only(args, rank, world):
     """Multi-process launch of the GPU arm: nothing runs on any GPU; rank 0 reports why."""
     if rank == 0:
@@ -661,6 +714,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch64(args)
+    if args.workload == "c5loop":
+        return run_c5_loop(args)
     return run_ours(args)
 
 

@@ -200,15 +200,19 @@ int thc_gemm_bf16x3(int batch, int M, int N, int K, const double *A, long long s
 
 /*
  * thc_sigma_tune -- THC_BF16X3 contexts: run one evaluation on G_tau (dev;
- * G_bmt as for thc_sigma_eval) with the autotuner on, which times both
- * tensor-core tile widths for every contraction shape not yet in the table
- * and keeps the faster; the evaluation's output is discarded.  Later
- * evaluations of any context use the table.  No-op for THC_FP64.  Synchronises.
+ * G_bmt as for thc_sigma_eval) with the autotuner on, which times, for every
+ * shape not yet in the table, both tensor-core tile widths of a single-chunk
+ * contraction and the three cluster shapes (1 x 1, 1 x 2, 2 x 2 CTAs) of a
+ * block of the fused B C/D kernel, and keeps the fastest; the evaluation's
+ * output is discarded.  Later evaluations of any context use the table.
+ * No-op for THC_FP64.  Synchronises.
  */
 int thc_sigma_tune(thc_ctx *ctx, const double *G_tau, const double *G_bmt);
 
 /* thc_autotune_save / thc_autotune_load -- write / merge the tile table
- * (text, one shape per line: class M N K batch width). */
+ * (text, one shape per line: class M N K batch choice, the choice being a tile
+ * width 128 / 256, or 10 CP + CR for a fused B C/D block whose batch field is
+ * its first P). */
 int thc_autotune_save(const char *path);
 int thc_autotune_load(const char *path);
 
@@ -245,7 +249,7 @@ int thc_profile(thc_ctx *ctx, int enable);
  * flops those launches carried out (2 per multiply-add; for sox_B, sox_CD and
  * sox_BCD only the part of the (P, R) square they compute).  Any out-pointer
  * may be NULL.
- * Synchronises the stream.  Class names: u_build, project, sox_A, sox_B,
+ * Synchronises the stream.  Class names, by index from 0: u_build, project, sox_A, sox_B,
  * sox_CD, polarisation, direct_VPi, direct_W, back_transform, energy, split,
  * sox_BCD, check, screen (sox_B and sox_CD are the FP64 path's; the split path runs
  * both contractions as the one fused sox_BCD kernel; check is the non-finite input

@@ -333,11 +333,13 @@ int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, 
 }
 
 // ------------------------------------------------------------- autotuner
-// Tile width (BN = 128 or 256 output columns) per contraction shape.  A shape
-// not in the table gets the width with the fewest padded columns (ties: 256);
-// a context in tuning mode times both widths on its first encounter of a
-// shape (CUDA events on its stream) and records the faster.  Timing runs the
-// contraction twice, so the outputs of a tuning evaluation are discarded.
+// The table holds, per contraction shape, the tile width (BN = 128 or 256 output
+// columns) of a single-chunk contraction, and per block of the fused B C/D kernel its
+// cluster shape (1 x 1, 1 x 2 or 2 x 2 CTAs).  A shape not in the table gets the width
+// with the fewest padded columns (ties: 256), or 1 x 2 clusters; a context in tuning
+// mode times every choice on its first encounter of a shape (CUDA events on its
+// stream) and records the fastest.  Timing runs the contraction once per choice, so
+// the outputs of a tuning evaluation are discarded.
 struct ShapeKey {
   int kclass;
   long long M, N, K, batch;
@@ -533,12 +535,58 @@ int launch_sox_a(thc_ctx* ctx, const Split& U, const Split& G, const Split& At, 
   return prof_end(ctx, &rec, cudaGetLastError(), "A");
 }
 
+// Cluster shapes of the fused B C/D kernel the autotuner chooses from, coded 10 CP + CR.
+// Without a table entry: pairs of CTAs along R sharing the P-side operands, measured on
+// GB300 at 200 and 500 AOs against a single CTA (-31% and -20% time) and a 2 x 2 cluster
+// (-9% and -2%).
+constexpr int kBcdShapes[3] = {12, 11, 22};
+
+int launch_bcd_code(thc_ctx* ctx, int code, const Split& Y, const Split& U, const Split& At, long long P0,
+                    long long Pc, double* D) {
+  switch (code) {
+    case 11: return launch_bcd_shape<1, 1>(ctx, Y, U, At, P0, Pc, D);
+    case 22: return launch_bcd_shape<2, 2>(ctx, Y, U, At, P0, Pc, D);
+    default: return launch_bcd_shape<1, 2>(ctx, Y, U, At, P0, Pc, D);
+  }
+}
+
 int launch_bcd(thc_ctx* ctx, const Split& Y, const Split& U, const Split& At, long long P0, long long Pc,
                double* D) {
   if (Pc <= 0) return THC_OK;
-  // Pairs of CTAs along R sharing the P-side operands: measured on GB300 at 200 and 500
-  // AOs against a single CTA (-31% and -20% time) and a 2 x 2 cluster (-9% and -2%).
-  return launch_bcd_shape<1, 2>(ctx, Y, U, At, P0, Pc, D);
+  const ShapeKey key{K_SOX_BCD, Pc, ctx->N, ctx->n, P0};
+  int code = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    auto it = g_tile_table.find(key);
+    if (it != g_tile_table.end()) code = it->second;
+  }
+  if (!code && ctx->tuning && !ctx->prof_on) {
+    // time every shape once on this block (each adds into D: a tuning evaluation's
+    // output is discarded) and record the fastest
+    cudaEvent_t e[4];
+    for (auto& x : e) THC_TRY(check_cuda(ctx, cudaEventCreate(&x), "tuning event"));
+    float best = 0.f;
+    int rc = check_cuda(ctx, cudaEventRecord(e[0], ctx->stream), "tuning event");
+    for (int i = 0; i < 3 && rc == THC_OK; ++i) {
+      rc = launch_bcd_code(ctx, kBcdShapes[i], Y, U, At, P0, Pc, D);
+      if (rc == THC_OK) rc = check_cuda(ctx, cudaEventRecord(e[i + 1], ctx->stream), "tuning event");
+    }
+    if (rc == THC_OK) rc = check_cuda(ctx, cudaEventSynchronize(e[3]), "tuning sync");
+    for (int i = 0; i < 3 && rc == THC_OK; ++i) {
+      float ms = 0.f;
+      rc = check_cuda(ctx, cudaEventElapsedTime(&ms, e[i], e[i + 1]), "tuning time");
+      if (rc == THC_OK && (i == 0 || ms < best)) {
+        best = ms;
+        code = kBcdShapes[i];
+      }
+    }
+    for (auto& x : e) cudaEventDestroy(x);
+    THC_TRY(rc);
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    g_tile_table[key] = code;
+    return THC_OK;
+  }
+  return launch_bcd_code(ctx, code ? code : kBcdShapes[0], Y, U, At, P0, Pc, D);
 }
 
 }  // namespace
@@ -750,7 +798,9 @@ int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* S
 }
 
 // ------------------------------------------------------- autotuner cache
-// Text file, one shape per line: kclass M N K batch BN.
+// Text file, one shape per line: kclass M N K batch choice (the tile width 128 / 256 of a
+// single-chunk contraction, or the cluster shape 10 CP + CR of a fused B C/D block, whose
+// "batch" field is the block's first P).
 int autotune_save(const char* path) {
   std::lock_guard<std::mutex> lock(g_tile_mu);
   FILE* f = std::fopen(path, "w");
@@ -769,7 +819,7 @@ int autotune_load(const char* path) {
   ShapeKey k;
   int bn;
   while (std::fscanf(f, "%d %lld %lld %lld %lld %d", &k.kclass, &k.M, &k.N, &k.K, &k.batch, &bn) == 6)
-    if (bn == 128 || bn == 256) g_tile_table[k] = bn;
+    if (k.kclass == K_SOX_BCD ? (bn == 11 || bn == 12 || bn == 22) : (bn == 128 || bn == 256)) g_tile_table[k] = bn;
   std::fclose(f);
   return THC_OK;
 }

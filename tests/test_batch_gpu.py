@@ -78,8 +78,9 @@ def test_autotuner_table_and_cache(tmp_path):
     thc.thc_autotune_save(path)
     lines = open(path).read().split("\n")
     assert sum(1 for l in lines if l.strip()) == n
-    for l in lines:
-        if l.strip():
-            assert int(l.split()[-1]) in (128, 256)
+    choices = [(int(l.split()[0]), int(l.split()[-1])) for l in lines if l.strip()]
+    bcd = [c for k, c in choices if k == thc.THC_KCLASS_SOX_BCD]
+    assert bcd and all(c in (11, 12, 22) for c in bcd)            # cluster shapes of the B C/D blocks
+    assert all(c in (128, 256) for k, c in choices if k != thc.THC_KCLASS_SOX_BCD)
     thc.thc_autotune_load(path)
     assert thc.thc_autotune_entries() == n
