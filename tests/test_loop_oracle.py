@@ -147,3 +147,46 @@ def test_cdiis_reaches_the_diis_fixed_point():
     r2 = so.run_loop(case, g, 3.0, tol=1e-11, mix="cdiis")
     assert r1["converged"] and r2["converged"]
     assert abs(r1["E"] - r2["E"]) < 1e-9
+
+
+def _linear_map(d, seed):
+    rng = np.random.default_rng(seed)
+    Q = np.linalg.qr(rng.standard_normal((d, d)))[0]
+    A = Q @ np.diag(rng.uniform(-0.8, 0.8, d)) @ Q.T       # a contraction
+    b = rng.standard_normal(d)
+    x_star = np.linalg.solve(np.eye(d) - A, b)
+    return (lambda x: A @ x + b), x_star, rng
+
+
+def test_diis_is_exact_on_a_linear_map_with_d_plus_one_iterates():
+    """Pulay / Anderson property: for f(x) = A x + b in d dimensions, d + 1 affinely
+    independent iterates make the residual combination vanish, and the mixed output is
+    the fixed point (I - A)^{-1} b."""
+    f, x_star, rng = _linear_map(4, 3)
+    xs = [rng.standard_normal(4) for _ in range(5)]
+    hist = [(f(x), f(x) - x) for x in xs]
+    assert np.allclose(so._diis(hist, 6), x_star, atol=1e-12, rtol=0)
+    assert np.allclose(so._diis(hist, 5), x_star, atol=1e-12, rtol=0)   # exactly d + 1 pairs
+    # a history window shorter than d + 1 does not reach it
+    assert np.abs(so._diis(hist, 3) - x_star).max() > 1e-6
+
+
+@pytest.mark.parametrize("complex_res", [False, True])
+def test_diis_two_point_closed_form(complex_res):
+    """Two pairs: c minimises |c r1 + (1 - c) r2| over real c, so
+    c = -Re<r2, r1 - r2> / |r1 - r2|^2 and the result is c out1 + (1 - c) out2
+    (complex residuals enter through their real and imaginary parts alike)."""
+    rng = np.random.default_rng(11)
+    shape = (3, 5)
+    o1, o2 = rng.standard_normal(shape), rng.standard_normal(shape)
+    r1, r2 = rng.standard_normal(shape), rng.standard_normal(shape)
+    if complex_res:
+        r1 = r1 + 1j * rng.standard_normal(shape)
+        r2 = r2 + 1j * rng.standard_normal(shape)
+    flat = lambda r: np.concatenate([np.real(r).ravel(), np.imag(r).ravel()])  # noqa: E731
+    d = flat(r1) - flat(r2)
+    c = -(flat(r2) @ d) / (d @ d)
+    assert np.allclose(so._diis([(o1, r1), (o2, r2)], 6), c * o1 + (1 - c) * o2, atol=1e-13, rtol=0)
+    # the last `size` pairs only
+    assert np.allclose(so._diis([(o2 * 7, r1 * 3), (o1, r1), (o2, r2)], 2), c * o1 + (1 - c) * o2,
+                       atol=1e-13, rtol=0)
