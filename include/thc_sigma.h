@@ -67,7 +67,7 @@ extern "C" {
 #define THC_DIRECT   1    /* second-order direct (bubble) term */
 #define THC_SOX      2    /* second-order screened exchange */
 #define THC_GW       4    /* screened direct term of scGW / scGWSOX (RPA W) in place of
-                             THC_DIRECT; FP64 path, restricted; needs thc_sigma_set_bosonic */
+                             THC_DIRECT; restricted; needs thc_sigma_set_bosonic */
 
 typedef struct thc_ctx thc_ctx;   /* opaque, library-owned */
 
@@ -127,8 +127,12 @@ int thc_sigma_eval(thc_ctx *ctx, const double *G_tau, const double *G_bmt, doubl
  *   to_tau   host, n_tau x n_omega: values at i W_m -> values at the tau points
  * Both map real functions symmetric under tau -> beta - tau (Pi~ and W~ of real
  * symmetric G); the frequencies need not be listed.  The first call allocates
- * 2 n_tau + n_omega + 1 N x N FP64 arrays and inverts V on the device.
- * THC_ENOTSUP for THC_BF16X3 contexts, THC_EINVAL without THC_GW.  Synchronises.
+ * 2 n_tau + n_omega + 1 N x N FP64 arrays (THC_BF16X3: tc more, the merged M of a tau
+ * chunk) and inverts V on the device.  The transforms, the inversions (Gauss-Jordan
+ * without pivoting, SPD; in blocks of 64 pivots with DFMA trailing updates above
+ * N = 128) and the merge run in FP64 on both paths; THC_BF16X3 takes G^X from its
+ * split projections (FP32) and runs the back-transform on the tensor cores.
+ * THC_EINVAL without THC_GW.  Synchronises.
  */
 int thc_sigma_set_bosonic(thc_ctx *ctx, int n_omega, const double *to_iw, const double *to_tau);
 

@@ -10,6 +10,9 @@
 // W is formed as the inverse of the symmetric positive definite V^{-1} - Pi~, a
 // Gauss-Jordan elimination without pivoting (stable for SPD matrices), batched
 // over the sampled frequencies; V^{-1} is formed the same way once per context.
+// Matrices up to 2 kGJBlock rows are eliminated one pivot at a time; larger ones in
+// blocks of kGJBlock pivots, whose trailing updates (2 N^2 kGJBlock flops each, 2 N^3
+// in all) run in the DFMA contraction tile.
 // The transforms to_iw, to_tau are inputs (the bosonic sampling matrices of the
 // caller's tau grid).  All arithmetic is FP64 in the DFMA tile or plain kernels.
 #include <algorithm>
@@ -57,6 +60,43 @@ __global__ void gj_update_kernel(long long n, int k, long long batch, double* __
   }
 }
 
+// Blocked elimination, step at pivots k0 .. k0 + kb - 1 of `batch` n x n matrices A:
+// C = A[:, k], R = A[k, :], P = A[k, k] copied out (C: n x kb, R: kb x n, P: kb x kb).
+__global__ void gj_panels_kernel(long long n, long long k0, long long kb, long long batch, const double* __restrict__ A,
+                                 double* __restrict__ C, double* __restrict__ R, double* __restrict__ P) {
+  const long long per = n * kb, total = per * batch;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long b = idx / per, e = idx - b * per, i = e / kb, c = e - i * kb;
+    const double* a = A + b * n * n;
+    C[idx] = a[i * n + k0 + c];                                   // C[b][i][c]
+    const long long r = e / n, j = e - r * n;                     // the same count, kb x n
+    R[idx] = a[(k0 + r) * n + j];                                 // R[b][r][j]
+    if (j < kb) P[b * kb * kb + r * kb + j] = a[(k0 + r) * n + k0 + j];
+  }
+}
+
+// A[k, :] = R' = P R except A[k, k] = P (P = A[k, k]^{-1}).
+__global__ void gj_rows_kernel(long long n, long long k0, long long kb, long long batch, const double* __restrict__ Rp,
+                               const double* __restrict__ P, double* __restrict__ A) {
+  const long long per = kb * n, total = per * batch;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long b = idx / per, e = idx - b * per, r = e / n, j = e - r * n;
+    const bool diag = j >= k0 && j < k0 + kb;
+    A[b * n * n + (k0 + r) * n + j] = diag ? P[b * kb * kb + r * kb + (j - k0)] : Rp[idx];
+  }
+}
+
+// A(b, m, c) -= v: the trailing update of a blocked step.
+struct SubEpi {
+  double* p;
+  long long sb, sr;
+  __device__ __forceinline__ void operator()(long long b, long long m, long long c, double v) const {
+    p[b * sb + m * sr + c] -= v;
+  }
+};
+
 // Pi~[k0 + b] = 2 GXp[b] o GXm[b]^T and GX[k0 + b] = GXp[b] for the tau points of a chunk.
 __global__ void gw_bubble_kernel(long long N, long long batch, const double* __restrict__ GXp,
                                  const double* __restrict__ GXm, double* __restrict__ Pi, double* __restrict__ GX) {
@@ -66,6 +106,18 @@ __global__ void gw_bubble_kernel(long long N, long long batch, const double* __r
     const long long b = idx / NN, r = idx - b * NN, i = r / N, j = r - i * N;
     Pi[idx] = 2.0 * GXp[idx] * GXm[b * NN + j * N + i];
     GX[idx] = GXp[idx];
+  }
+}
+
+// The same from the FP32 projections of the split path.
+__global__ void gw_bubble_f32_kernel(long long N, long long batch, const float* __restrict__ GXp,
+                                     const float* __restrict__ GXm, double* __restrict__ Pi, double* __restrict__ GX) {
+  const long long NN = N * N, total = NN * batch;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long b = idx / NN, r = idx - b * NN, i = r / N, j = r - i * N;
+    Pi[idx] = 2.0 * (double)GXp[idx] * (double)GXm[b * NN + j * N + i];
+    GX[idx] = (double)GXp[idx];
   }
 }
 
@@ -108,12 +160,11 @@ struct StoreE {
 
 }  // namespace
 
-// In-place inverse of `batch` SPD n x n matrices at A (no pivoting).
-int gj_invert_spd(thc_ctx* ctx, double* A, long long n, long long batch) {
-  if (!ctx->gw_scr)
-    THC_TRY(ctx_alloc(ctx, (void**)&ctx->gw_scr, sizeof(double) * (size_t)std::max<long long>(batch, ctx->gw_nw + 1) *
-                                                 (2 * (size_t)n + 1), "Gauss-Jordan scratch"));
-  double *row = ctx->gw_scr, *col = row + batch * n, *piv = col + batch * n;
+constexpr long long kGJBlock = 64;  // pivots per blocked step
+
+// One pivot at a time (matrices of up to 2 kGJBlock rows, and the diagonal blocks).
+int gj_invert_unblocked(thc_ctx* ctx, double* A, long long n, long long batch, double* row, double* col,
+                        double* piv) {
   const long long total = n * n * batch;
   for (int k = 0; k < n; ++k) {
     ProfRec rec;
@@ -127,10 +178,59 @@ int gj_invert_spd(thc_ctx* ctx, double* A, long long n, long long batch) {
   return THC_OK;
 }
 
+// In-place inverse of `batch` SPD n x n matrices at A (no pivoting).  A blocked step
+// at pivots k (P = A_kk^{-1}, C = A[:, k], R = A[k, :] before the step) sets
+//   A_ij -= C_i (P R_j)   (i, j outside k),   A_ik = -C_i P,   A_kj = P R_j,   A_kk = P,
+// the Gauss-Jordan step with a kb x kb pivot: all four follow from updating every
+// (i, j) with C (P R), then overwriting the block column and the block row.
+int gj_invert_spd(thc_ctx* ctx, double* A, long long n, long long batch) {
+  const bool blocked = n > 2 * kGJBlock;
+  const long long kb = std::min(n, kGJBlock);
+  // scratch: row, col, piv of the one-pivot steps (of n or of kb rows), and the panels
+  const long long nrow = blocked ? kb : n;
+  const size_t need = (size_t)batch * (2 * nrow + 1) + (blocked ? (size_t)batch * (3 * n * kb + kb * kb) : 0);
+  if (!ctx->gw_scr) {  // sized once, for the larger of this batch and the frequency count
+    const long long bmax = std::max<long long>(batch, ctx->gw_nw);
+    const size_t elems = (size_t)bmax * (2 * nrow + 1) + (blocked ? (size_t)bmax * (3 * n * kb + kb * kb) : 0);
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->gw_scr, sizeof(double) * elems, "Gauss-Jordan scratch"));
+    ctx->gw_scr_elems = elems;
+  }
+  if (need > ctx->gw_scr_elems) return fail(ctx, THC_EINVAL, "Gauss-Jordan scratch too small for this batch");
+  double *row = ctx->gw_scr, *col = row + batch * nrow, *piv = col + batch * nrow;
+  if (!blocked) return gj_invert_unblocked(ctx, A, n, batch, row, col, piv);
+  double *C = piv + batch, *R = C + batch * n * kb, *Rp = R + batch * n * kb, *P = Rp + batch * n * kb;
+  const long long nn = n * n;
+  for (long long k0 = 0; k0 < n; k0 += kGJBlock) {
+    const long long b = std::min(kGJBlock, n - k0);
+    ProfRec rec;
+    THC_TRY(prof_begin(ctx, K_SCREEN, 0.0, &rec));
+    gj_panels_kernel<<<blocks_for(n * b * batch), 256, 0, ctx->stream>>>(n, k0, b, batch, A, C, R, P);
+    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Gauss-Jordan panels"));
+    THC_TRY(gj_invert_unblocked(ctx, P, b, batch, row, col, piv));  // P = A_kk^{-1}
+    const dim3 gr((unsigned)((b + f64::BM - 1) / f64::BM), (unsigned)((n + f64::BN - 1) / f64::BN), (unsigned)batch);
+    THC_TRY(prof_begin(ctx, K_SCREEN, 2.0 * b * n * b * batch, &rec));  // R' = P R
+    f64::gemm_kernel<true, false><<<gr, f64::NT, 0, ctx->stream>>>(
+        b, n, b, View{P, b * b, b, 1}, View{R, n * b, n, 1}, f64::StoreEpi{Rp, n * b, n, 1, 1.0});
+    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Gauss-Jordan row panel"));
+    const dim3 gt((unsigned)((n + f64::BM - 1) / f64::BM), (unsigned)((n + f64::BN - 1) / f64::BN), (unsigned)batch);
+    THC_TRY(prof_begin(ctx, K_SCREEN, 2.0 * n * n * b * batch, &rec));  // A -= C R'
+    f64::gemm_kernel<true, false><<<gt, f64::NT, 0, ctx->stream>>>(
+        n, n, b, View{C, n * b, b, 1}, View{Rp, n * b, n, 1}, SubEpi{A, nn, n});
+    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Gauss-Jordan trailing update"));
+    const dim3 gc((unsigned)((n + f64::BM - 1) / f64::BM), (unsigned)((b + f64::BN - 1) / f64::BN), (unsigned)batch);
+    THC_TRY(prof_begin(ctx, K_SCREEN, 2.0 * n * b * b * batch, &rec));  // A[:, k] = -C P
+    f64::gemm_kernel<true, false><<<gc, f64::NT, 0, ctx->stream>>>(
+        n, b, b, View{C, n * b, b, 1}, View{P, b * b, b, 1}, f64::StoreEpi{A + k0, nn, n, 1, -1.0});
+    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Gauss-Jordan column panel"));
+    THC_TRY(prof_begin(ctx, K_SCREEN, 0.0, &rec));  // A[k, :] = R', A[k, k] = P
+    gj_rows_kernel<<<blocks_for(b * n * batch), 256, 0, ctx->stream>>>(n, k0, b, batch, Rp, P, A);
+    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Gauss-Jordan block row"));
+  }
+  return THC_OK;
+}
+
 int gw_set_transforms(thc_ctx* ctx, int n_omega, const double* to_iw, const double* to_tau) {
   const long long N = ctx->N, NN = N * N, nt = ctx->n_tau;
-  if (ctx->precision != THC_FP64)
-    return fail(ctx, THC_ENOTSUP, "the screened (GW) term runs on the FP64 path only");
   if (!(ctx->terms & THC_GW)) return fail(ctx, THC_EINVAL, "context was not created with THC_GW");
   if (n_omega < 1 || !to_iw || !to_tau) return fail(ctx, THC_EINVAL, "bad bosonic transforms");
   if (ctx->gw_nw && ctx->gw_nw != n_omega)
@@ -143,6 +243,8 @@ int gw_set_transforms(thc_ctx* ctx, int n_omega, const double* to_iw, const doub
     THC_TRY(ctx_alloc(ctx, (void**)&ctx->gw_pi, sizeof(double) * nt * NN, "Pi~(tau), W~(tau)"));
     THC_TRY(ctx_alloc(ctx, (void**)&ctx->gw_gx, sizeof(double) * nt * NN, "G^X(tau)"));
     THC_TRY(ctx_alloc(ctx, (void**)&ctx->gw_w, sizeof(double) * n_omega * NN, "W(i Omega)"));
+    if (ctx->precision != THC_FP64)  // the merged M of a chunk before its split
+      THC_TRY(ctx_alloc(ctx, (void**)&ctx->gw_m, sizeof(double) * ctx->tc * NN, "M of the screened term"));
     THC_TRY(check_cuda(ctx, cudaMemcpyAsync(ctx->gw_vinv, ctx->V, sizeof(double) * NN, cudaMemcpyDeviceToDevice,
                                             ctx->stream), "copy V"));
     THC_TRY(gj_invert_spd(ctx, ctx->gw_vinv, N, 1));
@@ -164,16 +266,27 @@ int gw_store_bubble(thc_ctx* ctx, long long c0, long long tc) {
   return prof_end(ctx, &rec, cudaGetLastError(), "GW bubble");
 }
 
+// The same from the split path's FP32 G^X(+-tau) buffers.
+int gw_store_bubble_f32(thc_ctx* ctx, long long c0, long long tc) {
+  const long long N = ctx->N, NN = N * N;
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, K_POLARISATION, 0.0, &rec));
+  gw_bubble_f32_kernel<<<blocks_for(NN * tc), 256, 0, ctx->stream>>>(N, tc, ctx->GXf, ctx->GXmf, ctx->gw_pi + c0 * NN,
+                                                                     ctx->gw_gx + c0 * NN);
+  return prof_end(ctx, &rec, cudaGetLastError(), "GW bubble");
+}
+
 // W~(tau_k) for every tau point (into gw_pi) from Pi~(tau_k) (in gw_pi).
 int gw_screen(thc_ctx* ctx) {
   const long long N = ctx->N, NN = N * N, nt = ctx->n_tau, nw = ctx->gw_nw;
-  // Pi~(i W_m) = sum_k to_iw[m][k] Pi~(tau_k): (m, e) = sum_k A(m, k) B(k, e)
+  // Pi~(i W_m) = sum_k to_iw[m][k] Pi~(tau_k), as the contraction (e, m) = sum_k A(e, k) B(k, m)
+  // with the N^2 elements e along the grid's first dimension (no 65535 limit there)
   {
     ProfRec rec;
     THC_TRY(prof_begin(ctx, K_SCREEN, 2.0 * nw * NN * nt, &rec));
-    const dim3 grid((unsigned)((nw + f64::BM - 1) / f64::BM), (unsigned)((NN + f64::BN - 1) / f64::BN), 1);
-    f64::gemm_kernel<true, false><<<grid, f64::NT, 0, ctx->stream>>>(
-        nw, NN, nt, View{ctx->gw_toiw, 0, nt, 1}, View{ctx->gw_pi, 0, NN, 1}, StoreE{ctx->gw_w, 0, NN, 1});
+    const dim3 grid((unsigned)((NN + f64::BM - 1) / f64::BM), (unsigned)((nw + f64::BN - 1) / f64::BN), 1);
+    f64::gemm_kernel<false, true><<<grid, f64::NT, 0, ctx->stream>>>(
+        NN, nw, nt, View{ctx->gw_pi, 0, 1, NN}, View{ctx->gw_toiw, 0, 1, nt}, StoreE{ctx->gw_w, 0, 1, NN});
     THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Pi~(i Omega)"));
   }
   ProfRec rec;
@@ -184,11 +297,11 @@ int gw_screen(thc_ctx* ctx) {
   THC_TRY(prof_begin(ctx, K_SCREEN, 0.0, &rec));
   gw_sub_kernel<<<blocks_for(NN * nw), 256, 0, ctx->stream>>>(NN, nw, ctx->V, ctx->gw_w);
   THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "W - V"));
-  // W~(tau_k) = sum_m to_tau[k][m] W~(i W_m)
+  // W~(tau_k) = sum_m to_tau[k][m] W~(i W_m), as (e, k) = sum_m A(e, m) B(m, k)
   THC_TRY(prof_begin(ctx, K_SCREEN, 2.0 * nt * NN * nw, &rec));
-  const dim3 grid((unsigned)((nt + f64::BM - 1) / f64::BM), (unsigned)((NN + f64::BN - 1) / f64::BN), 1);
-  f64::gemm_kernel<true, false><<<grid, f64::NT, 0, ctx->stream>>>(
-      nt, NN, nw, View{ctx->gw_totau, 0, nw, 1}, View{ctx->gw_w, 0, NN, 1}, StoreE{ctx->gw_pi, 0, NN, 1});
+  const dim3 grid((unsigned)((NN + f64::BM - 1) / f64::BM), (unsigned)((nt + f64::BN - 1) / f64::BN), 1);
+  f64::gemm_kernel<false, true><<<grid, f64::NT, 0, ctx->stream>>>(
+      NN, nt, nw, View{ctx->gw_w, 0, 1, NN}, View{ctx->gw_totau, 0, 1, nw}, StoreE{ctx->gw_pi, 0, 1, NN});
   return prof_end(ctx, &rec, cudaGetLastError(), "W~(tau)");
 }
 

@@ -119,25 +119,39 @@ __device__ __forceinline__ void split_store(bf16* hi, bf16* lo, long long o, flo
   lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// hi, lo and, when lo2 is set, the third term of v (the FP32 value exactly, 24 bits)
+__device__ __forceinline__ void split_store3(bf16* hi, bf16* lo, bf16* lo2, long long o, float v) {
+  const bf16 h = __float2bfloat16_rn(v);
+  const float r = v - __bfloat162float(h);
+  const bf16 l = __float2bfloat16_rn(r);
+  hi[o] = h;
+  lo[o] = l;
+  if (lo2) lo2[o] = __float2bfloat16_rn(r - __bfloat162float(l));
+}
+
 // dst(b, row, col) = scale * C, split; row-major, or transposed dst(b, col, row).
+// With lo2 set the third term is stored too.
 template <bool TRANSPOSED>
 struct EpiSplit {
   bf16 *hi, *lo;
   long long ld, bs;
   float scale;
+  bf16* lo2 = nullptr;
   __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int N) const {
     if (TRANSPOSED) {  // lanes along rows: dst(b, col, row) is contiguous in row
       const int row = row0 + lane;
       if (row >= M) return;
 #pragma unroll 4
       for (int j = 0; j < 32; ++j)
-        if (col0 + j < N) split_store(hi, lo, (long long)b * bs + (long long)(col0 + j) * ld + row, scale * t(lane, j));
+        if (col0 + j < N)
+          split_store3(hi, lo, lo2, (long long)b * bs + (long long)(col0 + j) * ld + row, scale * t(lane, j));
     } else {           // lanes along columns
       const int col = col0 + lane;
       if (col >= N) return;
 #pragma unroll 4
       for (int r = 0; r < 32; ++r)
-        if (row0 + r < M) split_store(hi, lo, (long long)b * bs + (long long)(row0 + r) * ld + col, scale * t(r, lane));
+        if (row0 + r < M)
+          split_store3(hi, lo, lo2, (long long)b * bs + (long long)(row0 + r) * ld + col, scale * t(r, lane));
     }
   }
 };
@@ -179,6 +193,7 @@ struct EpiMerge {
   const float* GX;
   int N;
   double cd;
+  bf16* lo2 = nullptr;  // third term of M, when set
   __device__ void operator()(int b, int row0, int col0, Tile t, int lane, int M, int Ncols) const {
     const int P = col0 + lane;
     if (P >= Ncols) return;
@@ -189,7 +204,7 @@ struct EpiMerge {
       if (R >= M) break;
       double m = cd * (double)GX[b * NN + (long long)R * N + P] * (double)t(r, lane);
       if (D) m += C_SOX * D[b * NN + (long long)P * N + R];
-      split_store(hi, lo, (long long)b * N * ld + (long long)R * ld + P, (float)m);
+      split_store3(hi, lo, lo2, (long long)b * N * ld + (long long)R * ld + P, (float)m);
     }
   }
 };
@@ -264,7 +279,7 @@ __global__ void kr_split_kernel(const double* __restrict__ X, int n, int N, int 
 __global__ void polarisation_split_kernel(long long N, long long batch, const float* __restrict__ GX,
                                           const float* __restrict__ GXm, const float* __restrict__ add,
                                           float* __restrict__ keep, bf16* __restrict__ hi, bf16* __restrict__ lo,
-                                          long long ld) {
+                                          bf16* __restrict__ lo2, long long ld) {
   const long long per = N * ld, total = per * batch;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -281,8 +296,11 @@ __global__ void polarisation_split_kernel(long long N, long long batch, const fl
     }
     if (keep) continue;
     const bf16 h = __float2bfloat16_rn(v);
+    const float r = v - __bfloat162float(h);
+    const bf16 l = __float2bfloat16_rn(r);
     hi[i] = h;
-    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    lo[i] = l;
+    if (lo2) lo2[i] = __float2bfloat16_rn(r - __bfloat162float(l));
   }
 }
 
@@ -301,21 +319,23 @@ int launch_split_f64(thc_ctx* ctx, const double* src, long long sb, long long sr
 // ----------------------------------------------------------- GEMM launch
 // C[b](M x N) = A[b](M x K) B[b](N x K)^T in split precision; epi consumes C.
 // AT = 3 multiplies the third term of A as well (A.lo2 must be set).
-template <int BN, bool MULTI, class Epi, int AT = 2>
+template <int BN, bool MULTI, class Epi, int AT = 2, int BT = 2>
 int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, const Split& B, bool b_batched,
                       long long M, long long N, long long K, long long batch, const Epi& epi, const char* what) {
   if (M <= 0 || N <= 0 || batch <= 0) return THC_OK;
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX || batch > INT32_MAX)
     return fail(ctx, THC_EINVAL, std::string(what) + ": contraction too large");
-  if (AT == 3 && !A.lo2) return fail(ctx, THC_EINVAL, std::string(what) + ": third operand term missing");
-  CUtensorMap ah, al, al2, bh, bl;
+  if ((AT == 3 && !A.lo2) || (BT == 3 && !B.lo2))
+    return fail(ctx, THC_EINVAL, std::string(what) + ": third operand term missing");
+  CUtensorMap ah, al, al2, bh, bl, bl2;
   THC_TRY(make_map(ctx, &ah, A.hi, K, A, tc::BM));
   THC_TRY(make_map(ctx, &al, A.lo, K, A, tc::BM));
   THC_TRY(make_map(ctx, &al2, AT == 3 ? A.lo2 : A.lo, K, A, tc::BM));
   THC_TRY(make_map(ctx, &bh, B.hi, K, B, BN));
   THC_TRY(make_map(ctx, &bl, B.lo, K, B, BN));
-  auto kern = tc::split_gemm_kernel<BN, MULTI, AT, Epi>;
-  using CfgE = tc::Cfg<BN, AT>;
+  THC_TRY(make_map(ctx, &bl2, BT == 3 ? B.lo2 : B.lo, K, B, BN));
+  auto kern = tc::split_gemm_kernel<BN, MULTI, AT, Epi, BT>;
+  using CfgE = tc::Cfg<BN, AT, BT>;
   int sms = 0;  // the kernel's shared-memory attribute is set once per device with it
   THC_TRY(per_device(reinterpret_cast<const void*>(kern), &sms, [&](int dev, int* v) {
     THC_TRY(check_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgE::SMEM),
@@ -326,7 +346,7 @@ int launch_split_gemm(thc_ctx* ctx, int kclass, const Split& A, bool a_batched, 
   const dim3 grid((unsigned)std::min<long long>(tiles, sms), 1, 1);  // persistent: one CTA per SM at most
   ProfRec rec;
   THC_TRY(prof_begin(ctx, kclass, 2.0 * M * N * K * batch, &rec));
-  kern<<<grid, tc::NTHREADS, CfgE::SMEM, ctx->stream>>>(ah, al, al2, bh, bl, (int)M, (int)N, (int)K, (int)batch,
+  kern<<<grid, tc::NTHREADS, CfgE::SMEM, ctx->stream>>>(ah, al, al2, bh, bl, bl2, (int)M, (int)N, (int)K, (int)batch,
                                                             tc::Operands{a_batched ? 1 : 0, b_batched ? 1 : 0}, epi,
                                                             ctx->d_err);
   return prof_end(ctx, &rec, cudaGetLastError(), what);
@@ -362,6 +382,8 @@ constexpr long long kSingleChunkK = 256;
 template <class Epi>
 int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool bb, long long M, long long N,
          long long K, long long batch, const Epi& epi, const char* what) {
+  if (A.lo2 && B.lo2)  // three-term X or V against a three-term data operand: six products
+    return launch_split_gemm<128, true, Epi, 3, 3>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
   if (A.lo2)  // three-term A operand (X or V): promoted, BN = 128 (five operand tiles per stage)
     return launch_split_gemm<128, true, Epi, 3>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
   if (K > kSingleChunkK) return launch_split_gemm<128, true>(ctx, kclass, A, ab, B, bb, M, N, K, batch, epi, what);
@@ -401,8 +423,8 @@ int gemm(thc_ctx* ctx, int kclass, const Split& A, bool ab, const Split& B, bool
 Split split_of(bf16* hi, bf16* lo, long long rows, long long ld, long long batch = 1) {
   return Split{hi, lo, rows, ld, batch, rows * ld};
 }
-Split split3_of(bf16* hi, bf16* lo, bf16* lo2, long long rows, long long ld) {
-  return Split{hi, lo, rows, ld, 1, rows * ld, lo2};
+Split split3_of(bf16* hi, bf16* lo, bf16* lo2, long long rows, long long ld, long long batch = 1) {
+  return Split{hi, lo, rows, ld, batch, rows * ld, lo2};
 }
 
 // Fused B and C/D of one tau point and P block (tc::sox_bcd_kernel):
@@ -610,7 +632,7 @@ int split_init(thc_ctx* ctx, size_t budget) {
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->Xs_l2, h * n * ldN, "Xs third term"));
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->Vs_l2, h * N * ldN, "Vs third term"));
   // blocking: per tau point and per P of the SOX block
-  const size_t per_t = h * 2 * (2 * n * ldn + 2 * N * ldn + 3 * N * ldN + n * ldN) + 4 * 2 * N * N + 8 * N * N;
+  const size_t per_t = h * 3 * (2 * n * ldn + 2 * N * ldn + 3 * N * ldN + n * ldN) + 4 * 2 * N * N + 8 * N * N;
   const size_t per_p = h * 2 * n * ldn;
   const bool sox = ctx->terms & THC_SOX;
   if (sox) THC_TRY(pair(&ctx->Us_h, &ctx->Us_l, (size_t)N * n * ldn, "U"));
@@ -621,16 +643,20 @@ int split_init(thc_ctx* ctx, size_t budget) {
   tc = std::min<size_t>(tc, (size_t)std::min(ctx->n_tau, 65535));
   ctx->Pb = (int)pb;
   ctx->tc = (int)tc;
-  THC_TRY(pair(&ctx->Gs_h, &ctx->Gs_l, tc * n * ldn, "G split"));
-  THC_TRY(pair(&ctx->Gms_h, &ctx->Gms_l, tc * n * ldn, "G(-tau) split"));
-  THC_TRY(pair(&ctx->Ys_h, &ctx->Ys_l, tc * N * ldn, "Y split"));
-  THC_TRY(pair(&ctx->Yms_h, &ctx->Yms_l, tc * N * ldn, "Ym split"));
+  auto triple = [&](bf16** hi, bf16** lo, bf16** lo2, size_t elems, const char* what) -> int {
+    THC_TRY(pair(hi, lo, elems, what));
+    return ctx_alloc(ctx, (void**)lo2, h * elems, what);
+  };
+  THC_TRY(triple(&ctx->Gs_h, &ctx->Gs_l, &ctx->Gs_l2, tc * n * ldn, "G split"));
+  THC_TRY(triple(&ctx->Gms_h, &ctx->Gms_l, &ctx->Gms_l2, tc * n * ldn, "G(-tau) split"));
+  THC_TRY(triple(&ctx->Ys_h, &ctx->Ys_l, &ctx->Ys_l2, tc * N * ldn, "Y split"));
+  THC_TRY(triple(&ctx->Yms_h, &ctx->Yms_l, &ctx->Yms_l2, tc * N * ldn, "Ym split"));
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->GXf, 4 * tc * N * N, "G^X"));
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->GXmf, 4 * tc * N * N, "G^X(-)"));
-  THC_TRY(pair(&ctx->Pis_h, &ctx->Pis_l, tc * N * ldN, "Pi split"));
-  THC_TRY(pair(&ctx->Ts_h, &ctx->Ts_l, tc * N * ldN, "V Pi split"));
-  THC_TRY(pair(&ctx->Ms_h, &ctx->Ms_l, tc * N * ldN, "M split"));
-  THC_TRY(pair(&ctx->T2s_h, &ctx->T2s_l, tc * n * ldN, "T2 split"));
+  THC_TRY(triple(&ctx->Pis_h, &ctx->Pis_l, &ctx->Pis_l2, tc * N * ldN, "Pi split"));
+  THC_TRY(triple(&ctx->Ts_h, &ctx->Ts_l, &ctx->Ts_l2, tc * N * ldN, "V Pi split"));
+  THC_TRY(triple(&ctx->Ms_h, &ctx->Ms_l, &ctx->Ms_l2, tc * N * ldN, "M split"));
+  THC_TRY(triple(&ctx->T2s_h, &ctx->T2s_l, &ctx->T2s_l2, tc * n * ldN, "T2 split"));
   THC_TRY(ctx_alloc(ctx, (void**)&ctx->Dd, 8 * tc * N * N, "D"));
   if (sox) {
     THC_TRY(pair(&ctx->Ats_h, &ctx->Ats_l, pb * n * ldn, "A^T blocks"));
@@ -679,21 +705,21 @@ int split_project(thc_ctx* ctx, const double* G_tau, const double* G_bmt, long l
                   bool need_minus) {
   const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau, ldn = ctx->ldn, nn = n * n, NN = N * N;
   const Split Xt = split3_of(ctx->Xt_h, ctx->Xt_l, ctx->Xt_l2, N, ldn);
-  const Split Gs = split_of(ctx->Gs_h, ctx->Gs_l, n, ldn, tc);
-  const Split Gms = split_of(ctx->Gms_h, ctx->Gms_l, n, ldn, tc);
-  const Split Ys = split_of(ctx->Ys_h, ctx->Ys_l, N, ldn, tc);
-  const Split Yms = split_of(ctx->Yms_h, ctx->Yms_l, N, ldn, tc);
+  const Split Gs = split3_of(ctx->Gs_h, ctx->Gs_l, ctx->Gs_l2, n, ldn, tc);
+  const Split Gms = split3_of(ctx->Gms_h, ctx->Gms_l, ctx->Gms_l2, n, ldn, tc);
+  const Split Ys = split3_of(ctx->Ys_h, ctx->Ys_l, ctx->Ys_l2, N, ldn, tc);
+  const Split Yms = split3_of(ctx->Yms_h, ctx->Yms_l, ctx->Yms_l2, N, ldn, tc);
   THC_TRY(launch_split_f64(ctx, G_tau + c0 * nn, nn, n, 1, 1.0, Gs, n, "split G"));
   if (G_bmt)
     THC_TRY(launch_split_f64(ctx, G_bmt + c0 * nn, nn, n, 1, -1.0, Gms, n, "split G(-tau)"));
   else
     THC_TRY(launch_split_f64(ctx, G_tau + (nt - 1 - c0) * nn, -nn, n, 1, -1.0, Gms, n, "split G(-tau)"));
-  THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Gs, true, N, n, n, tc, EpiSplit<false>{Ys.hi, Ys.lo, ldn, N * ldn, 1.f},
+  THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Gs, true, N, n, n, tc, EpiSplit<false>{Ys.hi, Ys.lo, ldn, N * ldn, 1.f, Ys.lo2},
                "Y"));
   if (!dir) return THC_OK;
   if (need_minus)
     THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Gms, true, N, n, n, tc,
-                 EpiSplit<false>{Yms.hi, Yms.lo, ldn, N * ldn, 1.f}, "Ym"));
+                 EpiSplit<false>{Yms.hi, Yms.lo, ldn, N * ldn, 1.f, Yms.lo2}, "Ym"));
   // G^X[P][R] = sum_q X^T[P][q] Y[R][q] (X as the three-term A operand)
   THC_TRY(gemm(ctx, K_PROJECT, Xt, false, Ys, true, N, N, n, tc, EpiF32{ctx->GXf, N, NN}, "G^X"));
   if (need_minus)
@@ -707,7 +733,7 @@ int split_polarisation(thc_ctx* ctx, long long tc, const float* add, float* keep
   ProfRec rec;
   THC_TRY(prof_begin(ctx, K_POLARISATION, 0.0, &rec));
   polarisation_split_kernel<<<blocks_for(tc * N * ldN), 256, 0, ctx->stream>>>(N, tc, ctx->GXf, ctx->GXmf, add, keep,
-                                                                               ctx->Pis_h, ctx->Pis_l, ldN);
+                                                                               ctx->Pis_h, ctx->Pis_l, ctx->Pis_l2, ldN);
   return prof_end(ctx, &rec, cudaGetLastError(), "polarisation");
 }
 
@@ -734,27 +760,60 @@ int split_sox(thc_ctx* ctx, long long tc) {
   return launch_mirror_upper(ctx, ctx->Dd, N, tc);  // D_PR = D_RP: fill P > R
 }
 
+// Sigma = X M X^T from the split M of the chunk (Ms[b][R][P]).
+int split_back(thc_ctx* ctx, long long tc, double* Sigma_chunk) {
+  const long long n = ctx->n, N = ctx->N, ldN = ctx->ldN, nn = n * n;
+  const Split Xs = split3_of(ctx->Xs_h, ctx->Xs_l, ctx->Xs_l2, n, ldN);
+  const Split Ms = split3_of(ctx->Ms_h, ctx->Ms_l, ctx->Ms_l2, N, ldN, tc);
+  const Split T2s = split3_of(ctx->T2s_h, ctx->T2s_l, ctx->T2s_l2, n, ldN, tc);
+  // T2t[r][R] = sum_P X[r][P] M[R][P]
+  THC_TRY(gemm(ctx, K_BACK, Xs, false, Ms, true, n, N, N, tc, EpiSplit<false>{T2s.hi, T2s.lo, ldN, n * ldN, 1.f, T2s.lo2},
+               "M X^T"));
+  return gemm(ctx, K_BACK, Xs, false, T2s, true, n, n, N, tc, EpiF64{Sigma_chunk, n, nn}, "X T2");
+}
+
 // M (merge of D and the direct term with T = V Pi in Ts, or D alone), then Sigma = X M X^T.
 int split_merge_back(thc_ctx* ctx, long long tc, bool sox, bool dir, double cd, double* Sigma_chunk) {
-  const long long n = ctx->n, N = ctx->N, ldN = ctx->ldN, nn = n * n, NN = N * N;
-  const Split Xs = split3_of(ctx->Xs_h, ctx->Xs_l, ctx->Xs_l2, n, ldN);
+  const long long N = ctx->N, ldN = ctx->ldN, NN = N * N;
   const Split Vs = split3_of(ctx->Vs_h, ctx->Vs_l, ctx->Vs_l2, N, ldN);
-  const Split Ts = split_of(ctx->Ts_h, ctx->Ts_l, N, ldN, tc);
-  const Split Ms = split_of(ctx->Ms_h, ctx->Ms_l, N, ldN, tc);
-  const Split T2s = split_of(ctx->T2s_h, ctx->T2s_l, n, ldN, tc);
+  const Split Ts = split3_of(ctx->Ts_h, ctx->Ts_l, ctx->Ts_l2, N, ldN, tc);
+  const Split Ms = split3_of(ctx->Ms_h, ctx->Ms_l, ctx->Ms_l2, N, ldN, tc);
   if (dir) {
     // W[P][R] = sum_S V[P][S] T[R][S] = (V Pi V)[P][R], symmetric, so the merge epilogue
     // reads the tile as W[R][P]
     THC_TRY(gemm(ctx, K_DIRECT_W, Vs, false, Ts, true, N, N, N, tc,
-                 EpiMerge{Ms.hi, Ms.lo, ldN, sox ? ctx->Dd : nullptr, ctx->GXf, (int)N, cd}, "W"));
+                 EpiMerge{Ms.hi, Ms.lo, ldN, sox ? ctx->Dd : nullptr, ctx->GXf, (int)N, cd, Ms.lo2}, "W"));
   } else {
     // M[R][P] = c_x D[P][R]
     THC_TRY(launch_split_f64(ctx, ctx->Dd, NN, 1, N, C_SOX, Ms, N, "split D^T"));
   }
-  // T2t[r][R] = sum_P X[r][P] M[R][P]
-  THC_TRY(gemm(ctx, K_BACK, Xs, false, Ms, true, n, N, N, tc, EpiSplit<false>{T2s.hi, T2s.lo, ldN, n * ldN, 1.f},
-               "M X^T"));
-  return gemm(ctx, K_BACK, Xs, false, T2s, true, n, n, N, tc, EpiF64{Sigma_chunk, n, nn}, "X T2");
+  return split_back(ctx, tc, Sigma_chunk);
+}
+
+// Screened direct term (THC_GW) with or without SOX, restricted: the bubble of every tau
+// point from the split projections first (the bosonic transform couples them), the
+// screening in FP64 (gw.cu), then per chunk SOX, the merge M = C_SOX D^T - G^X o W~ in
+// FP64, its split, and the split back-transform.
+int split_eval_gw(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
+  const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau, ldN = ctx->ldN, nn = n * n, NN = N * N;
+  const bool sox = ctx->terms & THC_SOX;
+  if (!ctx->gw_nw) return fail(ctx, THC_EINVAL, "THC_GW needs the bosonic transforms (thc_sigma_set_bosonic)");
+  for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
+    const long long tc = std::min<long long>(ctx->tc, nt - c0);
+    THC_TRY(split_project(ctx, G_tau, G_bmt, c0, tc, true, true));
+    THC_TRY(gw_store_bubble_f32(ctx, c0, tc));
+  }
+  THC_TRY(gw_screen(ctx));
+  for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
+    const long long tc = std::min<long long>(ctx->tc, nt - c0);
+    THC_TRY(split_project(ctx, G_tau, G_bmt, c0, tc, false, false));  // Y and G(-tau) for SOX
+    if (sox) THC_TRY(split_sox(ctx, tc));
+    THC_TRY(gw_merge(ctx, c0, tc, sox ? ctx->Dd : nullptr, ctx->gw_m));
+    const Split Ms = split3_of(ctx->Ms_h, ctx->Ms_l, ctx->Ms_l2, N, ldN, tc);
+    THC_TRY(launch_split_f64(ctx, ctx->gw_m, NN, N, 1, 1.0, Ms, N, "split M"));
+    THC_TRY(split_back(ctx, tc, Sigma + c0 * nn));
+  }
+  return THC_OK;
 }
 
 }  // namespace
@@ -772,8 +831,8 @@ int split_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const 
   const Split Vs = split3_of(ctx->Vs_h, ctx->Vs_l, ctx->Vs_l2, N, ldN);
   for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
     const long long tc = std::min<long long>(ctx->tc, nt - c0);
-    const Split Pis = split_of(ctx->Pis_h, ctx->Pis_l, N, ldN, tc);
-    const Split Ts = split_of(ctx->Ts_h, ctx->Ts_l, N, ldN, tc);
+    const Split Pis = split3_of(ctx->Pis_h, ctx->Pis_l, ctx->Pis_l2, N, ldN, tc);
+    const Split Ts = split3_of(ctx->Ts_h, ctx->Ts_l, ctx->Ts_l2, N, ldN, tc);
     if (nspin == 2 && dir) {
       THC_TRY(split_project(ctx, G_tau[1], G_bmt[1], c0, tc, true, true));
       THC_TRY(split_polarisation(ctx, tc, nullptr, ctx->Pif));
@@ -782,7 +841,7 @@ int split_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const 
     if (dir) {
       THC_TRY(split_polarisation(ctx, tc, nspin == 2 ? ctx->Pif : nullptr, nullptr));
       THC_TRY(gemm(ctx, K_DIRECT_VPI, Vs, false, Pis, true, N, N, N, tc,
-                   EpiSplit<false>{Ts.hi, Ts.lo, ldN, N * ldN, 1.f}, "V Pi"));
+                   EpiSplit<false>{Ts.hi, Ts.lo, ldN, N * ldN, 1.f, Ts.lo2}, "V Pi"));
     }
     for (int s = 0; s < nspin; ++s) {
       if (s == 1) THC_TRY(split_project(ctx, G_tau[1], G_bmt[1], c0, tc, dir, false));
@@ -794,6 +853,7 @@ int split_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const 
 }
 
 int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
+  if (ctx->terms & THC_GW) return split_eval_gw(ctx, G_tau, G_bmt, Sigma);
   return split_eval_spins(ctx, 1, &G_tau, &G_bmt, &Sigma);
 }
 

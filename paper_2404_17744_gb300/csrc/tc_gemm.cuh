@@ -7,7 +7,9 @@
 // lo = bf16(x - hi) (about 17 significant bits together).  The constant
 // operands X and V may carry a third term lo2 = bf16(x - hi - lo) (AT = 3,
 // one more product Alo2 Bhi per step): their rounding is coherent across the
-// whole scheme and otherwise dominates the error of the energy.  Both operands are
+// whole scheme and otherwise dominates the error of the energy.  A data operand may
+// carry the third term as well (BT = 3, with AT = 3: two more products, hi lo2 and
+// lo lo, so that every product down to 2^-16 relative is kept).  Both operands are
 // K-major (k contiguous), which every contraction of the THC scheme can be
 // brought to by the symmetry of G, U_Pqs and V or by writing its producer's
 // output transposed.
@@ -22,7 +24,7 @@
 //   warp 0    one lane issues the TMA loads (128-byte swizzle) of the four
 //             (AT = 3: five) operand tiles of each 64-deep K stage into a
 //             STAGES-deep ring;
-//   warp 1    allocates TMEM; one lane issues the (AT + 1) x 4 tcgen05.mma
+//   warp 1    allocates TMEM; one lane issues the (AT + 1 + 2 (BT - 2)) x 4 tcgen05.mma
 //             (kind::f16, M = 128, N = BN, K = 16) of a stage into one of two
 //             TMEM accumulators (stages alternate between them) and commits
 //             the stage back to the producer and to the epilogue (ragged
@@ -74,11 +76,14 @@ constexpr unsigned long long kWaitLimitNs = 4000000000ull;  // 4 s per wait
 // AT = number of BF16 terms of the A operand: 2 (hi, lo) or 3 (hi, lo, lo2 =
 // bf16(x - hi - lo), about 24 significant bits together, for the constant
 // operands X and V whose rounding otherwise dominates the energy error).
-template <int BN, int AT = 2>
+// BT = number of BF16 terms of the B operand: 2, or 3 for data operands kept to about
+// 24 bits (then the products down to 2^-16 relative are all issued: hi hi, hi lo,
+// lo hi, lo2 hi, hi lo2 and lo lo).
+template <int BN, int AT = 2, int BT = 2>
 struct Cfg {
   static constexpr int A_BYTES = BM * BKE * 2;
   static constexpr int B_BYTES = BN * BKE * 2;
-  static constexpr int STAGE = AT * A_BYTES + 2 * B_BYTES;
+  static constexpr int STAGE = AT * A_BYTES + BT * B_BYTES;
   static constexpr int TMEM_COLS = 2 * BN;   // two accumulators; BN in {128, 256}
   // promoted mode: each of the two stage buffers holds the hi*hi products and, in a second
   // accumulator, the small correction products (BN = 128 only)
@@ -91,6 +96,7 @@ struct Cfg {
   static_assert(SMEM <= 232448, "shared memory per CTA");
   static_assert(BN == 128 || BN == 256, "tile width");
   static_assert(AT == 2 || AT == 3, "A operand terms");
+  static_assert(BT == 2 || (BT == 3 && AT == 3), "B operand terms (three only with a three-term A)");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -249,13 +255,13 @@ struct Operands {
   int a_batched, b_batched;
 };
 
-template <int BN, bool MULTI, int AT, class Epi>
+template <int BN, bool MULTI, int AT, class Epi, int BT = 2>
 __global__ void __launch_bounds__(NTHREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                       const __grid_constant__ CUtensorMap mAlo2, const __grid_constant__ CUtensorMap mBhi,
-                      const __grid_constant__ CUtensorMap mBlo, int M, int N, int K, int batch, Operands ops, Epi epi,
-                      int* err) {
-  using C = Cfg<BN, AT>;
+                      const __grid_constant__ CUtensorMap mBlo, const __grid_constant__ CUtensorMap mBlo2, int M, int N,
+                      int K, int batch, Operands ops, Epi epi, int* err) {
+  using C = Cfg<BN, AT, BT>;
   constexpr int B_OFF = AT * C::A_BYTES;  // B hi, then B lo, after the A terms of a stage
   constexpr int TCOLS = MULTI ? C::TMEM_COLS_MULTI : C::TMEM_COLS;
   static_assert(TCOLS <= 512, "TMEM columns");
@@ -288,6 +294,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     prefetch_map(&mAhi);
     prefetch_map(&mAlo);
     if (AT == 3) prefetch_map(&mAlo2);
+    if (BT == 3) prefetch_map(&mBlo2);
     prefetch_map(&mBhi);
     prefetch_map(&mBlo);
   }
@@ -322,6 +329,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (AT == 3) tma_load_3d(st + 2 * C::A_BYTES, &mAlo2, &full[s], kb * BKE, mt * BM, ab);
           tma_load_3d(st + B_OFF, &mBhi, &full[s], kb * BKE, nt * BN, bb);
           tma_load_3d(st + B_OFF + C::B_BYTES, &mBlo, &full[s], kb * BKE, nt * BN, bb);
+          if (BT == 3) tma_load_3d(st + B_OFF + 2 * C::B_BYTES, &mBlo2, &full[s], kb * BKE, nt * BN, bb);
         }
       }
       // every copy issued has landed before the CTA may leave (immediate unless a wait ran out)
@@ -361,6 +369,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint64_t ah = sw128_desc(base), al = sw128_desc(base + C::A_BYTES);
           const uint64_t al2 = sw128_desc(base + 2 * C::A_BYTES);
           const uint64_t bh = sw128_desc(base + B_OFF), bl = sw128_desc(base + B_OFF + C::B_BYTES);
+          const uint64_t bl2 = sw128_desc(base + B_OFF + 2 * C::B_BYTES);
           // the last stage of a ragged K issues only the 16-deep steps that reach below K
           const int ksteps = min(BKE / 16, (K - kb * BKE + 15) >> 4);
 #pragma unroll
@@ -371,6 +380,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               mma_bf16(dc, ah + off, bl + off, idesc, MULTI ? (k != 0) : 1u);
               mma_bf16(dc, al + off, bh + off, idesc, 1u);
               if (AT == 3) mma_bf16(dc, al2 + off, bh + off, idesc, 1u);
+              if (BT == 3) {
+                mma_bf16(dc, ah + off, bl2 + off, idesc, 1u);
+                mma_bf16(dc, al + off, bl + off, idesc, 1u);
+              }
             }
           }
           mma_commit(&empty[s]);  // frees the smem stage once these MMAs have read it

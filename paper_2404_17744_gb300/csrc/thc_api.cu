@@ -222,8 +222,6 @@ int ctx_create(thc_ctx** out, int n_ao, int n_thc, int n_tau, double beta, const
   if (precision != THC_FP64 && precision != THC_BF16X3) return fail(nullptr, THC_EINVAL, "unknown precision");
   if (terms <= 0 || terms > (THC_DIRECT | THC_SOX | THC_GW) || ((terms & THC_DIRECT) && (terms & THC_GW)))
     return fail(nullptr, THC_EINVAL, "terms must be THC_DIRECT and/or THC_SOX, or THC_GW with or without THC_SOX");
-  if ((terms & THC_GW) && precision != THC_FP64)
-    return fail(nullptr, THC_ENOTSUP, "the screened (GW) term runs on the FP64 path only");
   thc_ctx* ctx = nullptr;
   try {
     ctx = new thc_ctx();

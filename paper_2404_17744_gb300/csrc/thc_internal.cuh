@@ -87,6 +87,9 @@ struct thc_ctx {
   __nv_bfloat16 *Ts_h = nullptr, *Ts_l = nullptr;   // V Pi, tc x N x ldN
   __nv_bfloat16 *Ms_h = nullptr, *Ms_l = nullptr;   // merged M, tc x N x ldN
   __nv_bfloat16 *T2s_h = nullptr, *T2s_l = nullptr; // (M X^T)^T, tc x n x ldN
+  // third terms of the data operands of the direct chain and the back-transform (24 bits)
+  __nv_bfloat16 *Gs_l2 = nullptr, *Gms_l2 = nullptr, *Ys_l2 = nullptr, *Yms_l2 = nullptr;
+  __nv_bfloat16 *Pis_l2 = nullptr, *Ts_l2 = nullptr, *Ms_l2 = nullptr, *T2s_l2 = nullptr;
   __nv_bfloat16 *Ats_h = nullptr, *Ats_l = nullptr; // A^T blocks, Pb x n x ldn
   double *Dd = nullptr;                             // D, tc x N x N
   float *Pif = nullptr;                             // Pi of spin b, tc x N x N (unrestricted only)
@@ -98,6 +101,8 @@ struct thc_ctx {
   double *gw_gx = nullptr;                          // G^X(tau), n_tau x N x N
   double *gw_w = nullptr;                           // W(i Omega), n_omega x N x N
   double *gw_scr = nullptr;                         // Gauss-Jordan scratch
+  double *gw_m = nullptr;                           // split path: M of a chunk, tc x N x N
+  size_t gw_scr_elems = 0;
   // device status words: [0] a tensor-core pipeline wait that ran out (its code),
   // [1] a non-finite value met in G_tau / G_bmt by an evaluation; read and cleared by status_check
   int *d_err = nullptr;
@@ -157,6 +162,7 @@ int gj_invert_spd(thc_ctx* ctx, double* A, long long n, long long batch);
 int gw_set_transforms(thc_ctx* ctx, int n_omega, const double* to_iw, const double* to_tau);
 int gw_store_bubble(thc_ctx* ctx, long long c0, long long tc);
 int gw_screen(thc_ctx* ctx);
+int gw_store_bubble_f32(thc_ctx* ctx, long long c0, long long tc);
 int gw_merge(thc_ctx* ctx, long long c0, long long tc, const double* D, double* M);
 
 // autotuner table of the split contractions (sigma_split.cu)

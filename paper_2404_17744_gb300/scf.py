@@ -42,7 +42,8 @@ class IterationRecord:
 
 
 class GF2Loop:
-    """Fully self-consistent GF2 with THC self-energies on one GPU.
+    """Fully self-consistent GF2 (or, with `bosonic` transforms, scGWSOX) with THC
+    self-energies on one GPU.
 
     grid: an object with tau, iw, U_tau, fit_tau, U_iw, fit_iw, u_beta, u_zero
     and basis.beta / basis.L (workloads.ir.LoopGrid); the tau points must be
@@ -50,7 +51,7 @@ class GF2Loop:
     """
 
     def __init__(self, X, V, F, S, grid, n_elec, precision=thc.THC_FP64, device="cuda:0", stream=None,
-                 damping=0.5, n_damp=2, diis_size=6, mixing="diis"):
+                 damping=0.5, n_damp=2, diis_size=6, mixing="diis", bosonic=None):
         import torch
         self.torch = torch
         self.dev = torch.device(device)
@@ -74,8 +75,13 @@ class GF2Loop:
             self.Sig_in = torch.zeros_like(self.G)
             self.scratch = torch.empty(512, dtype=torch.float64, device=self.dev)
         s = self.stream.cuda_stream
+        # bosonic: transforms (to_iw, to_tau) of the grid for the screened direct term, i.e. the
+        # scGWSOX loop (Sigma = Sigma^GW + Sigma^SOX); None: the GF2 loop (direct + SOX)
+        terms = (thc.THC_GW | thc.THC_SOX) if bosonic is not None else (thc.THC_DIRECT | thc.THC_SOX)
         self.ctx = thc.thc_sigma_init(self.n, self.N, self.n_tau, grid.basis.beta, self.X, self.V,
-                                      np.ascontiguousarray(grid.tau), precision, thc.THC_DIRECT | thc.THC_SOX, s)
+                                      np.ascontiguousarray(grid.tau), precision, terms, s)
+        if bosonic is not None:
+            thc.thc_sigma_set_bosonic(self.ctx, bosonic.to_iw, bosonic.to_tau)
         self.dy = thc.thc_dyson_init(self.n, self.n_tau, len(grid.iw), grid.basis.L, grid.basis.beta, self.S, self.F,
                                      grid.U_tau, grid.fit_tau, grid.U_iw, grid.fit_iw, grid.iw, grid.u_beta,
                                      grid.u_zero, s)

@@ -209,3 +209,37 @@ def test_cdiis_loop_matches_oracle_cdiis_loop():
     assert conv and ref["converged"]
     assert abs(recs[-1].E - ref["E"]) < 1e-9 and abs(recs[-1].E - plain["E"]) < 1e-9
     assert abs(len(recs) - ref["iters"]) <= 2
+
+
+def test_gwsox_loop_matches_oracle_loop():
+    """scGWSOX: the loop with the screened direct term (THC_GW | THC_SOX, FP64) against the
+    oracle's loop with sigma_gw_thc + SOX, on the same IR grid and bosonic transforms."""
+    from paper_2404_17744_gb300 import scf, thc
+    case = synth.make_sigma_case(20, 60, 4, 100.0, 17745, identity_S=False, n_occ=8)
+    g = grid_for(100.0, 10.0)
+    bt = ir.make_bosonic_transforms(g)
+    U = o.thc_U(case.X, case.V)
+
+    def sigma_fn(G_tau):
+        nt = G_tau.shape[0]
+        Gb = G_tau[::-1]
+        sox = np.stack([o.sigma_sox_thc(case.X, U, G_tau[k], o.g_minus_tau(Gb[k])) for k in range(nt)])
+        return o.sigma_gw_thc(case.X, case.V, G_tau, Gb, bt.to_iw, bt.to_tau) + sox
+
+    ref = so.run_loop(case, g, 8.0, tol=1e-10, sigma_fn=sigma_fn)
+    L = scf.GF2Loop(case.X, case.V, case.F, case.S, g, 8.0, precision=thc.THC_FP64, bosonic=bt)
+    try:
+        conv = L.run(tol=1e-10, max_iter=80)
+        recs = L.records
+    finally:
+        L.close()
+    gf2 = so.run_loop(case, g, 8.0, tol=1e-10)
+    print(f"scGWSOX oracle E {ref['E']:.12f} ({ref['iters']} it), GPU {recs[-1].E:.12f} ({len(recs)} it); "
+          f"GF2 E {gf2['E']:.12f}")
+    print("first energies, oracle / GPU:", [f"{h['E']:.10f}" for h in ref["history"][:6]],
+          [f"{r.E:.10f}" for r in recs[:6]])
+    assert conv and ref["converged"]
+    assert abs(recs[-1].E - ref["E"]) < 1e-9
+    assert abs(ref["E"] - gf2["E"]) > 1e-7           # the screening changes the converged energy
+    for r, h in zip(recs[:4], ref["history"][:4]):
+        assert abs(r.E - h["E"]) < 1e-9
