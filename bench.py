@@ -441,29 +441,38 @@ def leg_batch_c4(stream):
 
 def leg_c5(stream, fp64_rate):
     """c5 sizes: 1100 AOs, 5500 THC points, beta = 1000, IR grid with Lambda = 1e5: two iterations
-    of the 3xBF16 self-consistent loop (Sigma on every tau point, energy, mixing, Dyson with the
-    chemical-potential search) timed per iteration; the FP64 iteration time is extrapolated from
-    the FP64 Sigma rate measured on the 200-AO workload (the FP64 path is DFMA-bound at any size)."""
+    of the 3xBF16 scGWSOX loop (Sigma^GW + Sigma^SOX on every tau point, the screening in FP64,
+    energy, mixing, Dyson with the chemical-potential search) timed per iteration; the FP64
+    iteration time is extrapolated from the FP64 Sigma rate measured on the 200-AO workload (the
+    FP64 path is DFMA-bound at any size) plus the FP64 screening of this run."""
     from paper_2404_17744_gb300 import scf, thc
     from workloads import ir, synth
     case = synth.make_workload("thc1100", n_tau=2)
     grid = ir.make_loop_grid(1000.0, 100.0)
+    bt = ir.make_bosonic_transforms(grid)
     n_elec = float(np.sum(case.eps < 0))
     t0 = time.perf_counter()
-    L = scf.GF2Loop(case.X, case.V, case.F, case.S, grid, n_elec, precision=thc.THC_BF16X3, stream=stream)
+    L = scf.GF2Loop(case.X, case.V, case.F, case.S, grid, n_elec, precision=thc.THC_BF16X3, stream=stream,
+                    bosonic=bt)
+    thc.thc_profile(L.ctx, True)
     t_init = time.perf_counter() - t0
     try:
         L.run(tol=0.0, max_iter=2)
         recs = L.records
         flops = thc.thc_sigma_flops(L.ctx)[0]
+        screen = next((r for r in (thc.thc_profile_get(L.ctx, k) for k in range(32)) if r and r[0] == "screen"), None)
     finally:
         L.close()
     it = recs[-1]
-    return {"workload": f"c5: n_ao={case.n}, n_thc={case.N}, {len(grid.tau)} tau / {len(grid.iw)} Matsubara points "
-                        f"(IR, beta=1000, Lambda=1e5), 3xBF16 Sigma, FP64 Dyson",
+    screen_s = screen[2] * 1e-3 / len(recs) if screen else 0.0
+    screen_flops = screen[3] / len(recs) if screen else 0.0
+    return {"workload": f"c5: scGWSOX, n_ao={case.n}, n_thc={case.N}, {len(grid.tau)} tau / {len(grid.iw)} "
+                        f"Matsubara / {bt.to_iw.shape[0]} bosonic points (IR, beta=1000, Lambda=1e5), 3xBF16 "
+                        f"projections, SOX and back-transform, FP64 screening and Dyson",
             "init_s": t_init, "s_per_iteration_bf16x3": it.seconds, "sigma_s": it.sigma_seconds,
-            "sigma_tflops": flops / it.sigma_seconds / 1e12, "dyson_evals": it.dyson_evals,
-            "s_per_iteration_fp64_extrapolated": flops / (fp64_rate * 1e12) + (it.seconds - it.sigma_seconds),
+            "sigma_tflops": flops / it.sigma_seconds / 1e12, "screening_s": screen_s, "dyson_evals": it.dyson_evals,
+            "s_per_iteration_fp64_extrapolated": (flops - screen_flops) / (fp64_rate * 1e12) + screen_s
+                                                 + (it.seconds - it.sigma_seconds),
             "iterations_timed": len(recs)}
 
 
@@ -643,7 +652,7 @@ def run_batch64(args):
     return 0
 
 
-def run_c5_loop(args):
+def run_c5_loop(args, gw=False):
     """c5, learned part: the 3xBF16 GF2 loop at 1100 AOs, 5500 THC points, beta = 1000 (IR grid,
     Lambda = 1e5), plain damping against damping with one online-trained learned proposal
     (training inside the wall time), a fixed number of iterations each (args.steps, at least 8).
@@ -659,12 +668,13 @@ def run_c5_loop(args):
     stream = torch.cuda.Stream(device=torch.device("cuda", local))
     case = synth.make_workload("thc1100", n_tau=2)
     grid = ir.make_loop_grid(1000.0, 100.0)
+    bt = ir.make_bosonic_transforms(grid) if gw else None
     n_elec = float(np.sum(case.eps < 0))
     iters = max(8, args.steps)
     runs = {}
     for name, learned in (("damped", False), ("damped_learned", True)):
         L = scf.GF2Loop(case.X, case.V, case.F, case.S, grid, n_elec, precision=thc.THC_BF16X3, stream=stream,
-                        mixing="damp")
+                        mixing="damp", bosonic=bt)
         P = scf.LearnedProposer(L, max_proposals=1) if learned else None
         try:
             t0 = time.perf_counter()
@@ -687,7 +697,7 @@ def run_c5_loop(args):
     line = {"metric": METRIC, "value": None, "unit": "s per scGF2 iteration", "n_gpus": world, "steps": iters,
             "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
             "data": "synthetic",
-            "config": {"workload": f"c5 loop: n_ao={case.n}, n_thc={case.N}, {len(grid.tau)} tau / "
+            "config": {"workload": f"c5 {'scGWSOX' if gw else 'GF2'} loop: n_ao={case.n}, n_thc={case.N}, {len(grid.tau)} tau / "
                                    f"{len(grid.iw)} Matsubara points (IR, beta=1000, Lambda=1e5), 3xBF16 Sigma, "
                                    f"FP64 Dyson, damping 0.5, {iters} iterations per run"},
             "c5_learned": {"runs": runs, "final_E_difference": l["E"][-1] - d["E"][-1]}}
@@ -714,8 +724,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch64(args)
-    if args.workload == "c5loop":
-        return run_c5_loop(args)
+    if args.workload in ("c5loop", "c5loop_gw"):
+        return run_c5_loop(args, gw=args.workload == "c5loop_gw")
     return run_ours(args)
 
 
