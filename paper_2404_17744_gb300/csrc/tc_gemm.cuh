@@ -193,6 +193,20 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// The same for a narrow K block of 16 or 32 BF16 per row (32- or 64-byte rows, 32- or
+// 64-byte swizzle, 8-row groups 256 or 512 bytes apart): the last K block of a contraction
+// whose depth leaves only that much, loaded with a box as narrow.
+__device__ __forceinline__ uint64_t narrow_desc(uint32_t saddr, int width) {
+  const uint64_t row = static_cast<uint64_t>(width) * 2;  // bytes per row
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= ((8 * row) >> 4) << 32;                             // stride byte offset: one 8-row group
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(width == 16 ? 6 : 4) << 61;   // SWIZZLE_32B or SWIZZLE_64B
+  return d;
+}
+
 // Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |

@@ -19,7 +19,8 @@
 //     while the MMAs of the next accumulate.
 //
 // Warp roles as in split_gemm_kernel: warp 0 (one lane) loads the 64-deep K stages of
-// U rows and G(-tau) rows (hi and lo, 128-byte swizzle) by TMA; warp 1 allocates TMEM
+// U rows and G(-tau) rows (hi and lo, 128-byte swizzle; a last K block of at most 16 or
+// 32 columns in boxes that narrow) by TMA; warp 1 allocates TMEM
 // and one lane issues the 3 x 4 tcgen05.mma per stage (hi hi, hi lo, lo hi); warps 2-9
 // drain, split and store.  Every wait is bounded in time (mbarriers, globaltimer); a
 // wait that runs out sets *err and the CTA unwinds after draining its own copies, MMAs
@@ -52,11 +53,13 @@ struct SoxAArgs {
   int nvt;       // v blocks per item row: ceil(n / 256)
   int brows;     // rows of the G box: min(256, round-up-16(n))
   uint32_t tx;   // bytes per stage: 2 (128 + brows) 128
+  int tail;      // 16 or 32: the last K block (n mod 64 <= tail) is loaded with boxes that wide; 0: 64
 };
 
-// U: rows P n + q of the block (K = s); G: rows v (K = s); At: 3-D (q, v, P) store maps.
+// U: rows P n + q of the block (K = s); G: rows v (K = s); At: 3-D (q, v, P) store maps;
+// ut*, gt*: the narrow boxes of a shallow last K block.
 struct SoxAMaps {
-  CUtensorMap uh, ul, gh, gl, ath, atl;
+  CUtensorMap uh, ul, gh, gl, ath, atl, uth, utl, gth, gtl;
 };
 
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int c0, int c1, int c2) {
@@ -118,6 +121,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     prefetch_map(&maps.gl);
     prefetch_map(&maps.ath);
     prefetch_map(&maps.atl);
+    if (a.tail) {
+      prefetch_map(&maps.uth);
+      prefetch_map(&maps.utl);
+      prefetch_map(&maps.gth);
+      prefetch_map(&maps.gtl);
+    }
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -144,11 +153,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             break;
           }
           uint8_t* st = smem + s * C::STAGE;
-          mbar_arrive_expect_tx(&full[s], a.tx);
-          tma_load_3d(st, &maps.uh, &full[s], kb * BKE, urow, 0);
-          tma_load_3d(st + C::A_BYTES, &maps.ul, &full[s], kb * BKE, urow, 0);
-          tma_load_3d(st + 2 * C::A_BYTES, &maps.gh, &full[s], kb * BKE, grow, 0);
-          tma_load_3d(st + 2 * C::A_BYTES + C::B_BYTES, &maps.gl, &full[s], kb * BKE, grow, 0);
+          const bool tl = a.tail && kb == nkb - 1;  // narrow last K block: rows of 2 a.tail bytes
+          mbar_arrive_expect_tx(&full[s], tl ? (uint32_t)(2 * (BM + a.brows) * 2 * a.tail) : a.tx);
+          tma_load_3d(st, tl ? &maps.uth : &maps.uh, &full[s], kb * BKE, urow, 0);
+          tma_load_3d(st + C::A_BYTES, tl ? &maps.utl : &maps.ul, &full[s], kb * BKE, urow, 0);
+          tma_load_3d(st + 2 * C::A_BYTES, tl ? &maps.gth : &maps.gh, &full[s], kb * BKE, grow, 0);
+          tma_load_3d(st + 2 * C::A_BYTES + C::B_BYTES, tl ? &maps.gtl : &maps.gl, &full[s], kb * BKE, grow, 0);
         }
       }
       if (!drain_stages(full, C::STAGES, g)) atomicExch(err, 24);
@@ -178,8 +188,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           tc_fence_after();
           const uint32_t base = smem_u32(smem + s * C::STAGE);
-          const uint64_t ah = sw128_desc(base), al = sw128_desc(base + C::A_BYTES);
-          const uint64_t bh = sw128_desc(base + 2 * C::A_BYTES), bl = sw128_desc(base + 2 * C::A_BYTES + C::B_BYTES);
+          const bool tl = a.tail && kb == nkb - 1;
+          auto desc = [&](uint32_t addr) { return tl ? narrow_desc(addr, a.tail) : sw128_desc(addr); };
+          const uint64_t ah = desc(base), al = desc(base + C::A_BYTES);
+          const uint64_t bh = desc(base + 2 * C::A_BYTES), bl = desc(base + 2 * C::A_BYTES + C::B_BYTES);
           const int ksteps = min(BKE / 16, (a.n - kb * BKE + 15) >> 4);
 #pragma unroll
           for (int k = 0; k < BKE / 16; ++k) {
