@@ -81,7 +81,11 @@ def test_split_thc20_workload():
     _check(synth.make_workload("thc20"))
 
 
-@pytest.mark.parametrize("n,N,n_tau,seed", [(37, 131, 6, 1), (65, 67, 4, 2), (1, 1, 2, 3), (130, 70, 2, 6)])
+# n around the 64-column K blocks (a shallow last block is loaded in 16- or 32-column
+# boxes), the 128-row q blocks of the A contraction and its 256-column v blocks
+@pytest.mark.parametrize("n,N,n_tau,seed", [(37, 131, 6, 1), (65, 67, 4, 2), (1, 1, 2, 3), (130, 70, 2, 6),
+                                            (63, 70, 2, 7), (64, 96, 2, 8), (96, 100, 2, 12), (129, 140, 2, 9),
+                                            (257, 270, 2, 10)])
 def test_split_ragged(n, N, n_tau, seed):
     _check(synth.make_sigma_case(n, N, n_tau, 30.0, seed))
 
