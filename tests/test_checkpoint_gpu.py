@@ -9,6 +9,8 @@ metrics (host control around the library's kernels).
 * The metrics file has one JSON line per iteration with the energy, its change,
   mu, the electron count, the residual and the per-kernel-class GPU times.
 * A checkpoint of another loop (other sizes) is refused.
+* run_loop(LoopConfig) reproduces the hand-built loop, resumes from its checkpoint,
+  keeps the autotuner cache and runs the scGWSOX method.
 """
 import json
 
@@ -125,3 +127,40 @@ def test_checkpoint_of_another_loop_is_refused(tmp_path):
         assert L.iteration == 0
     finally:
         L.close()
+
+
+def test_run_loop_from_config(tmp_path):
+    """run_loop(config) gives the loop of the same knobs set by hand, resumes from its
+    checkpoint, writes its metrics and saves the autotuner cache; the scGWSOX method runs
+    with the bosonic transforms."""
+    from paper_2404_17744_gb300 import scf, thc
+    from paper_2404_17744_gb300.config import LoopConfig, run_loop
+    case, g = _case(), _grid()
+    cfg = LoopConfig(precision="fp64", mixing="diis", tol=1e-10, max_iter=60,
+                     checkpoint=str(tmp_path / "c.npz"), metrics=str(tmp_path / "c.jsonl"))
+    conv, recs = run_loop(case.X, case.V, case.F, case.S, g, 8.0, cfg)
+    L = scf.GF2Loop(case.X, case.V, case.F, case.S, g, 8.0, precision=thc.THC_FP64)
+    try:
+        assert L.run(tol=1e-10, max_iter=60)
+        ref = [r.E for r in L.records]
+    finally:
+        L.close()
+    assert conv and [r.E for r in recs] == ref
+    assert len(open(tmp_path / "c.jsonl").read().splitlines()) == len(ref)
+    # a run cut short and resumed from the checkpoint by a second call
+    short = LoopConfig(**{**cfg.__dict__, "max_iter": 3, "metrics": None})
+    assert not run_loop(case.X, case.V, case.F, case.S, g, 8.0, short)[0]
+    conv2, recs2 = run_loop(case.X, case.V, case.F, case.S, g, 8.0, LoopConfig(**{**cfg.__dict__, "metrics": None}),
+                            resume=True)
+    assert conv2 and [r.E for r in recs2] == ref
+    # 3xBF16 with the autotuner cache; scGWSOX with the screened term
+    tiles = tmp_path / "tiles.txt"
+    c3 = LoopConfig(precision="bf16x3", mixing="damp", tol=1e-6, max_iter=80, learned_proposals=1,
+                    autotune_cache=str(tiles))
+    conv3, recs3 = run_loop(case.X, case.V, case.F, case.S, g, 8.0, c3)
+    assert conv3 and tiles.exists() and abs(recs3[-1].E - ref[-1]) < 1e-5
+    cg = LoopConfig(method="gwsox", tol=1e-10, max_iter=60)
+    with pytest.raises(ValueError):
+        run_loop(case.X, case.V, case.F, case.S, g, 8.0, cg)
+    conv4, recs4 = run_loop(case.X, case.V, case.F, case.S, g, 8.0, cg, bosonic=ir.make_bosonic_transforms(g))
+    assert conv4 and abs(recs4[-1].E - ref[-1]) > 1e-7   # the screening moves the energy
