@@ -143,9 +143,8 @@ __global__ void gw_merge_kernel(long long N, long long batch, const double* __re
   const long long NN = N * N, total = NN * batch;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long b = idx / NN, r = idx - b * NN, R = r / N, P = r - R * N;
     double m = -GX[idx] * Wt[idx];
-    if (D) m += D[b * NN + P * N + R];
+    if (D) m += D[idx];  // D[P][R] = D[R][P]: D is mirrored to symmetric before the merge
     M[idx] = m;
   }
 }

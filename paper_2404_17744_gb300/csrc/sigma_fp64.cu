@@ -142,7 +142,7 @@ struct MergeEpi {
   __device__ __forceinline__ void operator()(long long b, long long r, long long p, double w) const {
     const long long o = b * N * N;
     double m = cd * GXp[o + r * N + p] * w;
-    if (D) m = fma(C_SOX, D[o + p * N + r], m);
+    if (D) m = fma(C_SOX, D[o + r * N + p], m);  // D[p][r] = D[r][p] (mirrored): read like GXp
     M[o + r * N + p] = m;
   }
 };

@@ -209,7 +209,7 @@ struct EpiMerge {
       const int R = row0 + r;
       if (R >= M) break;
       double m = cd * (double)GX[b * NN + (long long)R * N + P] * (double)t(r, lane);
-      if (D) m += C_SOX * D[b * NN + (long long)P * N + R];
+      if (D) m += C_SOX * D[b * NN + (long long)R * N + P];  // D is symmetric (mirrored): D[P][R] = D[R][P]
       split_store3(hi, lo, lo2, (long long)b * N * ld + (long long)R * ld + P, (float)m);
     }
   }
@@ -805,8 +805,8 @@ int split_merge_back(thc_ctx* ctx, long long tc, bool sox, bool dir, double cd, 
     THC_TRY(gemm(ctx, K_DIRECT_W, Vs, false, Ts, true, N, N, N, tc,
                  EpiMerge{Ms.hi, Ms.lo, ldN, sox ? ctx->Dd : nullptr, ctx->GXf, (int)N, cd, Ms.lo2}, "W"));
   } else {
-    // M[R][P] = c_x D[P][R]
-    THC_TRY(launch_split_f64(ctx, ctx->Dd, NN, 1, N, C_SOX, Ms, N, "split D^T"));
+    // M[R][P] = c_x D[P][R] = c_x D[R][P] (D mirrored): read along its rows
+    THC_TRY(launch_split_f64(ctx, ctx->Dd, NN, N, 1, C_SOX, Ms, N, "split D^T"));
   }
   return split_back(ctx, tc, Sigma_chunk);
 }
