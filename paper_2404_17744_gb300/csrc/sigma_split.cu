@@ -204,13 +204,24 @@ struct EpiMerge {
     const int P = col0 + lane;
     if (P >= Ncols) return;
     const long long NN = (long long)N * N;
-#pragma unroll 4
-    for (int r = 0; r < 32; ++r) {
-      const int R = row0 + r;
-      if (R >= M) break;
-      double m = cd * (double)GX[b * NN + (long long)R * N + P] * (double)t(r, lane);
-      if (D) m += C_SOX * D[b * NN + (long long)R * N + P];  // D is symmetric (mirrored): D[P][R] = D[R][P]
-      split_store3(hi, lo, lo2, (long long)b * N * ld + (long long)R * ld + P, (float)m);
+    // 16 rows at a time: all their G^X and D loads are issued before the first is used
+    for (int r0 = 0; r0 < 32; r0 += 16) {
+      float gx[16];
+      double dv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int R = row0 + r0 + i;
+        const long long o = b * NN + (long long)R * N + P;
+        gx[i] = R < M ? GX[o] : 0.f;
+        dv[i] = (D && R < M) ? D[o] : 0.0;  // D is symmetric (mirrored): D[P][R] = D[R][P]
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int R = row0 + r0 + i;
+        if (R >= M) return;
+        const double m = cd * (double)gx[i] * (double)t(r0 + i, lane) + C_SOX * dv[i];
+        split_store3(hi, lo, lo2, (long long)b * N * ld + (long long)R * ld + P, (float)m);
+      }
     }
   }
 };
