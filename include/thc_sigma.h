@@ -128,9 +128,10 @@ int thc_sigma_eval(thc_ctx *ctx, const double *G_tau, const double *G_bmt, doubl
  * Both map real functions symmetric under tau -> beta - tau (Pi~ and W~ of real
  * symmetric G); the frequencies need not be listed.  The first call allocates
  * 2 n_tau + n_omega + 1 N x N FP64 arrays (THC_BF16X3: tc more, the merged M of a tau
- * chunk) and inverts V on the device.  The transforms, the inversions (Gauss-Jordan
- * without pivoting, SPD; in blocks of 64 pivots with DFMA trailing updates above
- * N = 128) and the merge run in FP64 on both paths; THC_BF16X3 takes G^X from its
+ * chunk) and inverts V on the device.  The transforms, the inversions (SPD, without
+ * pivoting: Gauss-Jordan up to N = 128, above that the symmetric sweep in blocks of
+ * 64 pivots on the upper triangle with DFMA trailing updates, N^3 flops) and the
+ * merge run in FP64 on both paths; THC_BF16X3 takes G^X from its
  * split projections (FP32) and runs the back-transform on the tensor cores.
  * THC_EINVAL without THC_GW.  Synchronises.
  */

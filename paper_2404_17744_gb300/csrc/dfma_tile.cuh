@@ -173,7 +173,7 @@ struct TriStoreEpi {
   __device__ __forceinline__ void operator()(long long b, long long m, long long c, double v) const {
     p[b * sb + m * sr + c * sc] = alpha * v;
   }
-  __device__ __forceinline__ bool skip_tile(long long b, long long c_end) const { return c_end <= c0 + b; }
+  __device__ __forceinline__ bool skip_tile(long long b, long long, long long c_end) const { return c_end <= c0 + b; }
 };
 
 template <class E, class = void>
@@ -182,7 +182,8 @@ template <class E>
 struct HasSkipTile<E, std::void_t<decltype(&E::skip_tile)>> : std::true_type {};
 
 // Generic batched contraction: C(b) = epi(A(b) B(b)); grid (ceil(M/BM), ceil(Nn/BN), batch).
-// An epilogue with skip_tile(b, c_end) drops whole CTA tiles it does not need.
+// An epilogue with skip_tile(b, m0, c_end) drops whole CTA tiles (rows m0 .., columns
+// below c_end) it does not need.
 template <bool AK, bool BK_, class LA, class LB, class Epi>
 __global__ void __launch_bounds__(NT) gemm_kernel(long long M, long long Nn, long long K, LA la, LB lb,
                                                   Epi epi) {
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(long long M, long long Nn, lon
   const long long b = blockIdx.z;
   const long long m0 = (long long)blockIdx.x * BM, n0 = (long long)blockIdx.y * BN;
   if constexpr (HasSkipTile<Epi>::value) {
-    if (epi.skip_tile(b, n0 + BN)) return;
+    if (epi.skip_tile(b, m0, n0 + BN)) return;
   }
   const Lane L;
   double acc[4][4];

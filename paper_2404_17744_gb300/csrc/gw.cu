@@ -7,12 +7,13 @@
 //   W~(tau_k)  = sum_m to_tau[k][m] (W - V)(i W_m)
 //   Sigma^GW   = -X (G^X(tau) o W~(tau)) X^T
 //
-// W is formed as the inverse of the symmetric positive definite V^{-1} - Pi~, a
-// Gauss-Jordan elimination without pivoting (stable for SPD matrices), batched
-// over the sampled frequencies; V^{-1} is formed the same way once per context.
-// Matrices up to 2 kGJBlock rows are eliminated one pivot at a time; larger ones in
-// blocks of kGJBlock pivots, whose trailing updates (2 N^2 kGJBlock flops each, 2 N^3
-// in all) run in the DFMA contraction tile.
+// W is formed as the inverse of the symmetric positive definite V^{-1} - Pi~, an
+// elimination without pivoting (stable for SPD matrices), batched over the sampled
+// frequencies; V^{-1} is formed the same way once per context.  Matrices up to
+// 2 kGJBlock rows are eliminated one pivot at a time (Gauss-Jordan); larger ones by
+// the symmetric sweep in blocks of kGJBlock pivots on the upper triangle, whose
+// trailing updates (N^2 kGJBlock flops each, N^3 in all) run in the DFMA
+// contraction tile.
 // The transforms to_iw, to_tau are inputs (the bosonic sampling matrices of the
 // caller's tau grid).  All arithmetic is FP64 in the DFMA tile or plain kernels.
 #include <algorithm>
@@ -60,42 +61,73 @@ __global__ void gj_update_kernel(long long n, int k, long long batch, double* __
   }
 }
 
-// Blocked elimination, step at pivots k0 .. k0 + kb - 1 of `batch` n x n matrices A:
-// C = A[:, k], R = A[k, :], P = A[k, k] copied out (C: n x kb, R: kb x n, P: kb x kb).
-__global__ void gj_panels_kernel(long long n, long long k0, long long kb, long long batch, const double* __restrict__ A,
-                                 double* __restrict__ C, double* __restrict__ R, double* __restrict__ P) {
+// Blocked symmetric sweep (matrices of more than 2 kGJBlock rows).  Only the upper
+// triangle (i <= j) of A is read or written; sym(i, j) is element (min, max).
+// Step at pivots k0 .. k0 + kb - 1: CT[c][i] = sym(i, k0 + c) (n columns of kb rows)
+// and P = A[k, k] copied out.
+__global__ void sym_panels_kernel(long long n, long long k0, long long kb, long long batch,
+                                  const double* __restrict__ A, double* __restrict__ CT, double* __restrict__ P) {
   const long long per = n * kb, total = per * batch;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long b = idx / per, e = idx - b * per, i = e / kb, c = e - i * kb;
+    const long long b = idx / per, e = idx - b * per, c = e / n, i = e - c * n, k = k0 + c;
     const double* a = A + b * n * n;
-    C[idx] = a[i * n + k0 + c];                                   // C[b][i][c]
-    const long long r = e / n, j = e - r * n;                     // the same count, kb x n
-    R[idx] = a[(k0 + r) * n + j];                                 // R[b][r][j]
-    if (j < kb) P[b * kb * kb + r * kb + j] = a[(k0 + r) * n + k0 + j];
+    const double v = i <= k ? a[i * n + k] : a[k * n + i];
+    CT[idx] = v;
+    if (i >= k0 && i < k0 + kb) P[b * kb * kb + c * kb + (i - k0)] = v;
   }
 }
 
-// A[k, :] = R' = P R except A[k, k] = P (P = A[k, k]^{-1}).
-__global__ void gj_rows_kernel(long long n, long long k0, long long kb, long long batch, const double* __restrict__ Rp,
-                               const double* __restrict__ P, double* __restrict__ A) {
+// After the trailing update, with Rp = P C^T (kb x n, P = A[k, k]^{-1}): the block row
+// A[k][j] = Rp[:, j] (j > k), the block column A[i][k] = Rp[:, i]^T (i < k), and
+// A[k, k] = -P.
+__global__ void sym_rows_kernel(long long n, long long k0, long long kb, long long batch, const double* __restrict__ Rp,
+                                const double* __restrict__ P, double* __restrict__ A) {
   const long long per = kb * n, total = per * batch;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long b = idx / per, e = idx - b * per, r = e / n, j = e - r * n;
-    const bool diag = j >= k0 && j < k0 + kb;
-    A[b * n * n + (k0 + r) * n + j] = diag ? P[b * kb * kb + r * kb + (j - k0)] : Rp[idx];
+    double* a = A + b * n * n;
+    if (j < k0)
+      a[j * n + k0 + r] = Rp[idx];
+    else if (j < k0 + kb)
+      a[(k0 + r) * n + j] = -P[b * kb * kb + r * kb + (j - k0)];
+    else
+      a[(k0 + r) * n + j] = Rp[idx];
   }
 }
 
-// A(b, m, c) -= v: the trailing update of a blocked step.
-struct SubEpi {
+// A(b, m, c) -= v on and above the diagonal (m <= c); tiles wholly below it are skipped.
+struct SymSubEpi {
   double* p;
   long long sb, sr;
   __device__ __forceinline__ void operator()(long long b, long long m, long long c, double v) const {
-    p[b * sb + m * sr + c] -= v;
+    if (m <= c) p[b * sb + m * sr + c] -= v;
   }
+  __device__ __forceinline__ bool skip_tile(long long, long long m0, long long c_end) const { return c_end <= m0; }
 };
+
+// The sweep of every pivot leaves -A^{-1} in the upper triangle: A <- -sym(A), both
+// triangles, through a 32 x 32 tile in shared memory (grid: column tile, row tile, batch).
+__global__ void sym_finish_kernel(long long n, double* __restrict__ A) {
+  __shared__ double t[32][33];
+  const long long ti = blockIdx.y, tj = blockIdx.x;
+  if (ti > tj) return;
+  double* a = A + (long long)blockIdx.z * n * n;
+  const long long i0 = ti * 32, j0 = tj * 32;
+  const int x = threadIdx.x & 31, y0 = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int y = y0; y < 32; y += 8) {
+    const long long i = i0 + y, j = j0 + x;
+    if (i < n && j < n && i <= j) t[y][x] = -a[i * n + j];
+  }
+  __syncthreads();
+  for (int y = y0; y < 32; y += 8) {
+    const long long i = i0 + y, j = j0 + x;   // upper tile, element (i, j)
+    if (i < n && j < n && i <= j) a[i * n + j] = t[y][x];
+    const long long il = j0 + y, jl = i0 + x;  // lower tile, element (il, jl) = (jl, il) of the upper
+    if (il < n && jl < n && il > jl) a[il * n + jl] = t[x][y];
+  }
+}
 
 // Pi~[k0 + b] = 2 GXp[b] o GXm[b]^T and GX[k0 + b] = GXp[b] for the tau points of a chunk.
 __global__ void gw_bubble_kernel(long long N, long long batch, const double* __restrict__ GXp,
@@ -177,55 +209,58 @@ int gj_invert_unblocked(thc_ctx* ctx, double* A, long long n, long long batch, d
   return THC_OK;
 }
 
-// In-place inverse of `batch` SPD n x n matrices at A (no pivoting).  A blocked step
-// at pivots k (P = A_kk^{-1}, C = A[:, k], R = A[k, :] before the step) sets
-//   A_ij -= C_i (P R_j)   (i, j outside k),   A_ik = -C_i P,   A_kj = P R_j,   A_kk = P,
-// the Gauss-Jordan step with a kb x kb pivot: all four follow from updating every
-// (i, j) with C (P R), then overwriting the block column and the block row.
+// In-place inverse of `batch` SPD n x n matrices at A (no pivoting).  Up to 2 kGJBlock
+// rows: Gauss-Jordan one pivot at a time.  Above that: the symmetric sweep in blocks of
+// kb pivots, which keeps the matrix symmetric at every step and so works on the upper
+// triangle alone.  A step at pivots k (P = A_kk^{-1}, C = A[:, k] before the step) sets
+//   A_ij -= C_i P C_j^T   (i, j outside k),   A_ik = C_i P,   A_kj = P C_j^T,   A_kk = -P;
+// after every pivot has been swept the matrix holds -A^{-1}.  The trailing update,
+// n^2 kb flops per step on the upper tiles, is n^3 in all (Gauss-Jordan on the full
+// matrix: 2 n^3).
 int gj_invert_spd(thc_ctx* ctx, double* A, long long n, long long batch) {
   const bool blocked = n > 2 * kGJBlock;
   const long long kb = std::min(n, kGJBlock);
   // scratch: row, col, piv of the one-pivot steps (of n or of kb rows), and the panels
   const long long nrow = blocked ? kb : n;
-  const size_t need = (size_t)batch * (2 * nrow + 1) + (blocked ? (size_t)batch * (3 * n * kb + kb * kb) : 0);
+  auto elems_for = [&](long long bt) {
+    return (size_t)bt * (2 * nrow + 1) + (blocked ? (size_t)bt * (2 * n * kb + kb * kb) : 0);
+  };
   if (!ctx->gw_scr) {  // sized once, for the larger of this batch and the frequency count
-    const long long bmax = std::max<long long>(batch, ctx->gw_nw);
-    const size_t elems = (size_t)bmax * (2 * nrow + 1) + (blocked ? (size_t)bmax * (3 * n * kb + kb * kb) : 0);
+    const size_t elems = elems_for(std::max<long long>(batch, ctx->gw_nw));
     THC_TRY(ctx_alloc(ctx, (void**)&ctx->gw_scr, sizeof(double) * elems, "Gauss-Jordan scratch"));
     ctx->gw_scr_elems = elems;
   }
-  if (need > ctx->gw_scr_elems) return fail(ctx, THC_EINVAL, "Gauss-Jordan scratch too small for this batch");
+  if (elems_for(batch) > ctx->gw_scr_elems) return fail(ctx, THC_EINVAL, "Gauss-Jordan scratch too small for this batch");
   double *row = ctx->gw_scr, *col = row + batch * nrow, *piv = col + batch * nrow;
   if (!blocked) return gj_invert_unblocked(ctx, A, n, batch, row, col, piv);
-  double *C = piv + batch, *R = C + batch * n * kb, *Rp = R + batch * n * kb, *P = Rp + batch * n * kb;
+  double *CT = piv + batch, *Rp = CT + batch * n * kb, *P = Rp + batch * n * kb;
   const long long nn = n * n;
   for (long long k0 = 0; k0 < n; k0 += kGJBlock) {
     const long long b = std::min(kGJBlock, n - k0);
     ProfRec rec;
     THC_TRY(prof_begin(ctx, K_SCREEN, 0.0, &rec));
-    gj_panels_kernel<<<blocks_for(n * b * batch), 256, 0, ctx->stream>>>(n, k0, b, batch, A, C, R, P);
-    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Gauss-Jordan panels"));
+    sym_panels_kernel<<<blocks_for(n * b * batch), 256, 0, ctx->stream>>>(n, k0, b, batch, A, CT, P);
+    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "sweep panels"));
     THC_TRY(gj_invert_unblocked(ctx, P, b, batch, row, col, piv));  // P = A_kk^{-1}
     const dim3 gr((unsigned)((b + f64::BM - 1) / f64::BM), (unsigned)((n + f64::BN - 1) / f64::BN), (unsigned)batch);
-    THC_TRY(prof_begin(ctx, K_SCREEN, 2.0 * b * n * b * batch, &rec));  // R' = P R
+    THC_TRY(prof_begin(ctx, K_SCREEN, 2.0 * b * n * b * batch, &rec));  // Rp = P C^T
     f64::gemm_kernel<true, false><<<gr, f64::NT, 0, ctx->stream>>>(
-        b, n, b, View{P, b * b, b, 1}, View{R, n * b, n, 1}, f64::StoreEpi{Rp, n * b, n, 1, 1.0});
-    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Gauss-Jordan row panel"));
+        b, n, b, View{P, b * b, b, 1}, View{CT, n * b, n, 1}, f64::StoreEpi{Rp, n * b, n, 1, 1.0});
+    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "sweep row panel"));
     const dim3 gt((unsigned)((n + f64::BM - 1) / f64::BM), (unsigned)((n + f64::BN - 1) / f64::BN), (unsigned)batch);
-    THC_TRY(prof_begin(ctx, K_SCREEN, 2.0 * n * n * b * batch, &rec));  // A -= C R'
-    f64::gemm_kernel<true, false><<<gt, f64::NT, 0, ctx->stream>>>(
-        n, n, b, View{C, n * b, b, 1}, View{Rp, n * b, n, 1}, SubEpi{A, nn, n});
-    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Gauss-Jordan trailing update"));
-    const dim3 gc((unsigned)((n + f64::BM - 1) / f64::BM), (unsigned)((b + f64::BN - 1) / f64::BN), (unsigned)batch);
-    THC_TRY(prof_begin(ctx, K_SCREEN, 2.0 * n * b * b * batch, &rec));  // A[:, k] = -C P
-    f64::gemm_kernel<true, false><<<gc, f64::NT, 0, ctx->stream>>>(
-        n, b, b, View{C, n * b, b, 1}, View{P, b * b, b, 1}, f64::StoreEpi{A + k0, nn, n, 1, -1.0});
-    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Gauss-Jordan column panel"));
-    THC_TRY(prof_begin(ctx, K_SCREEN, 0.0, &rec));  // A[k, :] = R', A[k, k] = P
-    gj_rows_kernel<<<blocks_for(b * n * batch), 256, 0, ctx->stream>>>(n, k0, b, batch, Rp, P, A);
-    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "Gauss-Jordan block row"));
+    THC_TRY(prof_begin(ctx, K_SCREEN, 1.0 * n * (n + f64::BN) * b * batch, &rec));  // A -= C Rp (upper tiles)
+    f64::gemm_kernel<false, false><<<gt, f64::NT, 0, ctx->stream>>>(
+        n, n, b, View{CT, n * b, 1, n}, View{Rp, n * b, n, 1}, SymSubEpi{A, nn, n});
+    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "sweep trailing update"));
+    THC_TRY(prof_begin(ctx, K_SCREEN, 0.0, &rec));  // block row and column from Rp, A_kk = -P
+    sym_rows_kernel<<<blocks_for(b * n * batch), 256, 0, ctx->stream>>>(n, k0, b, batch, Rp, P, A);
+    THC_TRY(prof_end(ctx, &rec, cudaGetLastError(), "sweep block row"));
   }
-  return THC_OK;
+  ProfRec rec;
+  THC_TRY(prof_begin(ctx, K_SCREEN, 0.0, &rec));
+  const dim3 gf((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)batch);
+  sym_finish_kernel<<<gf, 256, 0, ctx->stream>>>(n, A);
+  return prof_end(ctx, &rec, cudaGetLastError(), "sweep sign and mirror");
 }
 
 int gw_set_transforms(thc_ctx* ctx, int n_omega, const double* to_iw, const double* to_tau) {
