@@ -282,8 +282,7 @@ long long thc_launch_count(const thc_ctx *ctx);
  *   E_dyn         host out; the result equals thc_energy's bit for bit
  *   stream        cudaStream_t (NULL: legacy default stream); synchronised
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: calls that overlap
+ * (cudaGetSymbolAddress) with that device current.  All calls share the array: calls that overlap
  * on the GPU (other streams or threads) race and must be serialised by the
  * caller.  Failures are described by thc_last_error(NULL).
  */
