@@ -43,6 +43,7 @@ struct thc_dyson {
   double *U_tau = nullptr, *fit_tau = nullptr;          // n_tau x L, L x n_tau
   double *Uiw_re = nullptr, *Uiw_im = nullptr;          // n_iw x L
   double *fit_re = nullptr, *fit_im = nullptr;          // L x n_iw
+  double *fold_re = nullptr, *fold_im = nullptr;        // L x n_iw/2: fit_iw folded onto the positive half
   double *ubeta_d = nullptr, *parity_d = nullptr;       // L
   double *sig_l = nullptr;                              // L x n^2
   double *Siw = nullptr;                                // n_iw x n^2 x 2 (interleaved complex)
@@ -58,7 +59,6 @@ struct thc_dyson {
   double *work2 = nullptr;                              // n_iw x n^2 x 2: S G (commutator, allocated on first use)
   double *trq = nullptr;                                // n_iw x 2: Tr[(G S)^2]
   int evals = 0;                                        // N(mu) evaluations of the last solve
-  double slope = 0.0;                                   // dN/dmu at the last evaluation (0: none)
   std::vector<void*> owned;
   std::string err;
 };
@@ -378,16 +378,20 @@ constexpr int kEnergyBlocks = 296;  // 2 per SM
 
 int blocks_for(long long total) { return (int)std::min<long long>((total + 255) / 256, 152LL * 32); }
 
-// sigma_l = fit_tau Sigma(tau);  Sigma(i w) = U_iw sigma_l  (interleaved complex)
-int sigma_to_iw(thc_dyson* d, const double* Sig_tau) {
-  const long long n2 = (long long)d->n * d->n, L = d->L, nt = d->n_tau, nw = d->n_iw;
+// sigma_l = fit_tau Sigma(tau);  Sigma(i w_m) = U_iw sigma_l (interleaved complex) for m >= m_first
+int sigma_to_iw(thc_dyson* d, const double* Sig_tau, long long m_first = 0) {
+  const long long n2 = (long long)d->n * d->n, L = d->L, nt = d->n_tau, nw = d->n_iw - m_first;
   THC_TRY(gemm<true, false>(d, L, n2, nt, View{d->fit_tau, 0, nt, 1}, View{Sig_tau, 0, n2, 1},
                             AccEpi{d->sig_l, 0, n2, 1, 1.0, false}, "sigma_l"));
-  THC_TRY(gemm<true, false>(d, nw, n2, L, View{d->Uiw_re, 0, L, 1}, View{d->sig_l, 0, n2, 1},
-                            AccEpi{d->Siw, 0, 2 * n2, 2, 1.0, false}, "Sigma(iw) re"));
-  return gemm<true, false>(d, nw, n2, L, View{d->Uiw_im, 0, L, 1}, View{d->sig_l, 0, n2, 1},
-                           AccEpi{d->Siw + 1, 0, 2 * n2, 2, 1.0, false}, "Sigma(iw) im");
+  double* out = d->Siw + 2 * m_first * n2;
+  THC_TRY(gemm<true, false>(d, nw, n2, L, View{d->Uiw_re + m_first * L, 0, L, 1}, View{d->sig_l, 0, n2, 1},
+                            AccEpi{out, 0, 2 * n2, 2, 1.0, false}, "Sigma(iw) re"));
+  return gemm<true, false>(d, nw, n2, L, View{d->Uiw_im + m_first * L, 0, L, 1}, View{d->sig_l, 0, n2, 1},
+                           AccEpi{out + 1, 0, 2 * n2, 2, 1.0, false}, "Sigma(iw) im");
 }
+
+// First frequency the inversions use: the positive half when the frequencies come in pairs.
+long long first_inverted(const thc_dyson* d) { return d->half ? d->n_iw / 2 : 0; }
 
 // Dynamic shared memory of gj_cluster_kernel: two pivot-row buffers and a column, plus the
 // CTA's rows when they are resident.
@@ -464,11 +468,27 @@ int invert(thc_dyson* d, long long m0, long long count) {
   return dcheck(d, e == cudaSuccess ? cudaGetLastError() : e, "Gauss-Jordan");
 }
 
+// Re sum_m c_m t_m over every frequency from the traces t (interleaved complex) of the
+// inverted ones: Tr[gamma S] = -Re sum_m c_m t_m, dN/dmu = Re sum_m c_m q_m; for the
+// mirrored half t_{n_iw - 1 - m} = conj(t_m) (likewise q).
+double freq_sum(const thc_dyson* d, const double* t) {
+  const long long nw = d->n_iw;
+  double acc = 0.0;
+  for (long long m = first_inverted(d); m < nw; ++m) {
+    acc += d->cre[m] * t[2 * m] - d->cim[m] * t[2 * m + 1];
+    if (d->half) {
+      const long long mm = nw - 1 - m;
+      acc += d->cre[mm] * t[2 * m] + d->cim[mm] * t[2 * m + 1];
+    }
+  }
+  return acc;
+}
+
 // G(i w_m) at chemical potential mu for every m (the positive half only when the
-// frequencies come in pairs); returns the electron count per spin and its slope dN/dmu.
-int dyson_at(thc_dyson* d, double mu, double* n_out, double* dn_out) {
+// frequencies come in pairs); returns the electron count per spin.
+int dyson_at(thc_dyson* d, double mu, double* n_out) {
   const long long n = d->n, nn = n * n, nw = d->n_iw;
-  const long long m0 = d->half ? nw / 2 : 0, cnt = nw - m0;
+  const long long m0 = first_inverted(d), cnt = nw - m0;
   const double* iw_d = d->scal + 8 + m0;  // frequencies live after 8 scalar slots
   build_kernel<<<blocks_for(nn * cnt), 256, 0, d->stream>>>((int)n, (int)cnt, iw_d, mu, d->S, d->F,
                                                             d->Siw + 2 * m0 * nn, d->Giw + 2 * m0 * nn);
@@ -477,36 +497,33 @@ int dyson_at(thc_dyson* d, double mu, double* n_out, double* dn_out) {
   trace_gs_kernel<<<(unsigned)cnt, 256, 0, d->stream>>>((int)n, reinterpret_cast<const double2*>(d->Giw) + m0 * nn,
                                                         d->S, d->tr + 2 * m0);
   THC_TRY(dcheck(d, cudaGetLastError(), "Tr[G S]"));
-  // slope: dG/dmu = -G S G, so dt_m/dmu = -Tr[(G_m S)^2] = -q_m; Y_m = G_m S (real and imaginary parts)
+  std::vector<double> t(2 * nw);
+  THC_TRY(dcheck(d, cudaMemcpyAsync(t.data() + 2 * m0, d->tr + 2 * m0, sizeof(double) * 2 * cnt,
+                                    cudaMemcpyDeviceToHost, d->stream),
+                 "copy traces"));
+  THC_TRY(dcheck(d, cudaStreamSynchronize(d->stream), "Dyson sync"));
+  *n_out = -freq_sum(d, t.data());
+  d->evals += 1;
+  return THC_OK;
+}
+
+// dN/dmu at the G(i w) of the last dyson_at: dG/dmu = -G S G, so dt_m/dmu = -Tr[(G_m S)^2] = -q_m,
+// from Y_m = G_m S (real and imaginary parts).
+int dyson_slope(thc_dyson* d, double* dn_out) {
+  const long long n = d->n, nn = n * n, nw = d->n_iw;
+  const long long m0 = first_inverted(d), cnt = nw - m0;
   for (int part = 0; part < 2; ++part)
     THC_TRY(gemm<true, false>(d, n, n, n, View{d->Giw + 2 * m0 * nn + part, 2 * nn, 2 * n, 2}, View{d->S, 0, n, 1},
                               AccEpi{d->work + 2 * m0 * nn + part, 2 * nn, 2 * n, 2, 1.0, false}, "G S", cnt));
   trace_sq_kernel<<<(unsigned)cnt, 256, 0, d->stream>>>((int)n, reinterpret_cast<const double2*>(d->work) + m0 * nn,
                                                         d->trq + 2 * m0);
   THC_TRY(dcheck(d, cudaGetLastError(), "Tr[(G S)^2]"));
-  std::vector<double> t(2 * nw), q(2 * nw);
-  THC_TRY(dcheck(d, cudaMemcpyAsync(t.data() + 2 * m0, d->tr + 2 * m0, sizeof(double) * 2 * cnt,
-                                    cudaMemcpyDeviceToHost, d->stream),
-                 "copy traces"));
+  std::vector<double> q(2 * nw);
   THC_TRY(dcheck(d, cudaMemcpyAsync(q.data() + 2 * m0, d->trq + 2 * m0, sizeof(double) * 2 * cnt,
                                     cudaMemcpyDeviceToHost, d->stream),
                  "copy slope traces"));
-  THC_TRY(dcheck(d, cudaStreamSynchronize(d->stream), "Dyson sync"));
-  // Tr[gamma S] = -Re sum_m c_m t_m and dN/dmu = Re sum_m c_m q_m, with t_{n_iw - 1 - m} = conj(t_m)
-  // (likewise q) for the mirrored half
-  double acc = 0.0, dacc = 0.0;
-  for (long long m = m0; m < nw; ++m) {
-    acc += d->cre[m] * t[2 * m] - d->cim[m] * t[2 * m + 1];
-    dacc += d->cre[m] * q[2 * m] - d->cim[m] * q[2 * m + 1];
-    if (d->half) {
-      const long long mm = nw - 1 - m;
-      acc += d->cre[mm] * t[2 * m] + d->cim[mm] * t[2 * m + 1];
-      dacc += d->cre[mm] * q[2 * m] + d->cim[mm] * q[2 * m + 1];
-    }
-  }
-  *n_out = -acc;
-  if (dn_out) *dn_out = dacc;
-  d->evals += 1;
+  THC_TRY(dcheck(d, cudaStreamSynchronize(d->stream), "Dyson slope sync"));
+  *dn_out = freq_sum(d, q.data());
   return THC_OK;
 }
 
@@ -589,6 +606,21 @@ int thc_dyson_init(thc_dyson** out, int n_ao, int n_tau, int n_iw, int n_l, doub
   d->half = n_iw % 2 == 0;
   for (int m = n_iw / 2; m < n_iw && d->half; ++m)
     if (!(iw[m] > 0.0) || !(std::fabs(iw[m] + iw[n_iw - 1 - m]) <= 1e-12 * iw[m])) d->half = false;
+  if (rc == THC_OK && d->half) {
+    // fit_iw folded onto the positive half: Re[f_m G_m + f_mm conj(G_m)] = (Re f_m + Re f_mm) Re G_m
+    // - (Im f_m - Im f_mm) Im G_m, mm = n_iw - 1 - m
+    const int h = n_iw / 2;
+    std::vector<double> fr(L * h), fi(L * h);
+    for (size_t l = 0; l < L; ++l)
+      for (int j = 0; j < h; ++j) {
+        const size_t m = (size_t)(h + j), mm = (size_t)(n_iw - 1) - m;
+        fr[l * h + j] = fit_iw[2 * (l * n_iw + m)] + fit_iw[2 * (l * n_iw + mm)];
+        fi[l * h + j] = fit_iw[2 * (l * n_iw + m) + 1] - fit_iw[2 * (l * n_iw + mm) + 1];
+      }
+    up(&d->fold_re, fr.data(), fr.size(), "folded fit_iw re");
+    up(&d->fold_im, fi.data(), fi.size(), "folded fit_iw im");
+    if (rc == THC_OK) rc = dcheck(d, cudaStreamSynchronize(d->stream), "folded fit_iw sync");
+  }
   if (rc == THC_OK) rc = choose_gj_cluster(d);
   if (rc != THC_OK) return bail(rc);
   *out = d;
@@ -601,17 +633,19 @@ int thc_dyson_solve(thc_dyson* d, const double* Sigma_tau, double n_elec, double
   const long long n2 = (long long)d->n * d->n, L = d->L, nt = d->n_tau, nw = d->n_iw;
   d->evals = 0;
   if (Sigma_tau) {
-    THC_TRY(sigma_to_iw(d, Sigma_tau));
+    THC_TRY(sigma_to_iw(d, Sigma_tau, first_inverted(d)));
   } else {
     THC_TRY(dcheck(d, cudaMemsetAsync(d->Siw, 0, sizeof(double) * 2 * n2 * nw, d->stream), "zero Sigma"));
   }
   if (!(tol > 0)) tol = 1e-10;
   // N(mu) is increasing.  Newton steps on the analytic slope dN/dmu (from
-  // dG/dmu = -G S G, evaluated with every count), each capped at 0.5 Ha, kept
-  // inside a bracket once one is known and replaced by bisection when they leave
-  // it, when the slope vanishes (mu in a gap) or every fourth step.
+  // dG/dmu = -G S G, evaluated with every count that another step follows), each
+  // capped at 0.5 Ha, kept inside a bracket once one is known and replaced by
+  // bisection when they leave it, when the slope vanishes (mu in a gap) or every
+  // fourth step.
   double m = *mu, nm = 0.0, dm = 0.0;
-  THC_TRY(dyson_at(d, m, &nm, &dm));
+  THC_TRY(dyson_at(d, m, &nm));
+  if (std::fabs(nm - n_elec) > tol) THC_TRY(dyson_slope(d, &dm));
   double lo = -INFINITY, hi = INFINITY;
   auto note = [&](double x, double nx) {
     if (nx < n_elec) {
@@ -635,10 +669,10 @@ int thc_dyson_solve(thc_dyson* d, const double* Sigma_tau, double n_elec, double
     }
     if (bracket && !(x > lo && x < hi)) x = 0.5 * (lo + hi);
     m = x;
-    THC_TRY(dyson_at(d, m, &nm, &dm));
+    THC_TRY(dyson_at(d, m, &nm));
     note(m, nm);
+    if (std::fabs(nm - n_elec) > tol) THC_TRY(dyson_slope(d, &dm));
   }
-  d->slope = dm;
   if (std::fabs(nm - n_elec) > 1e3 * tol)
     return dfail(d, THC_EINVAL, "thc_dyson_solve: chemical potential search did not converge");
   *mu = m;
@@ -647,10 +681,15 @@ int thc_dyson_solve(thc_dyson* d, const double* Sigma_tau, double n_elec, double
                                                                         reinterpret_cast<double2*>(d->Giw));
     THC_TRY(dcheck(d, cudaGetLastError(), "G(-i w)"));
   }
-  // g_l = Re[fit_iw G(iw)] ;  G(tau) = U_tau g
-  THC_TRY(gemm<true, false>(d, L, n2, nw, View{d->fit_re, 0, nw, 1}, View{d->Giw, 0, 2 * n2, 2},
+  // g_l = Re[fit_iw G(iw)] ;  G(tau) = U_tau g.  With the frequencies in pairs the sum runs
+  // over the positive half with the folded coefficients (fit_m + fit_{n_iw-1-m} on Re G_m,
+  // their imaginary parts' difference on Im G_m).
+  const long long m0 = first_inverted(d), kw = nw - m0;
+  const double* fre = d->half ? d->fold_re : d->fit_re;
+  const double* fim = d->half ? d->fold_im : d->fit_im;
+  THC_TRY(gemm<true, false>(d, L, n2, kw, View{fre, 0, kw, 1}, View{d->Giw + 2 * m0 * n2, 0, 2 * n2, 2},
                             AccEpi{d->g_l, 0, n2, 1, 1.0, false}, "g_l re"));
-  THC_TRY(gemm<true, false>(d, L, n2, nw, View{d->fit_im, 0, nw, 1}, View{d->Giw + 1, 0, 2 * n2, 2},
+  THC_TRY(gemm<true, false>(d, L, n2, kw, View{fim, 0, kw, 1}, View{d->Giw + 2 * m0 * n2 + 1, 0, 2 * n2, 2},
                             AccEpi{d->g_l, 0, n2, 1, -1.0, true}, "g_l im"));
   THC_TRY(gemm<true, false>(d, nt, n2, L, View{d->U_tau, 0, L, 1}, View{d->g_l, 0, n2, 1},
                             AccEpi{G_tau, 0, n2, 1, 1.0, false}, "G(tau)"));
@@ -662,14 +701,12 @@ int thc_dyson_count(thc_dyson* d, const double* Sigma_tau, double mu, double* n_
   if (!n_per_spin) return dfail(d, THC_EINVAL, "thc_dyson_count: NULL argument");
   const long long n2 = (long long)d->n * d->n;
   if (Sigma_tau) {
-    THC_TRY(sigma_to_iw(d, Sigma_tau));
+    THC_TRY(sigma_to_iw(d, Sigma_tau, first_inverted(d)));
   } else {
     THC_TRY(dcheck(d, cudaMemsetAsync(d->Siw, 0, sizeof(double) * 2 * n2 * d->n_iw, d->stream), "zero Sigma"));
   }
-  double dn = 0.0;
-  THC_TRY(dyson_at(d, mu, n_per_spin, &dn));
-  if (dn_dmu) *dn_dmu = dn;
-  return THC_OK;
+  THC_TRY(dyson_at(d, mu, n_per_spin));
+  return dn_dmu ? dyson_slope(d, dn_dmu) : THC_OK;
 }
 
 int thc_dyson_commutator(thc_dyson* d, const double* Sigma_out_tau, double* E_iw) {
