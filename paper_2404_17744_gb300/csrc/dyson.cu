@@ -52,8 +52,12 @@ struct thc_dyson {
   double *tr = nullptr;                                 // n_iw x 2 partial traces
   double *part = nullptr;                               // per-block partial sums of the energy contraction
   bool half = false;                                    // frequencies in pairs (w_m = -w_{n_iw-1-m}): invert m >= n_iw/2
-  int gj_cs = 1;                                        // CTAs per cluster of the Gauss-Jordan kernel
-  bool gj_resident = false;                             // its rows kept in shared memory
+  // Gauss-Jordan launch plan for the gj_count matrices of a set: the first gj_first with
+  // clusters of gj_cs[0] CTAs (rows resident in shared memory if gj_res[0]), the rest with
+  // gj_cs[1] / gj_res[1]
+  long long gj_count = 0, gj_first = 0;
+  int gj_cs[2] = {1, 1};
+  bool gj_res[2] = {false, false};
   double *scal = nullptr;                               // small scalar scratch
   double *work = nullptr;                               // n_iw x n^2 x 2: G S (count slope), H G (commutator)
   double *work2 = nullptr;                              // n_iw x n^2 x 2: S G (commutator, allocated on first use)
@@ -401,10 +405,11 @@ size_t gj_smem(int n, int cs, bool resident) {
 }
 constexpr size_t kGjSmemMax = 232448;  // 227 KB per CTA
 
-// Cluster size of the Gauss-Jordan kernel and whether a CTA's rows stay in shared
-// memory: the fewest steps' worth of work on the busiest CTA, i.e. rows per CTA times
-// waves of resident clusters, with rows kept in global memory (L2) counted twice
-// (ties: smaller clusters).
+// Launch plan of the Gauss-Jordan kernel.  A set's time is the sum over its launches of
+// the rows per CTA times the waves of resident clusters (rows kept in global memory, L2,
+// counted twice).  Candidates: one cluster size for every matrix, or whole waves of one
+// size followed by the remaining matrices with another (a last partial wave of small
+// clusters leaves most SMs idle; larger clusters spread those matrices over them).
 int choose_gj_cluster(thc_dyson* d) {
   THC_TRY(thc::per_device(reinterpret_cast<const void*>(gj_cluster_kernel), nullptr, [&](int, int*) {
     return dcheck(d, cudaFuncSetAttribute(gj_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -412,9 +417,12 @@ int choose_gj_cluster(thc_dyson* d) {
                   "Gauss-Jordan shared memory");
   }));
   const long long count = d->half ? d->n_iw / 2 : d->n_iw;
-  int best_cs = 1;
-  bool best_res = false;
-  long long best = -1;
+  struct Opt {
+    int cs;
+    bool res;
+    long long q, rows;  // resident clusters, cost of one wave
+  };
+  std::vector<Opt> opts;
   for (int cs = 1; cs <= 8 && cs <= d->n; ++cs) {
     for (int res = 0; res < 2; ++res) {
       const size_t smem = gj_smem(d->n, cs, res != 0);
@@ -435,37 +443,65 @@ int choose_gj_cluster(thc_dyson* d) {
         cudaGetLastError();
         continue;
       }
-      const long long cost = ((count + q - 1) / q) * ((d->n + cs - 1) / cs) * (res ? 1 : 2);
-      if (best < 0 || cost < best) {
+      opts.push_back(Opt{cs, res != 0, q, (long long)((d->n + cs - 1) / cs) * (res ? 1 : 2)});
+    }
+  }
+  if (opts.empty()) return dfail(d, THC_EINVAL, "no cluster shape of the Gauss-Jordan kernel fits this device");
+  auto waves = [](long long m, long long q) { return (m + q - 1) / q; };
+  long long best = -1;
+  for (const Opt& a : opts) {
+    const long long single = waves(count, a.q) * a.rows;
+    if (best < 0 || single < best) {  // ties: the earlier (smaller) cluster
+      best = single;
+      d->gj_first = count;
+      d->gj_cs[0] = d->gj_cs[1] = a.cs;
+      d->gj_res[0] = d->gj_res[1] = a.res;
+    }
+    const long long first = (count / a.q) * a.q, rest = count - first;
+    if (first == 0 || rest == 0) continue;
+    for (const Opt& b : opts) {
+      const long long cost = (first / a.q) * a.rows + waves(rest, b.q) * b.rows;
+      if (cost < best) {
         best = cost;
-        best_cs = cs;
-        best_res = res != 0;
+        d->gj_first = first;
+        d->gj_cs[0] = a.cs;
+        d->gj_res[0] = a.res;
+        d->gj_cs[1] = b.cs;
+        d->gj_res[1] = b.res;
       }
     }
   }
-  d->gj_cs = best_cs;
-  d->gj_resident = best_res;
+  d->gj_count = count;
   return THC_OK;
 }
 
-// Gauss-Jordan inversion of matrices m0 .. m0 + count - 1 of d->Giw, one cluster of d->gj_cs CTAs each.
-int invert(thc_dyson* d, long long m0, long long count) {
+// Gauss-Jordan inversion of count matrices of d->Giw from m0 on, clusters of cs CTAs each.
+int invert_launch(thc_dyson* d, long long m0, long long count, int cs, bool res) {
   if (count <= 0) return THC_OK;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)d->gj_cs;
+  attr[0].val.clusterDim.x = (unsigned)cs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3((unsigned)(count * d->gj_cs), 1, 1);
+  cfg.gridDim = dim3((unsigned)(count * cs), 1, 1);
   cfg.blockDim = dim3(1024, 1, 1);
-  cfg.dynamicSmemBytes = gj_smem(d->n, d->gj_cs, d->gj_resident);
+  cfg.dynamicSmemBytes = gj_smem(d->n, cs, res);
   cfg.stream = d->stream;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, gj_cluster_kernel, d->n, (int)m0, d->gj_resident ? 1 : 0,
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, gj_cluster_kernel, d->n, (int)m0, res ? 1 : 0,
                                            reinterpret_cast<double2*>(d->Giw));
   return dcheck(d, e == cudaSuccess ? cudaGetLastError() : e, "Gauss-Jordan");
+}
+
+// The matrices m0 .. m0 + count - 1 by the launch plan (one launch when count is not the
+// planned set).
+int invert(thc_dyson* d, long long m0, long long count) {
+  if (count != d->gj_count) return invert_launch(d, m0, count, d->gj_cs[0], d->gj_res[0]);
+  const long long first = std::min(count, d->gj_first);
+  THC_TRY(invert_launch(d, m0, first, d->gj_cs[0], d->gj_res[0]));
+  return invert_launch(d, m0 + first, count - first, d->gj_cs[1], d->gj_res[1]);
 }
 
 // Re sum_m c_m t_m over every frequency from the traces t (interleaved complex) of the
