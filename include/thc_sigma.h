@@ -234,8 +234,11 @@ int thc_set_stream(thc_ctx *ctx, void *stream);
  * and of the one-off U build, 2 N^2 n^2 (returned through u_flops if non-NULL).
  * The SOX intermediate D_PR is symmetric, so B, C and D are counted over the
  * N (N + 1) / 2 pairs P <= R that the library forms (the paper's scheme over all
- * (P, R) pairs would be 2 N^2 n^2 + N^2 n more per tau point).  The profiler below
- * reports what the kernels carry out, whole tiles included.
+ * (P, R) pairs would be 2 N^2 n^2 + N^2 n more per tau point).  With THC_GW the
+ * count adds, per tau point, the projections (2 N n^2 + 4 N^2 n) and, per evaluation,
+ * the two bosonic transforms (4 n_omega N^2 n_tau) and the n_omega inversions (N^3
+ * each by the symmetric sweep above N = 128, 2 N^3 by Gauss-Jordan below).  The
+ * profiler below reports what the kernels carry out, whole tiles included.
  */
 double thc_sigma_flops(const thc_ctx *ctx, double *u_flops);
 

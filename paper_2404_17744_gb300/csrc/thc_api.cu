@@ -373,9 +373,10 @@ double thc_sigma_flops(const thc_ctx* ctx, double* u_flops) {
   if (ctx->terms & THC_SOX) f += 2.0 * N * n * n * n + 2.0 * N * (N + 1) * n * n + N * (N + 1) * n;
   if (ctx->terms & THC_DIRECT) f += 2.0 * N * n * n + 4.0 * N * N * n + 4.0 * N * N * N;
   if (ctx->terms & THC_GW) {  // projections per tau; per evaluation the transforms and the inversions
-    const double nw = ctx->gw_nw;
+    // (the symmetric sweep above 128 rows: N^3 each; Gauss-Jordan on the whole matrix below: 2 N^3)
+    const double nw = ctx->gw_nw, inv = (ctx->N > 128 ? 1.0 : 2.0) * N * N * N;
     f += 2.0 * N * n * n + 4.0 * N * N * n;
-    if (nt > 0) f += (4.0 * nw * N * N * nt + 2.0 * nw * N * N * N) / nt;
+    if (nt > 0) f += (4.0 * nw * N * N * nt + nw * inv) / nt;
   }
   if (u_flops) *u_flops = (ctx->terms & THC_SOX) ? 2.0 * N * N * n * n : 0.0;
   return nt * f;
