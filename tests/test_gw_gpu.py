@@ -3,7 +3,7 @@ sigma_gw_thc (pinned by its weak-coupling limit, the one-orbital closed form and
 symmetry in tests/test_oracle_pins.py).  Bars: FP64 path 1e-10 Ha in Sigma; THC_BF16X3
 (split projections and back-transform, FP64 screening) 1e-6 Ha.  THC ranks above 128
 exercise the blocked symmetric-sweep inverse of the screening (blocks of 64 pivots on
-the upper triangle: 192 whole blocks, 300 a ragged last one)."""
+the upper triangle: 192 whole blocks, 300 and 600 a ragged last one)."""
 import functools
 
 import numpy as np
@@ -53,7 +53,7 @@ def _refs(n, N, seed):
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-6)])
-@pytest.mark.parametrize("n,N,seed", [(8, 30, 3), (21, 67, 4), (40, 150, 5), (24, 192, 7), (36, 300, 6)])
+@pytest.mark.parametrize("n,N,seed", [(8, 30, 3), (21, 67, 4), (40, 150, 5), (24, 192, 7), (36, 300, 6), (40, 600, 9)])
 def test_gw_and_gwsox_match_oracle(n, N, seed, precision, tol):
     from paper_2404_17744_gb300 import thc
     g, bt = _grid(50.0, 10.0)

@@ -97,6 +97,37 @@ def test_dyson_inversions_with_and_without_mirrored_frequencies(mirrored):
         thc.thc_dyson_destroy(d)
 
 
+def test_dyson_step_at_200_orbitals_matches_oracle():
+    """A 200-orbital Dyson step on the Lambda = 1e5 grid (96 Matsubara points in pairs: 48
+    inverted, more than one wave of resident clusters, so the set runs as whole waves of
+    one cluster size and the rest with another) with the oracle's second-order Sigma of
+    the noninteracting G, at the oracle's mu; and the search from mu = 0 to its count."""
+    from paper_2404_17744_gb300 import thc
+    case = synth.make_sigma_case(200, 40, 4, 100.0, 47, identity_S=False, n_occ=40)
+    g = grid_for(100.0, 1000.0)
+    nt = len(g.tau)
+    G0, mu0 = so.solve_dyson(g, case.S, case.F, None, 40.0, 0.0)
+    U = o.thc_U(case.X, case.V)
+    Sig = np.stack([o.sigma_sox_thc(case.X, U, G0[k], -G0[nt - 1 - k]) +
+                    o.sigma_direct_thc(case.X, case.V, G0[k], -G0[nt - 1 - k]) for k in range(nt)])
+    G_ref, mu_ref = so.solve_dyson(g, case.S, case.F, Sig, 40.0, mu0)
+    d = _dyson(case, g)
+    try:
+        dev = torch.device("cuda:0")
+        Gd = torch.empty((nt, case.n, case.n), dtype=torch.float64, device=dev)
+        Sd = torch.from_numpy(Sig).to(dev)
+        assert thc.thc_dyson_solve(d, Sd, 40.0, mu_ref, 10.0, Gd) == mu_ref
+        err = np.abs(Gd.cpu().numpy() - G_ref).max()
+        mu = thc.thc_dyson_solve(d, Sd, 40.0, 0.0, 1e-11, Gd)
+        _, _, n = thc.thc_dyson_energy(d, Gd, Sd)
+        print(f"200 orbitals, {len(g.iw)} frequencies: max|dG| = {err:.1e}; searched mu {mu:.10f} "
+              f"(oracle {mu_ref:.10f}), count {n:.12f}")
+        assert err < 1e-10
+        assert abs(n - 40.0) < 1e-9 and abs(mu - mu_ref) < 1e-4
+    finally:
+        thc.thc_dyson_destroy(d)
+
+
 def test_vector_utilities():
     from paper_2404_17744_gb300 import thc
     dev = torch.device("cuda:0")
