@@ -15,7 +15,10 @@ E_dyn (every measured margin is printed).
   points against the oracle's energy and samples; FP64 at the three stored tau points;
 * thc1100 (1100 AOs, 5500 THC points): one tau point next to 0, THC_BF16X3 against
   the FP64 GPU path (a secondary check: the oracle needs 53 GB for U_Pqs and hours per
-  tau point there, so it has no stored values at this size).
+  tau point there, so it has no stored values at this size); and the screened term
+  alone (THC_GW) on the loop's IR grid (beta = 1000, Lambda = 1e5: 95 tau points, 48
+  bosonic frequencies, 48 inversions of 5500 x 5500), THC_BF16X3 against FP64 on every
+  tau point (the same secondary reference).
 """
 import json
 import os
@@ -134,3 +137,39 @@ def test_thc1100_split_against_fp64_one_tau():
           f"|dE| {abs(Esp - E64):.2e}")
     assert np.abs(S64 - np.swapaxes(S64, 1, 2)).max() <= 1e-10
     assert err <= 1e-6
+
+
+def test_thc1100_screened_term_split_against_fp64():
+    """c5 sizes, the screened direct term alone on the loop's IR grid: THC_BF16X3 (split
+    projections and back-transform, FP64 screening) against the FP64 GPU path at every
+    tau point, 1e-6 Ha; the FP64 result symmetric at 1e-10."""
+    from paper_2404_17744_gb300 import thc
+    from workloads import ir
+    case = synth.make_workload("thc1100", n_tau=2)
+    g = ir.make_loop_grid(1000.0, 100.0)
+    bt = ir.make_bosonic_transforms(g)
+    G = synth.noninteracting_G(case.F, case.S, 0.0, 1000.0, g.tau)
+    dev = torch.device("cuda:0")
+    X = torch.from_numpy(case.X).to(dev)
+    V = torch.from_numpy(case.V).to(dev)
+    Gd = torch.from_numpy(np.ascontiguousarray(G)).to(dev)
+    out = []
+    for precision in (0, 1):
+        ctx = thc.thc_sigma_init(case.n, case.N, len(g.tau), 1000.0, X, V, np.ascontiguousarray(g.tau), precision,
+                                 thc.THC_GW)
+        try:
+            thc.thc_sigma_set_bosonic(ctx, bt.to_iw, bt.to_tau)
+            S = torch.empty_like(Gd)
+            thc.thc_sigma_eval(ctx, Gd, None, S)
+            thc.thc_sync(ctx)
+            out.append(S.cpu().numpy())
+            del S
+        finally:
+            thc.thc_destroy(ctx)
+            torch.cuda.empty_cache()
+    d = np.abs(out[1] - out[0])
+    print(f"thc1100 screened term, {len(g.tau)} tau / {len(bt.m)} bosonic points: max|Sigma^GW| "
+          f"{np.abs(out[0]).max():.3e}, max|dSigma| 3xBF16 vs FP64 {d.max():.2e}")
+    assert np.abs(out[0] - np.swapaxes(out[0], 1, 2)).max() <= 1e-10
+    assert np.abs(out[0]).max() > 1e-3
+    assert d.max() <= 1e-6
