@@ -255,6 +255,32 @@ def sigma_uhf_thc(X: np.ndarray, V: np.ndarray, U: np.ndarray, G_a: np.ndarray, 
     return out[0], out[1]
 
 
+def sigma_gw_uhf_thc(X: np.ndarray, V: np.ndarray, G_tau_a: np.ndarray, G_bmt_a: np.ndarray,
+                     G_tau_b: np.ndarray, G_bmt_b: np.ndarray, to_iw: np.ndarray,
+                     to_tau: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Screened direct term of an unrestricted G at every tau point (the THC-GW scheme
+    of Sec. II.C written for the two spin blocks of the spin-orbital G of Sec. II.A).
+
+    The RPA bubble runs over both spins, each closed loop carrying its own spin:
+      Pi~(tau) = G^X_a(tau) o G^X_a(-tau)^T + G^X_b(tau) o G^X_b(-tau)^T,
+    one screened interaction W(i Omega) = V [1 - Pi~(i Omega) V]^{-1} serves both
+    spins, and the outer line carries spin s:
+      Sigma^GW_s(tau) = -X (G^X_s(tau) o W~(tau)) X^T,   W~ = W - V.
+    For G_a = G_b this is ``sigma_gw_thc`` for both spins; its first order in the
+    bubble is the direct term of ``sigma_uhf_thc``."""
+    nt = G_tau_a.shape[0]
+    N = V.shape[0]
+    GX = [np.stack([X.T @ G[k] @ X for k in range(nt)]) for G in (G_tau_a, G_tau_b)]
+    GXm = [np.stack([X.T @ g_minus_tau(Gb[k]) @ X for k in range(nt)]) for Gb in (G_bmt_a, G_bmt_b)]
+    Pi = GX[0] * np.swapaxes(GXm[0], 1, 2) + GX[1] * np.swapaxes(GXm[1], 1, 2)
+    Pi_iw = np.einsum("mk,kab->mab", to_iw, Pi)
+    I = np.eye(N)
+    Wt_iw = np.stack([V @ np.linalg.inv(I - P @ V) - V for P in Pi_iw])
+    Wt = np.einsum("km,mab->kab", to_tau, Wt_iw)
+    a, b = (np.stack([-(X @ (g[k] * Wt[k]) @ X.T) for k in range(nt)]) for g in GX)
+    return a, b
+
+
 def energy_dyn_tau_uhf(G_bmt_a, G_bmt_b, S_a, S_b, weights) -> float:
     """Galitskii-Migdal dynamical energy (Eq. E2b) of an unrestricted G: one half of
     the sum over both spins of -int Tr[G_s(beta - tau) Sigma_s(tau)] dtau (equal to

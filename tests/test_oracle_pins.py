@@ -403,3 +403,70 @@ def test_gw_symmetric():
     G = synth.noninteracting_G(case.F, case.S, 0.0, 50.0, g.tau)
     S = o.sigma_gw_thc(case.X, case.V, G, G[::-1], bt.to_iw, bt.to_tau)
     assert np.abs(S - np.swapaxes(S, 1, 2)).max() <= 1e-13 * np.abs(S).max()
+
+
+def _uhf_pair(case, g):
+    """Two different spin blocks: G_a of F, G_b of F shifted by a symmetric perturbation."""
+    rng = np.random.default_rng(77)
+    Fb = case.F + 0.2 * synth.random_symmetric(1, case.n, rng)[0]
+    Ga = synth.noninteracting_G(case.F, case.S, 0.0, g.basis.beta, g.tau)
+    Gb = synth.noninteracting_G(Fb, case.S, 0.0, g.basis.beta, g.tau)
+    return Ga, Gb
+
+
+def test_gw_uhf_equal_spins_is_the_restricted_term():
+    g, bt = _bosonic(50.0)
+    case = synth.make_sigma_case(7, 20, 4, 50.0, 13, identity_S=False, n_occ=3)
+    G = synth.noninteracting_G(case.F, case.S, 0.0, 50.0, g.tau)
+    Sa, Sb = o.sigma_gw_uhf_thc(case.X, case.V, G, G[::-1], G, G[::-1], bt.to_iw, bt.to_tau)
+    R = o.sigma_gw_thc(case.X, case.V, G, G[::-1], bt.to_iw, bt.to_tau)
+    scale = np.abs(R).max()
+    assert np.abs(Sa - R).max() <= 1e-13 * scale and np.abs(Sb - R).max() <= 1e-13 * scale
+
+
+def test_gw_uhf_weak_coupling_is_the_unrestricted_bubble():
+    """Sigma^GW_s(lambda V) / lambda^2 tends to the direct term of sigma_uhf_thc (pinned to
+    the spin-orbital definition) with a remainder linear in lambda; the spins differ."""
+    g, bt = _bosonic(50.0)
+    case = synth.make_sigma_case(6, 14, 4, 50.0, 31, identity_S=False, n_occ=3)
+    Ga, Gb = _uhf_pair(case, g)
+    nt = len(g.tau)
+    U = o.thc_U(case.X, case.V)
+    ref = [np.empty_like(Ga), np.empty_like(Gb)]
+    for k in range(nt):
+        Gma, Gmb = o.g_minus_tau(Ga[nt - 1 - k]), o.g_minus_tau(Gb[nt - 1 - k])
+        ta, tb = o.sigma_uhf_thc(case.X, case.V, U, Ga[k], Gb[k], Gma, Gmb)
+        ref[0][k] = ta - o.sigma_sox_thc(case.X, U, Ga[k], Gma)
+        ref[1][k] = tb - o.sigma_sox_thc(case.X, U, Gb[k], Gmb)
+    assert np.abs(ref[0] - ref[1]).max() > 1e-3 * np.abs(ref[0]).max()   # the spins really differ
+    for s in range(2):
+        d = []
+        for lam in (1e-2, 5e-3):
+            S = o.sigma_gw_uhf_thc(case.X, lam * case.V, Ga, Ga[::-1], Gb, Gb[::-1], bt.to_iw, bt.to_tau)[s]
+            d.append(np.abs(S / lam ** 2 - ref[s]).max() / np.abs(ref[s]).max())
+        assert d[0] < 5e-2 and 1.6 < d[0] / d[1] < 2.4, (s, d)
+
+
+def test_gw_uhf_one_orbital_closed_form():
+    """One orbital, one THC point, levels e_a != e_b: each spin's bubble G_s(tau) G_s(-tau)
+    = -n_s (1 - n_s) is constant in tau, so only Omega = 0 screens, by the sum over both
+    spins: Sigma^GW_s(tau) = -v^2 c (1 - n_s) e^{-e_s tau} / (1 + v beta c) with
+    c = n_a (1 - n_a) + n_b (1 - n_b) and v = V X^4."""
+    beta = 50.0
+    g, bt = _bosonic(beta)
+    x, V, ea, eb = 0.9, 0.7, 0.03, -0.02
+    X = np.array([[x]])
+    Vm = np.array([[V]])
+
+    def G_of(e):
+        nv = o.fermi_pair(np.array([e]), beta)[1][0]
+        return np.array([[[-nv * np.exp(-e * t)]] for t in g.tau])
+    Ga, Gb = G_of(ea), G_of(eb)
+    Sa, Sb = o.sigma_gw_uhf_thc(X, Vm, Ga, Ga[::-1].copy(), Gb, Gb[::-1].copy(), bt.to_iw, bt.to_tau)
+    na, nva = (v[0] for v in o.fermi_pair(np.array([ea]), beta))
+    nb, nvb = (v[0] for v in o.fermi_pair(np.array([eb]), beta))
+    c = na * nva + nb * nvb
+    v = V * x ** 4
+    for S, nv, e in ((Sa, nva, ea), (Sb, nvb, eb)):
+        expect = -v * v * c * nv * np.exp(-e * g.tau) / (1.0 + v * beta * c)
+        assert np.abs(S[:, 0, 0] - expect).max() <= 1e-9 * np.abs(expect).max()
