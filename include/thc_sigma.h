@@ -67,7 +67,8 @@ extern "C" {
 #define THC_DIRECT   1    /* second-order direct (bubble) term */
 #define THC_SOX      2    /* second-order screened exchange */
 #define THC_GW       4    /* screened direct term of scGW / scGWSOX (RPA W) in place of
-                             THC_DIRECT; restricted; needs thc_sigma_set_bosonic */
+                             THC_DIRECT (restricted, or unrestricted through
+                             thc_sigma_eval_uhf); needs thc_sigma_set_bosonic */
 
 typedef struct thc_ctx thc_ctx;   /* opaque, library-owned */
 
@@ -145,6 +146,9 @@ int thc_sigma_set_bosonic(thc_ctx *ctx, int n_omega, const double *to_iw, const 
  *   Sigma^dir_s = -X (G^X_s(tau) o (V Pi V)) X^T with Pi summed over both spins,
  *                 Pi = sum_s' G^X_s'(tau) o G^X_s'(-tau)^T
  * (for G_a = G_b this is the restricted result of thc_sigma_eval for both spins).
+ * With THC_GW the bubble is screened: Pi~ = sum_s' G^X_s'(tau) o G^X_s'(-tau)^T, one
+ * W = V [1 - Pi~ V]^{-1} for both spins, Sigma^GW_s = -X (G^X_s o (W - V)) X^T; the
+ * first unrestricted call allocates one more n_tau x N x N FP64 array (G^X of spin b).
  * The Galitskii-Migdal energy is one half of the sum over both spins of the
  * per-spin expression: E_dyn = (thc_energy(a) + thc_energy(b)) / 2.
  *   G_tau_a, G_tau_b    dev, n_tau x n x n, G of spin a and b

@@ -1,11 +1,15 @@
 // Screened direct term (scGW, scGWSOX; Sec. II.C, first paragraph: the THC-GW
-// scheme) on the FP64 path.  Restricted, per spin:
+// scheme), its screening in FP64 on both paths.  Restricted, per spin:
 //
 //   Pi~(tau)   = 2 G^X(tau) o G^X(-tau)^T                   (spin-summed bubble)
 //   Pi~(i W_m) = sum_k to_iw[m][k] Pi~(tau_k)                (bosonic transform)
 //   W(i W_m)   = V [1 - Pi~ V]^{-1} = (V^{-1} - Pi~)^{-1}    (SPD: V SPD, Pi~ <= 0)
 //   W~(tau_k)  = sum_m to_tau[k][m] (W - V)(i W_m)
 //   Sigma^GW   = -X (G^X(tau) o W~(tau)) X^T
+//
+// Unrestricted (Sec. II.A's spin-orbitals, G block-diagonal in spin): Pi~ is the sum of
+// G^X_s(tau) o G^X_s(-tau)^T over both spins, one W serves both, and Sigma^GW_s takes
+// G^X_s on its outer line.
 //
 // W is formed as the inverse of the symmetric positive definite V^{-1} - Pi~, an
 // elimination without pivoting (stable for SPD matrices), batched over the sampled
@@ -129,26 +133,17 @@ __global__ void sym_finish_kernel(long long n, double* __restrict__ A) {
   }
 }
 
-// Pi~[k0 + b] = 2 GXp[b] o GXm[b]^T and GX[k0 + b] = GXp[b] for the tau points of a chunk.
-__global__ void gw_bubble_kernel(long long N, long long batch, const double* __restrict__ GXp,
-                                 const double* __restrict__ GXm, double* __restrict__ Pi, double* __restrict__ GX) {
+// Pi~[k0 + b] (+)= scale GXp[b] o GXm[b]^T and GX[k0 + b] = GXp[b] for the tau points of a
+// chunk (scale 2: both spins of a restricted G; 1 and accumulate: one spin after the other).
+template <class T>
+__global__ void gw_bubble_kernel(long long N, long long batch, const T* __restrict__ GXp, const T* __restrict__ GXm,
+                                 double scale, int accumulate, double* __restrict__ Pi, double* __restrict__ GX) {
   const long long NN = N * N, total = NN * batch;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long b = idx / NN, r = idx - b * NN, i = r / N, j = r - i * N;
-    Pi[idx] = 2.0 * GXp[idx] * GXm[b * NN + j * N + i];
-    GX[idx] = GXp[idx];
-  }
-}
-
-// The same from the FP32 projections of the split path.
-__global__ void gw_bubble_f32_kernel(long long N, long long batch, const float* __restrict__ GXp,
-                                     const float* __restrict__ GXm, double* __restrict__ Pi, double* __restrict__ GX) {
-  const long long NN = N * N, total = NN * batch;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long b = idx / NN, r = idx - b * NN, i = r / N, j = r - i * N;
-    Pi[idx] = 2.0 * (double)GXp[idx] * (double)GXm[b * NN + j * N + i];
+    const double p = scale * (double)GXp[idx] * (double)GXm[b * NN + j * N + i];
+    Pi[idx] = accumulate ? Pi[idx] + p : p;
     GX[idx] = (double)GXp[idx];
   }
 }
@@ -290,23 +285,32 @@ int gw_set_transforms(thc_ctx* ctx, int n_omega, const double* to_iw, const doub
   return check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "bosonic transforms sync");
 }
 
-// Pi~ and G^X of the tau points c0 .. c0 + tc - 1, from the chunk's G^X(+-tau) buffers.
-int gw_store_bubble(thc_ctx* ctx, long long c0, long long tc) {
-  const long long N = ctx->N, NN = N * N;
-  ProfRec rec;
-  THC_TRY(prof_begin(ctx, K_POLARISATION, 0.0, &rec));
-  gw_bubble_kernel<<<blocks_for(NN * tc), 256, 0, ctx->stream>>>(N, tc, ctx->GXp, ctx->GXm, ctx->gw_pi + c0 * NN,
-                                                                 ctx->gw_gx + c0 * NN);
-  return prof_end(ctx, &rec, cudaGetLastError(), "GW bubble");
+// G^X of spin s for every tau point: gw_gx (restricted, or spin a) or gw_gx_b (spin b,
+// allocated on the first unrestricted evaluation).
+int gw_gx_of(thc_ctx* ctx, int spin, double** gx) {
+  if (spin == 1 && !ctx->gw_gx_b)
+    THC_TRY(ctx_alloc(ctx, (void**)&ctx->gw_gx_b, sizeof(double) * ctx->n_tau * ctx->N * ctx->N, "G^X(tau) of spin b"));
+  *gx = spin == 1 ? ctx->gw_gx_b : ctx->gw_gx;
+  return THC_OK;
 }
 
-// The same from the split path's FP32 G^X(+-tau) buffers.
-int gw_store_bubble_f32(thc_ctx* ctx, long long c0, long long tc) {
+// Pi~ and G^X of the tau points c0 .. c0 + tc - 1, from the chunk's G^X(+-tau) buffers
+// (FP64 path; the split path's are FP32).  nspin 1: Pi~ = 2 G^X o G^X(-)^T; nspin 2: the
+// spin's own G^X o G^X(-)^T, spin b first, spin a added.
+int gw_store_bubble(thc_ctx* ctx, long long c0, long long tc, int nspin, int spin) {
   const long long N = ctx->N, NN = N * N;
+  double* gx = nullptr;
+  THC_TRY(gw_gx_of(ctx, spin, &gx));
+  const double scale = nspin == 1 ? 2.0 : 1.0;
+  const int acc = nspin == 2 && spin == 0;
   ProfRec rec;
   THC_TRY(prof_begin(ctx, K_POLARISATION, 0.0, &rec));
-  gw_bubble_f32_kernel<<<blocks_for(NN * tc), 256, 0, ctx->stream>>>(N, tc, ctx->GXf, ctx->GXmf, ctx->gw_pi + c0 * NN,
-                                                                     ctx->gw_gx + c0 * NN);
+  if (ctx->precision == THC_FP64)
+    gw_bubble_kernel<double><<<blocks_for(NN * tc), 256, 0, ctx->stream>>>(N, tc, ctx->GXp, ctx->GXm, scale, acc,
+                                                                         ctx->gw_pi + c0 * NN, gx + c0 * NN);
+  else
+    gw_bubble_kernel<float><<<blocks_for(NN * tc), 256, 0, ctx->stream>>>(N, tc, ctx->GXf, ctx->GXmf, scale, acc,
+                                                                        ctx->gw_pi + c0 * NN, gx + c0 * NN);
   return prof_end(ctx, &rec, cudaGetLastError(), "GW bubble");
 }
 
@@ -339,13 +343,14 @@ int gw_screen(thc_ctx* ctx) {
   return prof_end(ctx, &rec, cudaGetLastError(), "W~(tau)");
 }
 
-// M = C_SOX D^T - G^X o W~ for the tau points of a chunk (into M).
-int gw_merge(thc_ctx* ctx, long long c0, long long tc, const double* D, double* M) {
+// M = C_SOX D^T - G^X_s o W~ for the tau points of a chunk (into M), G^X of spin s.
+int gw_merge(thc_ctx* ctx, long long c0, long long tc, const double* D, double* M, int spin) {
   const long long N = ctx->N, NN = N * N;
+  double* gx = nullptr;
+  THC_TRY(gw_gx_of(ctx, spin, &gx));
   ProfRec rec;
   THC_TRY(prof_begin(ctx, K_DIRECT_W, 0.0, &rec));
-  gw_merge_kernel<<<blocks_for(NN * tc), 256, 0, ctx->stream>>>(N, tc, D, ctx->gw_gx + c0 * NN, ctx->gw_pi + c0 * NN,
-                                                                M);
+  gw_merge_kernel<<<blocks_for(NN * tc), 256, 0, ctx->stream>>>(N, tc, D, gx + c0 * NN, ctx->gw_pi + c0 * NN, M);
   return prof_end(ctx, &rec, cudaGetLastError(), "GW merge");
 }
 

@@ -305,28 +305,34 @@ int fp64_merge_back(thc_ctx* ctx, long long tc, bool sox, bool dir, double cd, d
   return fp64_back(ctx, tc, dir, Sigma_chunk);
 }
 
-// Screened direct term (THC_GW) with or without SOX, restricted: the bubble of every tau
-// point first (the bosonic transform couples them), then W~(tau), then per chunk SOX,
-// the merge M = C_SOX D^T - G^X o W~ and the back-transform.
-int fp64_eval_gw(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
+// Screened direct term (THC_GW) with or without SOX, restricted (nspin 1) or unrestricted
+// (nspin 2): the bubble of every tau point first (the bosonic transform couples them;
+// unrestricted, spin b and then spin a added), then W~(tau), then per chunk and spin SOX,
+// the merge M = C_SOX D^T - G^X_s o W~ and the back-transform.
+int fp64_eval_gw(thc_ctx* ctx, int nspin, const double* const* G_tau, const double* const* G_bmt,
+                 double* const* Sigma) {
   const long long n = ctx->n, nt = ctx->n_tau, nn = n * n;
   const bool sox = ctx->terms & THC_SOX;
   if (!ctx->gw_nw) return fail(ctx, THC_EINVAL, "THC_GW needs the bosonic transforms (thc_sigma_set_bosonic)");
   for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
     const long long tc = std::min<long long>(ctx->tc, nt - c0);
-    THC_TRY(fp64_project(ctx, spin_views(ctx, G_tau, G_bmt, c0), tc, true, true));
-    THC_TRY(gw_store_bubble(ctx, c0, tc));
+    for (int s = nspin - 1; s >= 0; --s) {
+      THC_TRY(fp64_project(ctx, spin_views(ctx, G_tau[s], G_bmt[s], c0), tc, true, true));
+      THC_TRY(gw_store_bubble(ctx, c0, tc, nspin, s));
+    }
   }
   THC_TRY(gw_screen(ctx));
   for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
     const long long tc = std::min<long long>(ctx->tc, nt - c0);
-    const SpinIn in = spin_views(ctx, G_tau, G_bmt, c0);
-    if (sox) {
-      THC_TRY(fp64_project(ctx, in, tc, false, false));  // Y for the SOX scheme
-      THC_TRY(fp64_sox(ctx, in, tc));
+    for (int s = 0; s < nspin; ++s) {
+      const SpinIn in = spin_views(ctx, G_tau[s], G_bmt[s], c0);
+      if (sox) {
+        THC_TRY(fp64_project(ctx, in, tc, false, false));  // Y for the SOX scheme
+        THC_TRY(fp64_sox(ctx, in, tc));
+      }
+      THC_TRY(gw_merge(ctx, c0, tc, sox ? ctx->D : nullptr, ctx->Pi, s));
+      THC_TRY(fp64_back(ctx, tc, true, Sigma[s] + c0 * nn));
     }
-    THC_TRY(gw_merge(ctx, c0, tc, sox ? ctx->D : nullptr, ctx->Pi));
-    THC_TRY(fp64_back(ctx, tc, true, Sigma + c0 * nn));
   }
   return THC_OK;
 }
@@ -335,11 +341,12 @@ int fp64_eval_gw(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double*
 
 // Restricted (nspin = 1: one per-spin G, direct factor C_DIRECT) or unrestricted
 // (nspin = 2: G of spin a and b, polarisation summed over both spins, direct factor -1
-// per spin, SOX within each spin).  Order per chunk, unrestricted: project b and form
+// per spin, SOX within each spin); with THC_GW the screened evaluation above.  Order per chunk, unrestricted: project b and form
 // Pi_b; project a and add Pi_a; T = V Pi; SOX a, merge a, back-transform a; project b
 // again (Y, G^X(tau)), SOX b, merge b, back-transform b.
 int fp64_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const double* const* G_bmt,
                     double* const* Sigma) {
+  if (ctx->terms & THC_GW) return fp64_eval_gw(ctx, nspin, G_tau, G_bmt, Sigma);
   const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau, nn = n * n, NN = N * N;
   const bool sox = ctx->terms & THC_SOX, dir = ctx->terms & THC_DIRECT;
   const double cd = nspin == 1 ? C_DIRECT : -1.0;
@@ -368,7 +375,6 @@ int fp64_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const d
 }
 
 int fp64_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
-  if (ctx->terms & THC_GW) return fp64_eval_gw(ctx, G_tau, G_bmt, Sigma);
   return fp64_eval_spins(ctx, 1, &G_tau, &G_bmt, &Sigma);
 }
 

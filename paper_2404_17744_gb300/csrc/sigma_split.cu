@@ -822,28 +822,34 @@ int split_merge_back(thc_ctx* ctx, long long tc, bool sox, bool dir, double cd, 
   return split_back(ctx, tc, Sigma_chunk);
 }
 
-// Screened direct term (THC_GW) with or without SOX, restricted: the bubble of every tau
-// point from the split projections first (the bosonic transform couples them), the
-// screening in FP64 (gw.cu), then per chunk SOX, the merge M = C_SOX D^T - G^X o W~ in
-// FP64, its split, and the split back-transform.
-int split_eval_gw(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
+// Screened direct term (THC_GW) with or without SOX, restricted (nspin 1) or unrestricted
+// (nspin 2): the bubble of every tau point from the split projections first (the bosonic
+// transform couples them; unrestricted, spin b and then spin a added), the screening in
+// FP64 (gw.cu), then per chunk and spin SOX, the merge M = C_SOX D^T - G^X_s o W~ in FP64,
+// its split, and the split back-transform.
+int split_eval_gw(thc_ctx* ctx, int nspin, const double* const* G_tau, const double* const* G_bmt,
+                  double* const* Sigma) {
   const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau, ldN = ctx->ldN, nn = n * n, NN = N * N;
   const bool sox = ctx->terms & THC_SOX;
   if (!ctx->gw_nw) return fail(ctx, THC_EINVAL, "THC_GW needs the bosonic transforms (thc_sigma_set_bosonic)");
   for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
     const long long tc = std::min<long long>(ctx->tc, nt - c0);
-    THC_TRY(split_project(ctx, G_tau, G_bmt, c0, tc, true, true));
-    THC_TRY(gw_store_bubble_f32(ctx, c0, tc));
+    for (int s = nspin - 1; s >= 0; --s) {
+      THC_TRY(split_project(ctx, G_tau[s], G_bmt[s], c0, tc, true, true));
+      THC_TRY(gw_store_bubble(ctx, c0, tc, nspin, s));
+    }
   }
   THC_TRY(gw_screen(ctx));
   for (long long c0 = 0; c0 < nt; c0 += ctx->tc) {
     const long long tc = std::min<long long>(ctx->tc, nt - c0);
-    THC_TRY(split_project(ctx, G_tau, G_bmt, c0, tc, false, false));  // Y and G(-tau) for SOX
-    if (sox) THC_TRY(split_sox(ctx, tc));
-    THC_TRY(gw_merge(ctx, c0, tc, sox ? ctx->Dd : nullptr, ctx->gw_m));
-    const Split Ms = split3_of(ctx->Ms_h, ctx->Ms_l, ctx->Ms_l2, N, ldN, tc);
-    THC_TRY(launch_split_f64(ctx, ctx->gw_m, NN, N, 1, 1.0, Ms, N, "split M"));
-    THC_TRY(split_back(ctx, tc, Sigma + c0 * nn));
+    for (int s = 0; s < nspin; ++s) {
+      THC_TRY(split_project(ctx, G_tau[s], G_bmt[s], c0, tc, false, false));  // Y and G(-tau) for SOX
+      if (sox) THC_TRY(split_sox(ctx, tc));
+      THC_TRY(gw_merge(ctx, c0, tc, sox ? ctx->Dd : nullptr, ctx->gw_m, s));
+      const Split Ms = split3_of(ctx->Ms_h, ctx->Ms_l, ctx->Ms_l2, N, ldN, tc);
+      THC_TRY(launch_split_f64(ctx, ctx->gw_m, NN, N, 1, 1.0, Ms, N, "split M"));
+      THC_TRY(split_back(ctx, tc, Sigma[s] + c0 * nn));
+    }
   }
   return THC_OK;
 }
@@ -851,10 +857,11 @@ int split_eval_gw(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double
 }  // namespace
 
 // Restricted (nspin = 1) or unrestricted (nspin = 2) evaluation; the steps and their order
-// are those of fp64_eval_spins.  The polarisation of spin b is kept in FP32 (Pif) and added
+// are those of fp64_eval_spins (THC_GW: split_eval_gw above).  The polarisation of spin b is kept in FP32 (Pif) and added
 // to that of spin a before the split of Pi.
 int split_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const double* const* G_bmt,
                      double* const* Sigma) {
+  if (ctx->terms & THC_GW) return split_eval_gw(ctx, nspin, G_tau, G_bmt, Sigma);
   const long long n = ctx->n, N = ctx->N, nt = ctx->n_tau, ldN = ctx->ldN, nn = n * n;
   const bool sox = ctx->terms & THC_SOX, dir = ctx->terms & THC_DIRECT;
   const double cd = nspin == 1 ? C_DIRECT : -1.0;
@@ -885,7 +892,6 @@ int split_eval_spins(thc_ctx* ctx, int nspin, const double* const* G_tau, const 
 }
 
 int split_eval(thc_ctx* ctx, const double* G_tau, const double* G_bmt, double* Sigma) {
-  if (ctx->terms & THC_GW) return split_eval_gw(ctx, G_tau, G_bmt, Sigma);
   return split_eval_spins(ctx, 1, &G_tau, &G_bmt, &Sigma);
 }
 

@@ -299,7 +299,6 @@ int thc_sigma_eval_uhf(thc_ctx* ctx, const double* G_tau_a, const double* G_bmt_
   const long long len = (long long)ctx->n_tau * ctx->n * ctx->n;
   for (const double* p : in)
     if (p) THC_TRY(launch_finite_scan(ctx, p, len, ctx->d_err + 1));
-  if (ctx->terms & THC_GW) return fail(ctx, THC_ENOTSUP, "the screened (GW) term is restricted only");
   const double* G[2] = {G_tau_a, G_tau_b};
   const double* Gb[2] = {G_bmt_a, G_bmt_b};
   double* S[2] = {Sigma_a, Sigma_b};

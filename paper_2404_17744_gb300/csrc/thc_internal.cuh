@@ -98,7 +98,8 @@ struct thc_ctx {
   double *gw_toiw = nullptr, *gw_totau = nullptr;   // n_omega x n_tau, n_tau x n_omega
   double *gw_vinv = nullptr;                        // V^-1, N x N
   double *gw_pi = nullptr;                          // Pi~(tau), then W~(tau): n_tau x N x N
-  double *gw_gx = nullptr;                          // G^X(tau), n_tau x N x N
+  double *gw_gx = nullptr;                          // G^X(tau), n_tau x N x N (restricted, or spin a)
+  double *gw_gx_b = nullptr;                        // G^X(tau) of spin b (unrestricted, on first use)
   double *gw_w = nullptr;                           // W(i Omega), n_omega x N x N
   double *gw_scr = nullptr;                         // Gauss-Jordan scratch
   double *gw_m = nullptr;                           // split path: M of a chunk, tc x N x N
@@ -160,10 +161,9 @@ void ctx_destroy(thc_ctx* ctx);
 // screened direct term (gw.cu)
 int gj_invert_spd(thc_ctx* ctx, double* A, long long n, long long batch);
 int gw_set_transforms(thc_ctx* ctx, int n_omega, const double* to_iw, const double* to_tau);
-int gw_store_bubble(thc_ctx* ctx, long long c0, long long tc);
+int gw_store_bubble(thc_ctx* ctx, long long c0, long long tc, int nspin, int spin);
 int gw_screen(thc_ctx* ctx);
-int gw_store_bubble_f32(thc_ctx* ctx, long long c0, long long tc);
-int gw_merge(thc_ctx* ctx, long long c0, long long tc, const double* D, double* M);
+int gw_merge(thc_ctx* ctx, long long c0, long long tc, const double* D, double* M, int spin);
 
 // autotuner table of the split contractions (sigma_split.cu)
 int autotune_save(const char* path);

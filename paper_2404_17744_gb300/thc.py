@@ -25,7 +25,7 @@ THC_TF32 = 2      # not built: thc_sigma_init returns THC_ENOTSUP
 THC_DIRECT = 1
 THC_SOX = 2
 THC_KCLASS_SOX_BCD = 11   # index of sox_BCD among the kernel classes (profiler and autotune table)
-THC_GW = 4        # screened direct term (scGW / scGWSOX), restricted; needs thc_sigma_set_bosonic
+THC_GW = 4        # screened direct term (scGW / scGWSOX); needs thc_sigma_set_bosonic
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libthcsigma.so")
 
