@@ -48,9 +48,9 @@ L2_BYTES = 129 * 1024 * 1024
 NCU_TRAFFIC = {
     ("sox_B", "thc200"): (0.324722e9 + 0.820432e9, "profiles/sox_b_gemm_kernel_thc200s.md (same per-launch shape)"),
     ("sox_B", "thc200s"): (0.324722e9 + 0.820432e9, "profiles/sox_b_gemm_kernel_thc200s.md"),
-    ("sox_BCD", "thc200:bf16x3"): (0.433399e9 + 0.007220e9,
+    ("sox_BCD", "thc200:bf16x3"): (0.433421e9 + 0.007113e9,
                                    "profiles/sox_bcd_kernel_thc200s.md (same per-launch shape)"),
-    ("sox_BCD", "thc200s:bf16x3"): (0.433399e9 + 0.007220e9, "profiles/sox_bcd_kernel_thc200s.md"),
+    ("sox_BCD", "thc200s:bf16x3"): (0.433421e9 + 0.007113e9, "profiles/sox_bcd_kernel_thc200s.md"),
 }
 
 

@@ -458,6 +458,12 @@ int launch_bcd_shape(thc_ctx* ctx, const Split& Y, const Split& U, const Split& 
   const long long udims[3] = {n, n, N}, adims[3] = {n, n, Pc};
   const long long strides[2] = {ldn * 2, n * ldn * 2};
   const int ubox[3] = {tc::BKE, 1, tc::BM / CP}, abox[3] = {tc::BKE, 1, tc::BM / CR};
+  // a last K block of at most 32 columns (after at least one full one) is loaded for both
+  // products into one stage, with boxes of 16 or 32 columns (32- or 64-byte swizzle)
+  const long long rem = n % tc::BKE;
+  const int tail = (n > tc::BKE && rem > 0) ? (rem <= 16 ? 16 : rem <= 32 ? 32 : 0) : 0;
+  const CUtensorMapSwizzle tsw = tail == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const int utbox[3] = {tail, 1, tc::BM / CP}, atbox[3] = {tail, 1, tc::BM / CR};
   for (int h = 0; h < 2; ++h) {
     tc::BcdMaps& m = h ? ml : mh;
     const bf16* y = h ? Y.lo : Y.hi;
@@ -465,6 +471,17 @@ int launch_bcd_shape(thc_ctx* ctx, const Split& Y, const Split& U, const Split& 
     THC_TRY(make_map(ctx, &m.yr, y, n, Y, tc::BM / CP));
     THC_TRY(make_map_3d(ctx, &m.u, h ? U.lo : U.hi, udims, strides, ubox));
     THC_TRY(make_map_3d(ctx, &m.at, h ? At.lo : At.hi, adims, strides, abox));
+    if (tail) {
+      THC_TRY(make_map(ctx, &m.ypt, y, n, Y, tc::BM / CR, tail, tsw));
+      THC_TRY(make_map(ctx, &m.yrt, y, n, Y, tc::BM / CP, tail, tsw));
+      THC_TRY(make_map_3d(ctx, &m.ut, h ? U.lo : U.hi, udims, strides, utbox, tsw));
+      THC_TRY(make_map_3d(ctx, &m.att, h ? At.lo : At.hi, adims, strides, atbox, tsw));
+    } else {
+      m.ypt = m.yp;
+      m.yrt = m.yr;
+      m.ut = m.u;
+      m.att = m.at;
+    }
   }
   auto kern = tc::sox_bcd_kernel<CP, CR>;
   int max_clusters = 0;  // resident clusters of this shape on the current device
@@ -531,7 +548,7 @@ int launch_bcd_shape(thc_ctx* ctx, const Split& Y, const Split& U, const Split& 
   ProfRec rec;
   THC_TRY(prof_begin(ctx, K_SOX_BCD, 2.0 * 2.0 * pairs * n * n, &rec));  // the tiles computed
   const cudaError_t e =
-      cudaLaunchKernelEx(&cfg, kern, mh, ml, tc::BcdArgs{(int)Pc, (int)P0, (int)N, (int)n, nvc, D}, ctx->d_err);
+      cudaLaunchKernelEx(&cfg, kern, mh, ml, tc::BcdArgs{(int)Pc, (int)P0, (int)N, (int)n, nvc, tail, D}, ctx->d_err);
   return prof_end(ctx, &rec, e == cudaSuccess ? cudaGetLastError() : e, "B C/D");
 }
 

@@ -68,14 +68,17 @@ struct BcdArgs {
   int N;      // THC rank: range of R, rows of Y, row length of D
   int n;      // AO count: range of v, depth (w, q) of both products
   int nvc;    // v chunks per cluster tile
+  int tail;   // 16 or 32: the last K block of both products (n mod 64 <= tail, n > 64) is
+              // loaded with boxes that wide into one shared stage; 0: every K block alone
   double* D;  // N x N FP64, D[P][R] at P * N + R
 };
 
 // Tensor maps of one operand half (hi or lo): Y rows for the P side (box 64 x 128/CR)
 // and the R side (box 64 x 128/CP), U (w, v, R) with box 64 x 1 x 128/CP, and
-// A^T (q, v, P) with box 64 x 1 x 128/CR.
+// A^T (q, v, P) with box 64 x 1 x 128/CR; the same four with boxes of the tail width.
 struct BcdMaps {
   CUtensorMap yp, yr, u, at;
+  CUtensorMap ypt, yrt, ut, att;
 };
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
@@ -132,6 +135,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t rank = CS > 1 ? cluster_ctarank() : 0u;
   const int pi = (int)rank / CR, rj = (int)rank % CR;
   const int nkb = (a.n + BKE - 1) / BKE;
+  // K blocks each product loads alone; with a tail, its last block shares one stage with the
+  // other product's (8 narrow blocks: C's Y_P and U_v, B's A^T_v and Y_R, hi and lo)
+  const int nkf = a.tail ? nkb - 1 : nkb;
+  const int NB = BM * 2 * a.tail;  // bytes of one narrow block
+  const int tk0 = (nkb - 1) * BKE;  // first K of the tail
   const int tm = (a.Pc + BM - 1) / BM, tn = (a.N + BM - 1) / BM;
   const int tm2 = (tm + CP - 1) / CP, tn2 = (tn + CR - 1) / CR;
   // D is symmetric: only cluster tiles that reach R >= P are computed.  Cluster row i
@@ -176,6 +184,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     prefetch_map(&lo.u);
     prefetch_map(&hi.at);
     prefetch_map(&lo.at);
+    if (a.tail) {
+      prefetch_map(&hi.ypt);
+      prefetch_map(&lo.ypt);
+      prefetch_map(&hi.yrt);
+      prefetch_map(&lo.yrt);
+      prefetch_map(&hi.ut);
+      prefetch_map(&lo.ut);
+      prefetch_map(&hi.att);
+      prefetch_map(&lo.att);
+    }
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -192,10 +210,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint16_t pmask = 0, rmask = 0;  // CTAs sharing this CTA's P tile / R tile
       for (int r = 0; r < CR; ++r) pmask |= (uint16_t)(1u << (pi * CR + r));
       for (int p = 0; p < CP; ++p) rmask |= (uint16_t)(1u << (p * CR + rj));
-      // one slice of an operand block: multicast when shared, a plain load otherwise
+      // one slice of an operand block (rows of rowb bytes): multicast when shared, a plain
+      // load otherwise
       auto load = [&](uint8_t* blk, int slice, int rows, const CUtensorMap* m, uint64_t* bar, int c0, int c1, int c2,
-                      uint16_t mask, bool shared) {
-        uint8_t* dst = blk + slice * rows * 128;
+                      uint16_t mask, bool shared, int rowb = 128) {
+        uint8_t* dst = blk + slice * rows * rowb;
         if (shared)
           tma_load_3d_mc(dst, m, bar, c0, c1, c2, mask);
         else
@@ -209,7 +228,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int prow = pt * BM + rj * PROWS, rrow = rt * BM + pi * RROWS;  // first rows of this CTA's slices
         for (int v = v0; v < v1 && ok; ++v) {
           for (int prod = 0; prod < 2 && ok; ++prod) {
-            for (int kb = 0; kb < nkb; ++kb, ++g) {
+            for (int kb = 0; kb < nkf; ++kb, ++g) {
               const int s = (int)(g % C::STAGES);
               const uint32_t r = (uint32_t)(g / C::STAGES);
               if (!mbar_wait(&empty[s], (r & 1) ^ 1)) {
@@ -232,6 +251,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 load(st + 3 * C::OP, pi, RROWS, &lo.yr, &full[s], k0, rrow, 0, rmask, CP > 1);
               }
             }
+          }
+          if (a.tail && ok) {  // the tails of both products in one stage
+            const int s = (int)(g % C::STAGES);
+            const uint32_t r = (uint32_t)(g / C::STAGES);
+            if (!mbar_wait(&empty[s], (r & 1) ^ 1)) {
+              atomicExch(err, 11);
+              ok = false;
+              break;
+            }
+            uint8_t* st = smem + s * C::STAGE;
+            const int rb = 2 * a.tail;
+            mbar_arrive_expect_tx(&full[s], (uint32_t)(8 * NB));
+            load(st, rj, PROWS, &hi.ypt, &full[s], tk0, a.P0 + prow, 0, pmask, CR > 1, rb);
+            load(st + NB, rj, PROWS, &lo.ypt, &full[s], tk0, a.P0 + prow, 0, pmask, CR > 1, rb);
+            load(st + 2 * NB, pi, RROWS, &hi.ut, &full[s], tk0, v, rrow, rmask, CP > 1, rb);
+            load(st + 3 * NB, pi, RROWS, &lo.ut, &full[s], tk0, v, rrow, rmask, CP > 1, rb);
+            load(st + 4 * NB, rj, PROWS, &hi.att, &full[s], tk0, v, prow, pmask, CR > 1, rb);
+            load(st + 5 * NB, rj, PROWS, &lo.att, &full[s], tk0, v, prow, pmask, CR > 1, rb);
+            load(st + 6 * NB, pi, RROWS, &hi.yrt, &full[s], tk0, rrow, 0, rmask, CP > 1, rb);
+            load(st + 7 * NB, pi, RROWS, &lo.yrt, &full[s], tk0, rrow, 0, rmask, CP > 1, rb);
+            ++g;
           }
         }
       }
@@ -267,7 +307,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tc_fence_after();
           for (int prod = 0; prod < 2 && ok; ++prod) {
             const uint32_t d = tmem + static_cast<uint32_t>(buf * 256 + prod * 128);
-            for (int kb = 0; kb < nkb; ++kb, ++g) {
+            for (int kb = 0; kb < nkf; ++kb, ++g) {
               const int s = (int)(g % C::STAGES);
               if (!mbar_wait(&full[s], (uint32_t)(g / C::STAGES) & 1)) {
                 atomicExch(err, 12);
@@ -293,6 +333,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               else
                 mma_commit(&empty[s]);
             }
+          }
+          if (a.tail && ok) {  // the tails of C_v and B_v from the shared stage (accumulating)
+            const int s = (int)(g % C::STAGES);
+            if (!mbar_wait(&full[s], (uint32_t)(g / C::STAGES) & 1)) {
+              atomicExch(err, 12);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + s * C::STAGE);
+            const int ksteps = (a.n - tk0 + 15) >> 4;  // 1 or 2 for a tail of 16 or 32
+            for (int prod = 0; prod < 2; ++prod) {
+              const uint32_t d = tmem + static_cast<uint32_t>(buf * 256 + prod * 128);
+              const uint32_t b0 = base + (uint32_t)(4 * prod * NB);
+              const uint64_t ah = narrow_desc(b0, a.tail), al = narrow_desc(b0 + NB, a.tail);
+              const uint64_t bh = narrow_desc(b0 + 2 * NB, a.tail), bl = narrow_desc(b0 + 3 * NB, a.tail);
+              for (int k = 0; k < ksteps; ++k) {
+                const uint64_t off = static_cast<uint64_t>((k * 32) >> 4);
+                mma_bf16(d, ah + off, bh + off, idesc, 1u);
+                mma_bf16(d, ah + off, bl + off, idesc, 1u);
+                mma_bf16(d, al + off, bh + off, idesc, 1u);
+              }
+            }
+            if constexpr (CS > 1)
+              mma_commit_mc(&empty[s], all);
+            else
+              mma_commit(&empty[s]);
+            ++g;
           }
           if (ok) mma_commit(&acc_full[buf]);  // C_v and B_v of this v complete
         }
