@@ -32,7 +32,10 @@ Two routes are implemented for each term:
 
 Pins (tests/test_oracle_pins.py): four-index agreement, one-orbital closed
 form, finite-temperature MP2 closed form, zero-temperature textbook MP2,
-symmetry, V-scaling, fragment separability.
+symmetry, V-scaling, fragment separability; unrestricted: the spin-orbital
+four-index definition and the restricted limit; screened term: the weak-coupling
+limit, one-orbital closed forms (one spin level, and two different ones
+unrestricted), symmetry, the restricted limit of the unrestricted form.
 """
 from __future__ import annotations
 
