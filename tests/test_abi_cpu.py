@@ -84,3 +84,38 @@ def test_wait_selftest_rejects_bad_limits_without_gpu(lib):
         with pytest.raises(thc.ThcError) as ei:
             thc.thc_wait_selftest(bad)
         assert ei.value.code == thc.THC_EINVAL
+
+
+def test_autotune_cache_round_trip_and_validation(lib, tmp_path):
+    """The tile-table cache is host logic: a load keeps only the choices the kernels can
+    take (tile widths 128 / 256; fused B C/D cluster shapes 11, 12, 22), stops at a line
+    it cannot parse, and a save writes back what the table holds; a missing file is
+    THC_EINVAL."""
+    from paper_2404_17744_gb300 import thc
+    bcd = thc.THC_KCLASS_SOX_BCD
+    src = tmp_path / "tiles.txt"
+    src.write_text(
+        f"3 1000 1000 200 4 256\n"        # a contraction class, BN 256: kept
+        f"3 1000 1000 200 8 128\n"        # BN 128: kept
+        f"3 1000 1000 200 16 64\n"        # BN 64: no such tile, dropped
+        f"{bcd} 1000 1000 200 0 12\n"     # 1 x 2 cluster: kept
+        f"{bcd} 1000 1000 200 512 22\n"   # 2 x 2 cluster: kept
+        f"{bcd} 1000 1000 200 256 13\n"   # 1 x 3: not a shape of the kernel, dropped
+        f"{bcd} 1000 1000 200 768 128\n"  # a tile width for the cluster class, dropped
+        "garbage line\n"
+        f"3 1000 1000 200 32 256\n")      # after the unparsable line: not read
+    before = thc.thc_autotune_entries()
+    thc.thc_autotune_load(src)
+    assert thc.thc_autotune_entries() == before + 4
+    out = tmp_path / "saved.txt"
+    thc.thc_autotune_save(out)
+    saved = {tuple(int(x) for x in line.split()) for line in out.read_text().splitlines()}
+    for row in ((3, 1000, 1000, 200, 4, 256), (3, 1000, 1000, 200, 8, 128), (bcd, 1000, 1000, 200, 0, 12),
+                (bcd, 1000, 1000, 200, 512, 22)):
+        assert row in saved
+    for key in ((3, 1000, 1000, 200, 16), (bcd, 1000, 1000, 200, 256), (bcd, 1000, 1000, 200, 768),
+                (3, 1000, 1000, 200, 32)):
+        assert not any(r[:5] == key for r in saved)
+    with pytest.raises(thc.ThcError) as ei:
+        thc.thc_autotune_load(tmp_path / "missing.txt")
+    assert ei.value.code == thc.THC_EINVAL
