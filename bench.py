@@ -706,6 +706,88 @@ def run_c5_loop(args, gw=False):
     return 0
 
 
+def run_c1(args):
+    """c1 sizes (20 AOs, 60 THC points, 32 Gauss-Legendre tau points, beta = 100): the whole
+    Sigma evaluation on the GPU (FP64 and 3xBF16, CUDA events, median of args.steps after
+    args.warmup) and the oracle run and timed in the same process on the host cores: its
+    THC route over all 32 tau points, and its four-index route (the definition, an
+    unoptimised eight-index sum per term, one thread) on one tau point, extrapolated
+    linearly to the 32 points and labelled so."""
+    import torch
+    from oracle import thc_oracle as o
+    from paper_2404_17744_gb300 import thc
+    from workloads import synth
+    rank, world, local = dist_env()
+    if world > 1:
+        return single_gpu_only(args, rank, world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    case = synth.make_workload("thc20")
+    flops = algorithmic_flops(case.n, case.N, case.n_tau)
+    X = torch.from_numpy(case.X).to(dev)
+    V = torch.from_numpy(case.V).to(dev)
+    G = torch.from_numpy(np.ascontiguousarray(case.G_tau)).to(dev)
+    gpu = {}
+    for name, prec in (("fp64", thc.THC_FP64), ("bf16x3", thc.THC_BF16X3)):
+        ctx = thc.thc_sigma_init(case.n, case.N, case.n_tau, case.beta, X, V, np.ascontiguousarray(case.tau), prec, 3,
+                                 stream.cuda_stream)
+        try:
+            S = torch.empty_like(G)
+            ts = []
+            for i in range(max(3, args.warmup) + max(1, args.steps)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                thc.thc_sigma_eval(ctx, G, None, S)
+                b.record(stream)
+                thc.thc_sync(ctx)
+                if i >= max(3, args.warmup):
+                    ts.append(a.elapsed_time(b) * 1e-3)
+            E = thc.thc_energy(ctx, G, None, S, np.ascontiguousarray(case.tau_w))
+            gpu[name] = {"s_per_sigma_eval": float(np.median(ts)), "tflops": flops / float(np.median(ts)) / 1e12,
+                         "E_dyn": E, "Sigma": S.cpu().numpy()}
+        finally:
+            thc.thc_destroy(ctx)
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    ref = o.sigma_thc(case.X, case.V, case.G_tau, case.G_bmt)  # U built inside (0.1 % of the work here)
+    t_thc = time.perf_counter() - t0
+    E_ref = o.energy_dyn_tau(case.G_bmt, ref, case.tau_w)
+    print(f"c1: GPU FP64 {gpu['fp64']['s_per_sigma_eval'] * 1e3:.3f} ms, 3xBF16 "
+          f"{gpu['bf16x3']['s_per_sigma_eval'] * 1e3:.3f} ms; oracle THC route {t_thc:.3f} s", file=sys.stderr, flush=True)
+    v = o.eri_from_thc(case.X, case.V)
+    k = 0
+    Gm = o.g_minus_tau(case.G_bmt[k])
+    t0 = time.perf_counter()
+    four = o.sigma_sox_four_index(v, case.G_tau[k], Gm)
+    t_sox = time.perf_counter() - t0
+    print(f"c1: four-index SOX term, one tau point: {t_sox:.1f} s", file=sys.stderr, flush=True)
+    t0 = time.perf_counter()
+    four = four + o.sigma_direct_four_index(v, case.G_tau[k], Gm)
+    t_four = t_sox + time.perf_counter() - t0
+    print(f"c1: four-index both terms, one tau point: {t_four:.1f} s", file=sys.stderr, flush=True)
+    out = {"metric": METRIC, "value": gpu["fp64"]["tflops"], "unit": UNIT, "n_gpus": 1, "steps": max(1, args.steps),
+           "warmup": max(3, args.warmup), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"c1: n_ao={case.n}, n_thc={case.N}, n_tau={case.n_tau} (Gauss-Legendre), "
+                                  f"beta={case.beta}, S = I, G = noninteracting G(tau) of a seeded F"},
+           "c1": {"gpu_fp64": {k2: w for k2, w in gpu["fp64"].items() if k2 != "Sigma"},
+                  "gpu_bf16x3": {k2: w for k2, w in gpu["bf16x3"].items() if k2 != "Sigma"},
+                  "max_abs_dsigma_fp64_vs_oracle": float(np.abs(gpu["fp64"]["Sigma"] - ref).max()),
+                  "max_abs_dsigma_bf16x3_vs_oracle": float(np.abs(gpu["bf16x3"]["Sigma"] - ref).max()),
+                  "E_dyn_oracle": E_ref,
+                  "oracle_thc_route": {"s_all_tau": t_thc, "cores": cores,
+                                       "tflops": flops / t_thc / 1e12},
+                  "oracle_four_index_route": {"s_one_tau": t_four, "s_one_tau_sox_term": t_sox,
+                                              "s_all_tau_extrapolated": t_four * case.n_tau,
+                                              "cores": 1, "kind": "oracle, brute force",
+                                              "sample": "tau point 0 of 32, both terms, extrapolated linearly",
+                                              "max_abs_dsigma_vs_thc_route": float(np.abs(four - ref[k]).max())}}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def single_gpu_only(args, rank, world):
     """Multi-process launch of the GPU arm: nothing runs on any GPU; rank 0 reports why."""
     if rank == 0:
@@ -726,6 +808,8 @@ def main():
         return run_batch64(args)
     if args.workload in ("c5loop", "c5loop_gw"):
         return run_c5_loop(args, gw=args.workload == "c5loop_gw")
+    if args.workload == "c1":
+        return run_c1(args)
     return run_ours(args)
 
 
